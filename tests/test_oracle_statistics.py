@@ -1,0 +1,94 @@
+"""Statistical pins of the oracle on the paper's 21x21 periodic lattice
+(Section 3 and Section 4).
+
+* At u0 = 0 both bases coincide and the equal-time correlations are the ideal
+  gas's (Eq. dfdf, scaled by kT): <df_i df_j> = kT rho0 w_i delta_ij, less the
+  k = 0 contribution of the three exactly conserved modes (1/N of their share).
+* At u0 != 0 the Hermite-norm run drifts away from kT f_i^0(rho0,u0) while the
+  f-norm run stays close (Figs. 2-4 versus 12-14), and the quadratic drift of
+  the moment correlators matches the coefficients printed in Section 4
+  (tests/golden/paper_q_coefficients.json) within the looseness those numbers
+  carry (unstated relaxation rates, look-up-table variant).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_1204_6734_gb300 import inputs
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "paper_q_coefficients.json")
+KT = 1e-4
+OMEGA = inputs.omega_groups(1.0, 0.8, 1.0)
+
+
+def _batched_cov(oracle, p, warmup, nbatch, per_batch):
+    run = oracle.Run(p, warmup=warmup, every=1)
+    run.step(warmup)
+    covs = []
+    prev = (run.S1.copy(), run.S2.copy(), run.nsamp)
+    for _ in range(nbatch):
+        run.step(per_batch)
+        S1, S2, n = run.S1 - prev[0], run.S2 - prev[1], run.nsamp - prev[2]
+        covs.append(oracle.covariance(S1, S2, n)[0])
+        prev = (run.S1.copy(), run.S2.copy(), run.nsamp)
+    covs = np.array(covs)
+    return covs.mean(0), covs.std(0) / np.sqrt(nbatch), run
+
+
+@pytest.mark.parametrize("basis", ["standard", "local"])
+def test_ideal_gas_at_rest(oracle, basis):
+    vx, vy, w, P, _ = oracle.tables()
+    p = inputs.LatticeParams(21, 21, 1.0, 0.0, 0.0, KT, OMEGA, basis, "fp64", seed=31)
+    C, err, _ = _batched_cov(oracle, p, 500, 10, 400)
+    N = 21 * 21
+    cons = [w * P[a] for a in range(3)]
+    expect = KT * (np.diag(w) - sum(np.outer(c, c) for c in cons) / N)
+    z = np.abs(C - expect) / (err + 1e-3 * KT * w.max())
+    assert z.max() < 5, z.max()
+
+
+def _drift(oracle, basis, u, seed):
+    p = inputs.LatticeParams(21, 21, 1.0, u, 0.0, KT, OMEGA, basis, "fp64", seed=seed)
+    run = oracle.Run(p, warmup=500, every=1).step(6500)
+    C, _ = run.covariance()
+    CM = oracle.moment_covariance(C, basis, u, 0.0)
+    return C, np.diag(CM) / KT - 1.0
+
+
+def test_galilean_drift_matches_printed_coefficients(oracle):
+    gold = json.load(open(GOLD))
+    idx = gold["moments"]
+    us = np.array([0.1, 0.15, 0.2, 0.25])
+    q = {}
+    for basis in ("standard", "local"):
+        d = np.array([_drift(oracle, basis, u, seed=40 + k)[1] for k, u in enumerate(us)])
+        # <dM^a dM^a> is even in u_x0, so l = 0 on the diagonal: fit d = q u^2
+        q[basis] = {name: float(np.sum(d[:, a] * us ** 2) / np.sum(us ** 4))
+                    for name, a in idx.items()}
+    for name in idx:
+        qh, qf = q["standard"][name], q["local"][name]
+        assert qh == pytest.approx(gold["q_hermite"][name], rel=0.3), (name, qh)
+        assert qf == pytest.approx(gold["q_fnorm"][name], rel=0.5), (name, qf)
+    # the f-norm reduces the drift of rho and Pi_xx-yy by more than 2x
+    assert q["standard"]["rho"] > 2.5 * q["local"]["rho"]
+    assert q["standard"]["Pi_xx-yy"] > 2 * q["local"]["Pi_xx-yy"]
+
+
+def test_fnorm_follows_f0_and_hermite_does_not(oracle):
+    """<df_i df_i> / (kT f_i^0(rho0,u0)) at u0 = 0.2: within 7% of one for the
+    f-norm (Figs. 12-14), off by more than 30% for some i with the Hermite
+    norm (Figs. 2-4)."""
+    f0 = oracle.feq(1.0, 0.2, 0.0)
+    Cs, _ = _drift(oracle, "standard", 0.2, seed=61)
+    Cl, _ = _drift(oracle, "local", 0.2, seed=62)
+    rs = np.diag(Cs) / (KT * f0)
+    rl = np.diag(Cl) / (KT * f0)
+    assert np.abs(rl - 1).max() < 0.07, rl
+    assert np.abs(rs - 1).max() > 0.3, rs
+    # mirror symmetry of Figs. 3-4: <df2^2> = <df4^2>, <df5^2> = <df8^2>, <df6^2> = <df7^2>
+    for C in (Cs, Cl):
+        d = np.diag(C) / KT
+        for a, b in ((2, 4), (5, 8), (6, 7)):
+            assert d[a] == pytest.approx(d[b], rel=0.03)
