@@ -1,0 +1,300 @@
+"""Benchmark of the fused fluctuating D2Q9 step on GB300.
+
+One benchmark step = one pass of the whole hot path over the 4096x4096 FP32
+lattice: pull streaming, density and velocity, the per-node basis, relaxation,
+Philox noise, back transform and store (the step kernel), with the equal-time
+correlation sums sampled on every step (fused into the step kernel) and reduced
+into the FP64 accumulators (second kernel). Inputs (two 604 MB population
+buffers) are larger than L2 and stay resident in HBM.
+
+Prints one JSON line. Multi-GPU runs are independent replicas (one lattice per
+rank, weak scaling); ranks only meet at the barriers around the timed region.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS & % of HBM roofline (FP32 vs FP64); batched replica-steps/s, p50/p99"
+UNIT = "MLUPS"
+BYTES_PER_NODE = {"fp32": 72, "fp64": 144}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--basis", default="local", choices=["local", "standard"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--ux0", type=float, default=0.1)
+    ap.add_argument("--side", type=int, default=4096)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def smi_id(dev):
+    """nvidia-smi identifier of torch device `dev` (honours CUDA_VISIBLE_DEVICES)."""
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "").strip()
+    if vis:
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if dev < len(ids):
+            return ids[dev]
+    return str(dev)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_mlups(p, max_seconds=10.0, side=512):
+    """Oracle (plain FP64 C, one thread) on a side x side sample of the workload's
+    parameters: calibrate one step, then run enough steps to fill ~max_seconds."""
+    import oracle as O
+    from paper_1204_6734_gb300 import inputs
+    q = inputs.LatticeParams(side, side, p.rho0, p.ux0, p.uy0, p.kT, p.omega, p.basis, "fp64",
+                             seed=p.seed)
+    run = O.Run(q, warmup=0, every=1)
+    t0 = time.perf_counter()
+    run.step(1)
+    one = time.perf_counter() - t0
+    n = max(1, int(max_seconds / max(one, 1e-6)) - 1)
+    t0 = time.perf_counter()
+    run.step(n)
+    dt = time.perf_counter() - t0
+    return side * side * n / dt / 1e6, f"{side}x{side} lattice, {n} steps (sampling on), same parameters", 1
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_1204_6734_gb300 import inputs
+    p = inputs.single_lattice(args.ux0, args.basis, side=args.side, precision="fp64")
+    import oracle as O
+    side = 256
+    q = inputs.LatticeParams(side, side, p.rho0, p.ux0, p.uy0, p.kT, p.omega, p.basis, "fp64",
+                             seed=p.seed)
+    run = O.Run(q, warmup=0, every=1)
+    run.step(args.warmup)
+    t0 = time.perf_counter()
+    run.step(args.steps)
+    dt = time.perf_counter() - t0
+    value = side * side * args.steps / dt / 1e6
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"{p.Lx}x{p.Ly} periodic D2Q9, {p.basis} basis, u_x0={p.ux0}",
+                   "sample": f"{side}x{side} lattice per step", "l2": "oracle on host cores"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{side}x{side} lattice, {args.steps} steps"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+
+    from paper_1204_6734_gb300 import flb, inputs
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    flb.load()
+
+    p = inputs.single_lattice(args.ux0, args.basis, side=args.side, precision=args.precision)
+    p.replica = rank                      # independent replica per rank
+    p.seed = p.seed + 7919 * rank
+    nodes = p.Lx * p.Ly
+    stream = torch.cuda.Stream(device=dev)
+    lat = flb.Lattice(p, stream=stream)
+    lat.set_sampling(0, 1)                # sample (and reduce) every step
+
+    # warm-up
+    lat.step(args.warmup)
+    lat.sync()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    t_all0 = torch.cuda.Event(enable_timing=True)
+    t_all1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    with ClockSampler(smi_id(dev)) as clk:
+        t_all0.record(stream)
+        for k in range(args.steps):
+            starts[k].record(stream)
+            flb.flb_step(lat.h, 1)
+            ends[k].record(stream)
+        t_all1.record(stream)
+        barrier()
+    lat.sync()
+    total_ms = t_all0.elapsed_time(t_all1)
+    per_step = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = nodes * world * args.steps / (total_ms * 1e-3) / 1e6
+    step_ms = statistics.mean(per_step)
+
+    peak, peak_kind = measured_peaks()
+    algo_bytes = BYTES_PER_NODE[args.precision] * nodes
+    achieved = algo_bytes / (step_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                "kernel": f"step_kernel<{args.precision},{args.basis},sample>"}
+
+    Cff, CMM, mean, ns = lat.correlations(args.basis)
+    lat.close()
+
+    # end to end through the host-buffer entry point: upload the initial state
+    # from pinned host memory, run the same number of steps with sampling,
+    # copy back the final state and the sums
+    e2e = None
+    if not args.no_e2e:
+        f_host = torch.empty((9, p.Ly, p.Lx), dtype=torch.float64, pin_memory=True)
+        f_out = torch.empty((9, p.Ly, p.Lx), dtype=torch.float64, pin_memory=True)
+        with flb.Lattice(p) as tmp:        # equilibrium initial state, not timed
+            flb.flb_get_populations(tmp.h, p.Lx, p.Ly, out=f_host.numpy())
+        barrier()
+        t0 = time.perf_counter()
+        flb.flb_run_host(p, f_host.numpy(), args.steps, warmup=0, every=1, f_out=f_out.numpy())
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        state_bytes = 9 * nodes * 8
+        e2e = {"value": nodes * args.steps / dt / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": state_bytes / args.steps,
+               "d2h_bytes_per_step": (state_bytes + 8 * 90) / args.steps,
+               "what": "flb_run_host: pinned host state in, steps with sampling, state + sums out"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, sample, cores = oracle_mlups(p)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": f"{p.Lx}x{p.Ly} periodic D2Q9 lattice, {args.precision} SoA, "
+                                   f"{args.basis} basis, u_x0={p.ux0}, kT={p.kT}, "
+                                   f"omega shear/bulk/ghost=1.0/0.8/1.0, correlations sampled every step",
+                       "Lx": p.Lx, "Ly": p.Ly, "basis": args.basis, "precision": args.precision,
+                       "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (2 x 604 MB population buffers)"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": 2 * args.steps,
+            "clocks": clk.summary(),
+            "mlups_roofline_frac": value / (peak * 1e9 / BYTES_PER_NODE[args.precision] / 1e6) / world,
+            "n_samples": ns,
+        }
+        print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

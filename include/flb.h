@@ -1,0 +1,189 @@
+/*
+ * flb.h -- C ABI of the GB300 (sm_103a) fluctuating D2Q9 lattice-Boltzmann library.
+ *
+ * The library implements the fused stream-collide-noise step of Kaehler & Wagner,
+ * "A fluctuating lattice-Boltzmann method with improved Galilean invariance"
+ * (arXiv:1204.6734), with either the standard Hermite-norm moment basis
+ * (Section 2, Eqs. fluctf5, d2q93a, d2q93b, d2q94) or the paper's f-norm basis
+ * orthogonalised at every node against the local equilibrium (Section 4,
+ * Eqs. fnorm, gramschmidt, gsortho, Mtilde, fnormmeq), plus the reduction of the
+ * equal-time correlations <df_i df_j> and <dM^a dM^b> (Eqs. dfdef, efif0,
+ * dfidfj2dmadmb).
+ *
+ * Conventions used by every entry point:
+ *  - Return value: FLB_OK (0) or a negative FLB_ERR_* code. No entry point
+ *    aborts, traps or prints. flb_error_string() names a code.
+ *  - Velocities i = 0..8: 0 rest, 1 (+x), 2 (+y), 3 (-x), 4 (-y), 5 (+x+y),
+ *    6 (-x+y), 7 (-x-y), 8 (+x-y) -- the order the j_x, j_y rows of Eq. d2q93a
+ *    imply. Moments a = 0..8: rho, j_x, j_y, Pi_xx-yy, Pi_xy, Pi_xx+yy, q_x,
+ *    q_y, epsilon (Eq. d2q93a).
+ *  - Host population arrays are double, SoA, f[i][y][x] at index
+ *    i*Lx*Ly + y*Lx + x, and hold the pre-collision (post-streaming) state
+ *    f_i(x, t) of Eq. LBE1.
+ *  - Noise: Philox4x32-10 (Salmon et al., SC'11) with counter
+ *    (node = x + Lx*y, step t, replica, 0) and key (seed low, seed high);
+ *    the 128 output bits give six 21-bit fields, three Box-Muller pairs, and
+ *    the normals N^a of a = 3..8 in order. The variance scale is k_B T:
+ *    xi^a = sqrt(kT rho omega_a (2 - omega_a)) (Eq. noiseamp with 1/tau = omega),
+ *    rho the density of the colliding node.
+ *  - Ownership: the caller owns every host pointer passed in; the library copies
+ *    what it needs before returning. A lattice handle owns its device memory
+ *    unless the caller passed a device workspace to flb_create.
+ *  - Streams: all device work of a handle is ordered on the stream given to
+ *    flb_create (NULL = the legacy default stream). Calls on one handle must
+ *    not be made concurrently from several host threads.
+ *  - Errors found on the device (a node whose velocity leaves the region where
+ *    every f_i^0(1,u) > 0, Fig. 11; a non-finite density) are recorded by the
+ *    kernel, which leaves that node uncollided; they are reported by the next
+ *    flb_sync / flb_get_populations / flb_correlations / flb_conservation and
+ *    make the handle refuse further steps until flb_set_populations or
+ *    flb_reset_error.
+ */
+#ifndef FLB_H
+#define FLB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FLB_OK 0
+#define FLB_ERR_ARG (-1)              /* invalid argument or parameter */
+#define FLB_ERR_OOM (-2)              /* device allocation failed or workspace too small */
+#define FLB_ERR_INVALID_VELOCITY (-3) /* some f_i^0(1,u) <= 0 at a node (Fig. 11) */
+#define FLB_ERR_NONFINITE (-4)        /* non-finite or non-positive density at a node */
+#define FLB_ERR_TIMEOUT (-5)          /* a bounded device wait gave up */
+#define FLB_ERR_CUDA (-6)             /* a CUDA runtime call failed */
+#define FLB_ERR_STATE (-7)            /* call not valid in the handle's state (e.g. no samples) */
+
+typedef enum { FLB_BASIS_STANDARD = 0, FLB_BASIS_LOCAL = 1 } flb_basis;
+typedef enum { FLB_FP64 = 0, FLB_FP32 = 1, FLB_FP16_DEV = 2 } flb_precision;
+
+/* Parameters of one periodic lattice. */
+typedef struct {
+    int32_t Lx, Ly;      /* lattice sides, 1 <= Lx, Ly and Lx*Ly < 2^31 */
+    double rho0;         /* mean density (> 0); initial state f^0(rho0, u0) */
+    double ux0, uy0;     /* mean velocity u0; f_i^0(1,u0) > 0 for all i required */
+    double kT;           /* k_B T, the variance scale of the noise (>= 0) */
+    double omega[9];     /* relaxation rate 1/tau^a of moment a; entries 0..2
+                            (conserved) are ignored, 3..8 must lie in (0, 2) */
+    int32_t basis;       /* flb_basis */
+    int32_t precision;   /* flb_precision: FP64 and FP32 compute in that type;
+                            FP16_DEV is reserved */
+    uint64_t seed;       /* Philox key */
+    uint32_t replica;    /* third Philox counter word */
+    uint32_t reserved;   /* must be 0 */
+} flb_params;
+
+typedef struct flb_lattice_s* flb_lattice;
+
+/* Device bytes a lattice with these parameters needs (populations, two
+ * buffers, plus reduction scratch); 0 if the parameters are invalid. */
+size_t flb_workspace_bytes(const flb_params* p);
+
+/* Create a lattice on the current CUDA device, initialised to the uniform
+ * equilibrium f_i = f_i^0(rho0, u0) (Eq. d2q9f0) at time t = 0.
+ *  dev_workspace: NULL to let the library allocate, or a device pointer to at
+ *                 least flb_workspace_bytes(p) bytes, 256-byte aligned, that the
+ *                 caller keeps alive until flb_destroy.
+ *  stream:        a cudaStream_t (as void*), or NULL for the default stream.
+ * Errors: FLB_ERR_ARG (parameters), FLB_ERR_OOM, FLB_ERR_CUDA. */
+int flb_create(const flb_params* p, void* dev_workspace, size_t workspace_bytes,
+               void* stream, flb_lattice* out);
+
+/* Release the lattice and, if the library allocated it, its device memory.
+ * Waits for the handle's stream. NULL is accepted. */
+int flb_destroy(flb_lattice h);
+
+/* Sample the pre-collision state of every step t with t >= warmup and
+ * (t - warmup) % every == 0 into the equal-time correlation sums (every = 0
+ * switches sampling off). Also clears the sums. */
+int flb_set_sampling(flb_lattice h, int64_t warmup, int64_t every);
+
+/* Clear the correlation sums and the sample count. */
+int flb_reset_statistics(flb_lattice h);
+
+/* Enqueue n time steps of Eq. LBE1 (pull streaming, collision with noise) on
+ * the handle's stream; returns without waiting. Errors: FLB_ERR_ARG (n < 0),
+ * a recorded device error (sticky), FLB_ERR_CUDA. */
+int flb_step(flb_lattice h, int64_t n);
+
+/* Wait for the handle's stream and report any device error recorded so far. */
+int flb_sync(flb_lattice h);
+
+/* Current time step t (number of collisions performed). */
+int flb_time(flb_lattice h, int64_t* t);
+
+/* Node and step of the first recorded device error (-1, -1 if none). */
+int flb_error_location(flb_lattice h, int64_t* node, int64_t* step);
+
+/* Forget a recorded device error (the state is left as it is). */
+int flb_reset_error(flb_lattice h);
+
+/* Equal-time correlations of the sampled pre-collision populations (a second
+ * kernel reduces the per-block partial sums; all in FP64):
+ *  Cff[81]   <df_i df_j> = centred covariance of f_i over nodes and samples
+ *            (Eqs. dfdef, efif0; the mean is the sample mean);
+ *  CMM[81]   <dM^a dM^b> = sum_ij m^a_i m^b_j <df_i df_j> (Eq. dfidfj2dmadmb),
+ *            m = the Hermite rows (measure_basis = FLB_BASIS_STANDARD) or the
+ *            f-norm basis at the mean velocity u0 (FLB_BASIS_LOCAL, the choice
+ *            made after Eq. fidjx); orthonormal under w resp. f^0(1,u0), so the
+ *            ideal gas gives CMM = kT rho0 I;
+ *  mean_dev[9]  mean of f_i - f_i^0(rho0, u0);
+ *  n_samples    number of node samples (nodes x sampled steps).
+ * Any output pointer may be NULL. Errors: FLB_ERR_STATE when nothing was
+ * sampled, device errors. Synchronises the handle's stream. */
+int flb_correlations(flb_lattice h, int32_t measure_basis, double* Cff, double* CMM,
+                     double* mean_dev, int64_t* n_samples);
+
+/* Raw FP64 sums S1[i] = sum (f_i - c_i), S2[i*9+j] = sum (f_i - c_i)(f_j - c_j),
+ * c = f^0(rho0, u0), over all samples. Any pointer may be NULL. */
+int flb_raw_sums(flb_lattice h, double* S1, double* S2, int64_t* n_samples);
+
+/* Total mass and momentum of the current state, sum_x (rho, j_x, j_y), reduced
+ * in FP64 on the device. Synchronises. */
+int flb_conservation(flb_lattice h, double sums[3]);
+
+/* Copy the current pre-collision state f_i(x, t) to host memory
+ * (9*Lx*Ly doubles, layout above). Synchronises. */
+int flb_get_populations(flb_lattice h, double* host_out);
+
+/* Replace the current pre-collision state f_i(x, t) by host data (9*Lx*Ly
+ * doubles, layout above; converted to the handle's precision). Clears a
+ * recorded device error. Synchronises. */
+int flb_set_populations(flb_lattice h, const double* host_in);
+
+/* Whole-job entry point with host buffers: create a lattice, upload the
+ * initial state (or start from equilibrium when f_in is NULL), run nsteps
+ * with sampling (warmup, every), and copy back the final state (f_out may be
+ * NULL) and the correlation sums (S1[9], S2[81], n_samples; may be NULL).
+ * Host-device copies are part of the call. */
+int flb_run_host(const flb_params* p, const double* f_in, int64_t nsteps, int64_t warmup,
+                 int64_t every, double* f_out, double* S1, double* S2, int64_t* n_samples);
+
+/* Noise draws of the device code, for testing: for each of n nodes, the six
+ * 21-bit Philox fields and the six standard normals N^3..N^8 the step kernel
+ * of the given precision (FLB_FP64 or FLB_FP32) uses at (seed, replica, node,
+ * step). nodes, fields (6n) and normals (6n) are host arrays. Synchronous. */
+int flb_noise_draws(uint64_t seed, uint32_t replica, uint32_t step, const uint32_t* nodes,
+                    int32_t n, int32_t precision, uint32_t* fields, double* normals);
+
+/* One collision (Eq. LBEMRT) of n independent nodes by the device code, for
+ * testing: g (9n, node-major g[k*9+i]) in, fstar (9n) out, with node index
+ * node_ids[k] and time step `step` for the noise. Computes in p->precision;
+ * p->Lx, p->Ly are ignored. status[k] (may be NULL) receives 0 or an FLB_ERR_*
+ * code per node. Synchronous. */
+int flb_collide_nodes(const flb_params* p, const double* g, const uint32_t* node_ids,
+                      uint32_t step, int32_t n, double* fstar, int32_t* status);
+
+const char* flb_error_string(int code);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int flb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FLB_H */

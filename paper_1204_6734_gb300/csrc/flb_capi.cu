@@ -1,0 +1,780 @@
+// flb_capi.cu -- the C ABI declared in include/flb.h: lattice handles, device
+// memory, kernel launches, correlation/conservation reductions, state I/O.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+
+#include "../../include/flb.h"
+#include "flb_kernels.cuh"
+
+namespace flb {
+
+// ---------------------------------------------------------------------------
+// Reduction kernels
+// ---------------------------------------------------------------------------
+
+__global__ void accumulate_partials_kernel(const double* partials, int nblocks, double* acc) {
+    // one thread per sum, blocks summed in index order: deterministic
+    const int k = threadIdx.x;
+    if (k >= kSums) return;
+    double t = 0.0;
+    for (int b = 0; b < nblocks; ++b) t += partials[(long long)b * kSums + k];
+    acc[k] += t;
+}
+
+// Rows of the basis the correlations are measured in: the Hermite rows
+// (Eq. d2q93a), or the f-norm basis at (ux0, uy0) -- Cholesky of the full 9x9
+// Gram matrix sum_i p^a_i p^b_i f_i^0(1,u0), m~ = L^{-1} P. One thread.
+__global__ void measure_basis_kernel(int basis, double ux0, double uy0, double* out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double P[9][9];
+    {
+        double D[9];
+        for (int a = 0; a < 9; ++a) {
+            for (int b = 0; b < 9; ++b) D[b] = (a == b) ? 1.0 : 0.0;
+            double h[9];
+            hermite_back<double>(D, h);     // column a of P^T = row a of P
+            for (int i = 0; i < 9; ++i) P[a][i] = h[i];
+        }
+    }
+    if (basis == FLB_BASIS_STANDARD) {
+        for (int a = 0; a < 9; ++a)
+            for (int i = 0; i < 9; ++i) out[a * 9 + i] = P[a][i];
+        return;
+    }
+    double W[9];
+    const double usq = ux0 * ux0 + uy0 * uy0;
+    for (int i = 0; i < 9; ++i) {
+        const double uv = ux0 * cvx(i) + uy0 * cvy(i);
+        const double wi = i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+        W[i] = wi * (1.0 + 3.0 * uv + 4.5 * uv * uv - 1.5 * usq);
+    }
+    double L[9][9];
+    for (int a = 0; a < 9; ++a)
+        for (int b = 0; b < 9; ++b) {
+            double s = 0.0;
+            for (int i = 0; i < 9; ++i) s += P[a][i] * W[i] * P[b][i];
+            L[a][b] = s;
+        }
+    for (int j = 0; j < 9; ++j) {
+        double d = L[j][j];
+        for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
+        d = sqrt(d);
+        L[j][j] = d;
+        for (int i = j + 1; i < 9; ++i) {
+            double s = L[i][j];
+            for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
+            L[i][j] = s / d;
+        }
+    }
+    for (int i = 0; i < 9; ++i)          // forward substitution per column of P
+        for (int a = 0; a < 9; ++a) {
+            double s = P[a][i];
+            for (int k = 0; k < a; ++k) s -= L[a][k] * out[k * 9 + i];
+            out[a * 9 + i] = s / L[a][a];
+        }
+}
+
+__global__ void finalize_kernel(const double* acc, long long nsamp, const double* B,
+                                double* out) {
+    __shared__ double C[81];
+    __shared__ double mean[9];
+    const int t = threadIdx.x;
+    const double inv = 1.0 / (double)nsamp;
+    if (t < 9) mean[t] = acc[t] * inv;
+    __syncthreads();
+    if (t < 81) {
+        const int i = t / 9, j = t % 9;
+        const int a = i < j ? i : j, b = i < j ? j : i;
+        // index of (a, b), a <= b, in the packed upper triangle after S1
+        const int k = 9 + a * 9 - a * (a - 1) / 2 + (b - a);
+        C[t] = acc[k] * inv - mean[i] * mean[j];
+        out[t] = C[t];
+    }
+    __syncthreads();
+    if (t < 81) {
+        const int a = t / 9, b = t % 9;
+        double s = 0.0;
+        for (int i = 0; i < 9; ++i)
+            for (int j = 0; j < 9; ++j) s += B[a * 9 + i] * C[i * 9 + j] * B[b * 9 + j];
+        out[81 + t] = s;
+    }
+    if (t < 9) out[162 + t] = mean[t];
+}
+
+// Total mass and momentum of the pre-collision state, FP64 per block.
+template <class T>
+__global__ void __launch_bounds__(kStepThreads)
+conservation_kernel(const T* src, Geometry geo, double* partials) {
+    const long long N = (long long)geo.Lx * geo.Ly;
+    double r = 0.0, jx = 0.0, jy = 0.0;
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
+         n += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(n / geo.Lx), x = (int)(n - (long long)y * geo.Lx);
+        for (int i = 0; i < 9; ++i) {
+            const int xs = (x - cvx(i) + geo.Lx) % geo.Lx, ys = (y - cvy(i) + geo.Ly) % geo.Ly;
+            const double v = (double)src[i * geo.plane + ys * geo.pitch + xs];
+            r += v;
+            jx += v * cvx(i);
+            jy += v * cvy(i);
+        }
+    }
+    __shared__ double red[3][kStepThreads / 32];
+    for (int o = 16; o > 0; o >>= 1) {
+        r += __shfl_xor_sync(0xffffffffu, r, o);
+        jx += __shfl_xor_sync(0xffffffffu, jx, o);
+        jy += __shfl_xor_sync(0xffffffffu, jy, o);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[0][warp] = r;
+        red[1][warp] = jx;
+        red[2][warp] = jy;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double t = 0.0;
+        for (int w = 0; w < kStepThreads / 32; ++w) t += red[threadIdx.x][w];
+        partials[blockIdx.x * 3 + threadIdx.x] = t;
+    }
+}
+
+__global__ void sum3_kernel(const double* partials, int nblocks, double* out) {
+    const int k = threadIdx.x;
+    if (k >= 3) return;
+    double t = 0.0;
+    for (int b = 0; b < nblocks; ++b) t += partials[b * 3 + k];
+    out[k] = t;
+}
+
+// ---------------------------------------------------------------------------
+// State I/O: host layout f[i][y][x] (pre-collision) <-> device buffer holding
+// f*_i(x) = f_i(x + v_i).
+// ---------------------------------------------------------------------------
+
+template <class T>
+__global__ void scatter_state_kernel(const double* in, Geometry geo, T* buf) {
+    const long long N = (long long)geo.Lx * geo.Ly;
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
+         n += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(n / geo.Lx), x = (int)(n - (long long)y * geo.Lx);
+        for (int i = 0; i < 9; ++i) {
+            const int xd = (x + cvx(i) + geo.Lx) % geo.Lx, yd = (y + cvy(i) + geo.Ly) % geo.Ly;
+            buf[i * geo.plane + yd * geo.pitch + xd] = (T)in[i * N + n];
+        }
+    }
+}
+
+template <class T>
+__global__ void gather_state_kernel(const T* buf, Geometry geo, double* out) {
+    const long long N = (long long)geo.Lx * geo.Ly;
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
+         n += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(n / geo.Lx), x = (int)(n - (long long)y * geo.Lx);
+        for (int i = 0; i < 9; ++i) {
+            const int xs = (x - cvx(i) + geo.Lx) % geo.Lx, ys = (y - cvy(i) + geo.Ly) % geo.Ly;
+            out[i * N + n] = (double)buf[i * geo.plane + ys * geo.pitch + xs];
+        }
+    }
+}
+
+template <class T>
+__global__ void fill_kernel(T* buf, Geometry geo, Vec9 v) {
+    const long long total = 9 * geo.plane;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < total;
+         k += (long long)gridDim.x * blockDim.x)
+        buf[k] = (T)v.v[k / geo.plane];
+}
+
+// ---------------------------------------------------------------------------
+// Test hooks
+// ---------------------------------------------------------------------------
+
+template <class T>
+__global__ void noise_draws_kernel(uint64_t seed, uint32_t replica, uint32_t step,
+                                   const uint32_t* nodes, int n, uint32_t* fields,
+                                   double* normals) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    uint32_t f[6];
+    draw_fields(node_draw(seed, replica, nodes[k], step), f);
+    T z[6];
+    box_muller(f, z);
+    for (int q = 0; q < 6; ++q) {
+        fields[k * 6 + q] = f[q];
+        normals[k * 6 + q] = (double)z[q];
+    }
+}
+
+template <class T, int BASIS>
+__global__ void collide_nodes_kernel(const double* g, const uint32_t* ids, uint32_t step,
+                                     int n, CollideConst<T> cc, double* fs, int* status) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    T gg[9], ff[9];
+    for (int i = 0; i < 9; ++i) gg[i] = (T)g[k * 9 + i];
+    const int st = collide<T, BASIS>(gg, ids[k], step, cc, ff);
+    for (int i = 0; i < 9; ++i) fs[k * 9 + i] = (double)ff[i];
+    status[k] = st;
+}
+
+}  // namespace flb
+
+// ===========================================================================
+// Handle and C ABI
+// ===========================================================================
+
+using namespace flb;
+
+struct flb_lattice_s {
+    flb_params p;
+    int elem;            // bytes per population value
+    Geometry geo;
+    char* ws;
+    bool own_ws;
+    size_t ws_bytes;
+    void* buf[2];
+    int cur;             // buf[cur] holds f*(t-1), the source of the next pull
+    double* partials;
+    int nblocks;         // grid of the step kernel
+    double* acc;         // kSums running sums
+    double* small;       // basis (81) + finalize output (171) + conservation (3)
+    DevError* err;
+    cudaStream_t stream;
+    int64_t t, warmup, every, nsamp;
+    int sticky;
+    double ref[9];
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+int valid_params(const flb_params* p) {
+    if (!p) return 0;
+    if (p->Lx < 1 || p->Ly < 1) return 0;
+    if ((long long)p->Lx * p->Ly >= (1LL << 31)) return 0;
+    if (!(p->rho0 > 0) || !std::isfinite(p->rho0)) return 0;
+    if (!(p->kT >= 0) || !std::isfinite(p->kT)) return 0;
+    if (!std::isfinite(p->ux0) || !std::isfinite(p->uy0)) return 0;
+    for (int a = 3; a < 9; ++a)
+        if (!(p->omega[a] > 0 && p->omega[a] < 2)) return 0;
+    if (p->basis != FLB_BASIS_STANDARD && p->basis != FLB_BASIS_LOCAL) return 0;
+    if (p->precision != FLB_FP64 && p->precision != FLB_FP32) return 0;
+    if (p->reserved != 0) return 0;
+    // the mean velocity must leave every f_i^0(1,u0) > 0 (Fig. 11)
+    const double usq = p->ux0 * p->ux0 + p->uy0 * p->uy0;
+    for (int i = 0; i < 9; ++i) {
+        const double uv = p->ux0 * cvx(i) + p->uy0 * cvy(i);
+        if (!(1.0 + 3.0 * uv + 4.5 * uv * uv - 1.5 * usq > 0.0)) return 0;
+    }
+    return 1;
+}
+
+int elem_size(int prec) { return prec == FLB_FP64 ? 8 : 4; }
+
+Geometry make_geometry(const flb_params* p) {
+    Geometry g;
+    g.Lx = p->Lx;
+    g.Ly = p->Ly;
+    g.pitch = (long long)((p->Lx + 31) / 32 * 32);   // rows start on 128-byte boundaries
+    g.plane = g.pitch * p->Ly;
+    return g;
+}
+
+int device_sms() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    return sms;
+}
+
+int step_grid(const Geometry& g, int sms) {
+    const long long N = (long long)g.Lx * g.Ly;
+    long long blocks = (N + kStepThreads - 1) / kStepThreads;
+    const long long cap = (long long)(sms > 0 ? sms : 1) * 8;
+    if (blocks > cap) blocks = cap;
+    return (int)(blocks < 1 ? 1 : blocks);
+}
+
+struct Layout {
+    size_t buf_bytes, partial_off, acc_off, small_off, err_off, total;
+    int nblocks;
+};
+
+Layout layout(const flb_params* p, int sms) {
+    Layout L;
+    const Geometry g = make_geometry(p);
+    L.nblocks = step_grid(g, sms);
+    L.buf_bytes = align_up((size_t)(9 * g.plane) * elem_size(p->precision));
+    size_t off = 2 * L.buf_bytes;
+    L.partial_off = off;
+    off += align_up(sizeof(double) * (size_t)L.nblocks * kSums);
+    L.acc_off = off;
+    off += align_up(sizeof(double) * kSums);
+    L.small_off = off;
+    off += align_up(sizeof(double) * (81 + 171 + 3 + 3 * (size_t)L.nblocks));
+    L.err_off = off;
+    off += align_up(sizeof(DevError));
+    L.total = off;
+    return L;
+}
+
+void feq_host(double rho, double ux, double uy, double f[9]) {
+    const double usq = ux * ux + uy * uy;
+    for (int i = 0; i < 9; ++i) {
+        const double uv = ux * cvx(i) + uy * cvy(i);
+        const double wi = i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+        f[i] = rho * wi * (1.0 + 3.0 * uv + 4.5 * uv * uv - 1.5 * usq);
+    }
+}
+
+template <class T>
+CollideConst<T> collide_const(const flb_params* p) {
+    CollideConst<T> cc;
+    for (int a = 0; a < 6; ++a) {
+        const double om = p->omega[3 + a];
+        cc.omega[a] = (T)om;
+        const double v = p->kT * om * (2.0 - om);
+        cc.amp[a] = (T)(v > 0 ? std::sqrt(v) : 0.0);
+    }
+    cc.seed = p->seed;
+    cc.replica = p->replica;
+    return cc;
+}
+
+int cuda_rc(cudaError_t e) { return e == cudaSuccess ? FLB_OK : FLB_ERR_CUDA; }
+
+int map_status(int code) {
+    if (code == kStatusInvalidVelocity) return FLB_ERR_INVALID_VELOCITY;
+    if (code == kStatusNonfinite) return FLB_ERR_NONFINITE;
+    return code ? FLB_ERR_STATE : FLB_OK;
+}
+
+int grid_for(long long n) {
+    long long b = (n + 255) / 256;
+    if (b > 4096) b = 4096;
+    return (int)(b < 1 ? 1 : b);
+}
+
+template <class T, int BASIS, bool SAMPLE>
+cudaError_t launch_step_t(flb_lattice h) {
+    StepArgs<T> a;
+    a.src = (const T*)h->buf[h->cur];
+    a.dst = (T*)h->buf[h->cur ^ 1];
+    a.geo = h->geo;
+    a.step = (uint32_t)h->t;
+    a.partials = h->partials;
+    a.err = h->err;
+    for (int i = 0; i < 9; ++i) a.ref[i] = (T)h->ref[i];
+    step_kernel<T, BASIS, SAMPLE><<<h->nblocks, kStepThreads, 0, h->stream>>>(
+        a, collide_const<T>(&h->p));
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_step_p(flb_lattice h, bool sample) {
+    if (h->p.basis == FLB_BASIS_STANDARD)
+        return sample ? launch_step_t<T, 0, true>(h) : launch_step_t<T, 0, false>(h);
+    return sample ? launch_step_t<T, 1, true>(h) : launch_step_t<T, 1, false>(h);
+}
+
+cudaError_t launch_step(flb_lattice h, bool sample) {
+    if (h->p.precision == FLB_FP64) return launch_step_p<double>(h, sample);
+    return launch_step_p<float>(h, sample);
+}
+
+int check_device_error(flb_lattice h) {
+    DevError e;
+    cudaError_t ce = cudaMemcpyAsync(&e, h->err, sizeof(e), cudaMemcpyDeviceToHost, h->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
+    if (ce != cudaSuccess) return FLB_ERR_CUDA;
+    if (e.code != 0 && h->sticky == 0) h->sticky = map_status(e.code);
+    return h->sticky;
+}
+
+}  // namespace
+
+extern "C" {
+
+int flb_version(void) { return 100; }
+
+const char* flb_error_string(int code) {
+    switch (code) {
+        case FLB_OK: return "ok";
+        case FLB_ERR_ARG: return "invalid argument";
+        case FLB_ERR_OOM: return "out of device memory or workspace too small";
+        case FLB_ERR_INVALID_VELOCITY: return "a node velocity left the region where all f_i^0(1,u) > 0";
+        case FLB_ERR_NONFINITE: return "non-finite or non-positive density at a node";
+        case FLB_ERR_TIMEOUT: return "a bounded device wait timed out";
+        case FLB_ERR_CUDA: return "CUDA runtime error";
+        case FLB_ERR_STATE: return "call not valid in the current state";
+        default: return "unknown error";
+    }
+}
+
+size_t flb_workspace_bytes(const flb_params* p) {
+    if (!valid_params(p)) return 0;
+    return layout(p, device_sms()).total;
+}
+
+int flb_create(const flb_params* p, void* dev_workspace, size_t workspace_bytes, void* stream,
+               flb_lattice* out) {
+    if (!out) return FLB_ERR_ARG;
+    *out = nullptr;
+    if (!valid_params(p)) return FLB_ERR_ARG;
+    const int sms = device_sms();
+    if (sms <= 0) return FLB_ERR_CUDA;
+    const Layout L = layout(p, sms);
+    flb_lattice h = new (std::nothrow) flb_lattice_s();
+    if (!h) return FLB_ERR_OOM;
+    h->p = *p;
+    h->elem = elem_size(p->precision);
+    h->geo = make_geometry(p);
+    h->stream = (cudaStream_t)stream;
+    if (dev_workspace) {
+        if (workspace_bytes < L.total || ((uintptr_t)dev_workspace % kAlign) != 0) {
+            delete h;
+            return FLB_ERR_OOM;
+        }
+        h->ws = (char*)dev_workspace;
+        h->own_ws = false;
+    } else {
+        void* ptr = nullptr;
+        if (cudaMalloc(&ptr, L.total) != cudaSuccess) {
+            cudaGetLastError();
+            delete h;
+            return FLB_ERR_OOM;
+        }
+        h->ws = (char*)ptr;
+        h->own_ws = true;
+    }
+    h->ws_bytes = L.total;
+    h->buf[0] = h->ws;
+    h->buf[1] = h->ws + L.buf_bytes;
+    h->partials = (double*)(h->ws + L.partial_off);
+    h->acc = (double*)(h->ws + L.acc_off);
+    h->small = (double*)(h->ws + L.small_off);
+    h->err = (DevError*)(h->ws + L.err_off);
+    h->nblocks = L.nblocks;
+    h->cur = 0;
+    feq_host(p->rho0, p->ux0, p->uy0, h->ref);
+
+    cudaError_t ce = cudaMemsetAsync(h->ws + L.partial_off, 0, L.total - L.partial_off, h->stream);
+    Vec9 v;
+    for (int i = 0; i < 9; ++i) v.v[i] = h->ref[i];
+    if (ce == cudaSuccess) {
+        if (p->precision == FLB_FP64)
+            fill_kernel<double><<<grid_for(9 * h->geo.plane), 256, 0, h->stream>>>(
+                (double*)h->buf[0], h->geo, v);
+        else
+            fill_kernel<float><<<grid_for(9 * h->geo.plane), 256, 0, h->stream>>>(
+                (float*)h->buf[0], h->geo, v);
+        ce = cudaGetLastError();
+    }
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
+    if (ce != cudaSuccess) {
+        if (h->own_ws) cudaFree(h->ws);
+        delete h;
+        return FLB_ERR_CUDA;
+    }
+    *out = h;
+    return FLB_OK;
+}
+
+int flb_destroy(flb_lattice h) {
+    if (!h) return FLB_OK;
+    cudaError_t ce = cudaStreamSynchronize(h->stream);
+    if (h->own_ws) {
+        cudaError_t fe = cudaFree(h->ws);
+        if (ce == cudaSuccess) ce = fe;
+    }
+    delete h;
+    return cuda_rc(ce);
+}
+
+int flb_reset_statistics(flb_lattice h) {
+    if (!h) return FLB_ERR_ARG;
+    h->nsamp = 0;
+    return cuda_rc(cudaMemsetAsync(h->acc, 0, sizeof(double) * kSums, h->stream));
+}
+
+int flb_set_sampling(flb_lattice h, int64_t warmup, int64_t every) {
+    if (!h || warmup < 0 || every < 0) return FLB_ERR_ARG;
+    h->warmup = warmup;
+    h->every = every;
+    return flb_reset_statistics(h);
+}
+
+int flb_step(flb_lattice h, int64_t n) {
+    if (!h || n < 0) return FLB_ERR_ARG;
+    if (h->sticky) return h->sticky;
+    const long long N = (long long)h->p.Lx * h->p.Ly;
+    for (int64_t s = 0; s < n; ++s) {
+        const bool sample =
+            h->every > 0 && h->t >= h->warmup && ((h->t - h->warmup) % h->every) == 0;
+        cudaError_t ce = launch_step(h, sample);
+        if (ce == cudaSuccess && sample) {
+            accumulate_partials_kernel<<<1, 64, 0, h->stream>>>(h->partials, h->nblocks, h->acc);
+            ce = cudaGetLastError();
+            h->nsamp += N;
+        }
+        if (ce != cudaSuccess) return FLB_ERR_CUDA;
+        h->t += 1;
+        h->cur ^= 1;
+    }
+    return FLB_OK;
+}
+
+int flb_sync(flb_lattice h) {
+    if (!h) return FLB_ERR_ARG;
+    return check_device_error(h);
+}
+
+int flb_time(flb_lattice h, int64_t* t) {
+    if (!h || !t) return FLB_ERR_ARG;
+    *t = h->t;
+    return FLB_OK;
+}
+
+int flb_error_location(flb_lattice h, int64_t* node, int64_t* step) {
+    if (!h) return FLB_ERR_ARG;
+    DevError e;
+    cudaError_t ce = cudaMemcpyAsync(&e, h->err, sizeof(e), cudaMemcpyDeviceToHost, h->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
+    if (ce != cudaSuccess) return FLB_ERR_CUDA;
+    if (node) *node = e.code ? e.node : -1;
+    if (step) *step = e.code ? e.step : -1;
+    return FLB_OK;
+}
+
+int flb_reset_error(flb_lattice h) {
+    if (!h) return FLB_ERR_ARG;
+    h->sticky = 0;
+    cudaError_t ce = cudaMemsetAsync(h->err, 0, sizeof(DevError), h->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
+    return cuda_rc(ce);
+}
+
+int flb_raw_sums(flb_lattice h, double* S1, double* S2, int64_t* n_samples) {
+    if (!h) return FLB_ERR_ARG;
+    double acc[kSums];
+    cudaError_t ce = cudaMemcpyAsync(acc, h->acc, sizeof(acc), cudaMemcpyDeviceToHost, h->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
+    if (ce != cudaSuccess) return FLB_ERR_CUDA;
+    const int rc = check_device_error(h);
+    if (rc) return rc;
+    if (S1)
+        for (int i = 0; i < 9; ++i) S1[i] = acc[i];
+    if (S2) {
+        int k = 9;
+        for (int i = 0; i < 9; ++i)
+            for (int j = i; j < 9; ++j, ++k) S2[i * 9 + j] = S2[j * 9 + i] = acc[k];
+    }
+    if (n_samples) *n_samples = h->nsamp;
+    return FLB_OK;
+}
+
+int flb_correlations(flb_lattice h, int32_t measure_basis, double* Cff, double* CMM,
+                     double* mean_dev, int64_t* n_samples) {
+    if (!h) return FLB_ERR_ARG;
+    if (measure_basis != FLB_BASIS_STANDARD && measure_basis != FLB_BASIS_LOCAL)
+        return FLB_ERR_ARG;
+    int rc = check_device_error(h);
+    if (rc) return rc;
+    if (n_samples) *n_samples = h->nsamp;
+    if (h->nsamp <= 0) return FLB_ERR_STATE;
+    double* basis = h->small;
+    double* res = h->small + 81;
+    measure_basis_kernel<<<1, 32, 0, h->stream>>>(measure_basis, h->p.ux0, h->p.uy0, basis);
+    finalize_kernel<<<1, 96, 0, h->stream>>>(h->acc, h->nsamp, basis, res);
+    double host[171];
+    cudaError_t ce = cudaGetLastError();
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(host, res, sizeof(host), cudaMemcpyDeviceToHost, h->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
+    if (ce != cudaSuccess) return FLB_ERR_CUDA;
+    if (Cff) std::memcpy(Cff, host, 81 * sizeof(double));
+    if (CMM) std::memcpy(CMM, host + 81, 81 * sizeof(double));
+    if (mean_dev) std::memcpy(mean_dev, host + 162, 9 * sizeof(double));
+    return FLB_OK;
+}
+
+int flb_conservation(flb_lattice h, double sums[3]) {
+    if (!h || !sums) return FLB_ERR_ARG;
+    double* part = h->small + 81 + 171 + 3;
+    double* res = h->small + 81 + 171;
+    if (h->p.precision == FLB_FP64)
+        conservation_kernel<double><<<h->nblocks, kStepThreads, 0, h->stream>>>(
+            (const double*)h->buf[h->cur], h->geo, part);
+    else
+        conservation_kernel<float><<<h->nblocks, kStepThreads, 0, h->stream>>>(
+            (const float*)h->buf[h->cur], h->geo, part);
+    sum3_kernel<<<1, 32, 0, h->stream>>>(part, h->nblocks, res);
+    cudaError_t ce = cudaGetLastError();
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(sums, res, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
+    if (ce != cudaSuccess) return FLB_ERR_CUDA;
+    return check_device_error(h);
+}
+
+int flb_get_populations(flb_lattice h, double* host_out) {
+    if (!h || !host_out) return FLB_ERR_ARG;
+    const size_t n = (size_t)9 * h->p.Lx * h->p.Ly;
+    double* tmp = nullptr;
+    if (cudaMalloc(&tmp, n * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return FLB_ERR_OOM;
+    }
+    const int grid = grid_for((long long)h->p.Lx * h->p.Ly);
+    if (h->p.precision == FLB_FP64)
+        gather_state_kernel<double><<<grid, 256, 0, h->stream>>>((const double*)h->buf[h->cur],
+                                                                 h->geo, tmp);
+    else
+        gather_state_kernel<float><<<grid, 256, 0, h->stream>>>((const float*)h->buf[h->cur],
+                                                                h->geo, tmp);
+    cudaError_t ce = cudaGetLastError();
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(host_out, tmp, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
+    cudaFree(tmp);
+    if (ce != cudaSuccess) return FLB_ERR_CUDA;
+    return check_device_error(h);
+}
+
+int flb_set_populations(flb_lattice h, const double* host_in) {
+    if (!h || !host_in) return FLB_ERR_ARG;
+    const size_t n = (size_t)9 * h->p.Lx * h->p.Ly;
+    double* tmp = nullptr;
+    if (cudaMalloc(&tmp, n * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return FLB_ERR_OOM;
+    }
+    cudaError_t ce = cudaMemcpyAsync(tmp, host_in, n * sizeof(double), cudaMemcpyHostToDevice,
+                                     h->stream);
+    const int grid = grid_for((long long)h->p.Lx * h->p.Ly);
+    if (ce == cudaSuccess) {
+        if (h->p.precision == FLB_FP64)
+            scatter_state_kernel<double><<<grid, 256, 0, h->stream>>>(tmp, h->geo,
+                                                                      (double*)h->buf[h->cur]);
+        else
+            scatter_state_kernel<float><<<grid, 256, 0, h->stream>>>(tmp, h->geo,
+                                                                     (float*)h->buf[h->cur]);
+        ce = cudaGetLastError();
+    }
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(h->err, 0, sizeof(DevError), h->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
+    cudaFree(tmp);
+    h->sticky = 0;
+    return cuda_rc(ce);
+}
+
+int flb_run_host(const flb_params* p, const double* f_in, int64_t nsteps, int64_t warmup,
+                 int64_t every, double* f_out, double* S1, double* S2, int64_t* n_samples) {
+    if (!p || nsteps < 0) return FLB_ERR_ARG;
+    flb_lattice h = nullptr;
+    int rc = flb_create(p, nullptr, 0, nullptr, &h);
+    if (rc) return rc;
+    if (f_in) rc = flb_set_populations(h, f_in);
+    if (!rc) rc = flb_set_sampling(h, warmup, every);
+    if (!rc) rc = flb_step(h, nsteps);
+    if (!rc) rc = flb_sync(h);
+    if (!rc && f_out) rc = flb_get_populations(h, f_out);
+    if (!rc && (S1 || S2 || n_samples)) rc = flb_raw_sums(h, S1, S2, n_samples);
+    const int drc = flb_destroy(h);
+    return rc ? rc : drc;
+}
+
+int flb_noise_draws(uint64_t seed, uint32_t replica, uint32_t step, const uint32_t* nodes,
+                    int32_t n, int32_t precision, uint32_t* fields, double* normals) {
+    if (n < 0 || (n > 0 && (!nodes || !fields || !normals))) return FLB_ERR_ARG;
+    if (precision != FLB_FP64 && precision != FLB_FP32) return FLB_ERR_ARG;
+    if (n == 0) return FLB_OK;
+    uint32_t *d_nodes = nullptr, *d_fields = nullptr;
+    double* d_normals = nullptr;
+    cudaError_t ce = cudaMalloc(&d_nodes, n * sizeof(uint32_t));
+    if (ce == cudaSuccess) ce = cudaMalloc(&d_fields, 6 * (size_t)n * sizeof(uint32_t));
+    if (ce == cudaSuccess) ce = cudaMalloc(&d_normals, 6 * (size_t)n * sizeof(double));
+    if (ce == cudaSuccess)
+        ce = cudaMemcpy(d_nodes, nodes, n * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) {
+        const int grid = (n + 127) / 128;
+        if (precision == FLB_FP64)
+            noise_draws_kernel<double><<<grid, 128>>>(seed, replica, step, d_nodes, n, d_fields,
+                                                      d_normals);
+        else
+            noise_draws_kernel<float><<<grid, 128>>>(seed, replica, step, d_nodes, n, d_fields,
+                                                     d_normals);
+        ce = cudaGetLastError();
+    }
+    if (ce == cudaSuccess)
+        ce = cudaMemcpy(fields, d_fields, 6 * (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToHost);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpy(normals, d_normals, 6 * (size_t)n * sizeof(double), cudaMemcpyDeviceToHost);
+    cudaFree(d_nodes);
+    cudaFree(d_fields);
+    cudaFree(d_normals);
+    return cuda_rc(ce);
+}
+
+int flb_collide_nodes(const flb_params* p, const double* g, const uint32_t* node_ids,
+                      uint32_t step, int32_t n, double* fstar, int32_t* status) {
+    if (!p || n < 0 || (n > 0 && (!g || !node_ids || !fstar))) return FLB_ERR_ARG;
+    flb_params q = *p;
+    q.Lx = q.Ly = 1;
+    if (!valid_params(&q)) return FLB_ERR_ARG;
+    if (n == 0) return FLB_OK;
+    double *d_g = nullptr, *d_f = nullptr;
+    uint32_t* d_ids = nullptr;
+    int* d_st = nullptr;
+    cudaError_t ce = cudaMalloc(&d_g, 9 * (size_t)n * sizeof(double));
+    if (ce == cudaSuccess) ce = cudaMalloc(&d_f, 9 * (size_t)n * sizeof(double));
+    if (ce == cudaSuccess) ce = cudaMalloc(&d_ids, (size_t)n * sizeof(uint32_t));
+    if (ce == cudaSuccess) ce = cudaMalloc(&d_st, (size_t)n * sizeof(int));
+    if (ce == cudaSuccess)
+        ce = cudaMemcpy(d_g, g, 9 * (size_t)n * sizeof(double), cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpy(d_ids, node_ids, (size_t)n * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) {
+        const int grid = (n + 127) / 128;
+        if (p->precision == FLB_FP64) {
+            if (p->basis == FLB_BASIS_STANDARD)
+                collide_nodes_kernel<double, 0><<<grid, 128>>>(d_g, d_ids, step, n,
+                                                               collide_const<double>(p), d_f, d_st);
+            else
+                collide_nodes_kernel<double, 1><<<grid, 128>>>(d_g, d_ids, step, n,
+                                                               collide_const<double>(p), d_f, d_st);
+        } else {
+            if (p->basis == FLB_BASIS_STANDARD)
+                collide_nodes_kernel<float, 0><<<grid, 128>>>(d_g, d_ids, step, n,
+                                                              collide_const<float>(p), d_f, d_st);
+            else
+                collide_nodes_kernel<float, 1><<<grid, 128>>>(d_g, d_ids, step, n,
+                                                              collide_const<float>(p), d_f, d_st);
+        }
+        ce = cudaGetLastError();
+    }
+    if (ce == cudaSuccess)
+        ce = cudaMemcpy(fstar, d_f, 9 * (size_t)n * sizeof(double), cudaMemcpyDeviceToHost);
+    int* st = nullptr;
+    if (ce == cudaSuccess && status) {
+        st = new (std::nothrow) int[n];
+        if (st) {
+            ce = cudaMemcpy(st, d_st, (size_t)n * sizeof(int), cudaMemcpyDeviceToHost);
+            for (int k = 0; k < n && ce == cudaSuccess; ++k) status[k] = map_status(st[k]);
+            delete[] st;
+        }
+    }
+    cudaFree(d_g);
+    cudaFree(d_f);
+    cudaFree(d_ids);
+    cudaFree(d_st);
+    return cuda_rc(ce);
+}
+
+}  // extern "C"

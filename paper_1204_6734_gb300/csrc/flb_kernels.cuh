@@ -1,0 +1,135 @@
+// flb_kernels.cuh -- lattice kernels: fused pull-stream + collide (+ sampling),
+// correlation reduction and finalisation, conservation sums, state I/O.
+//
+// Storage: 9 SoA planes per buffer, plane i row y at base + i*plane + y*pitch.
+// A buffer holds the post-collision populations f*_i(x, t-1); the step kernel
+// pulls g_i(x) = f*_i(x - v_i) (periodic), which is the pre-collision state
+// f_i(x, t) of Eq. LBE1, collides it and writes f*_i(x, t) to the other buffer.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "flb_device.cuh"
+
+namespace flb {
+
+constexpr int kSums = 54;          // 9 first moments + 45 unique second moments
+constexpr int kStepThreads = 256;
+
+struct DevError {
+    int code;        // 0 = none, else kStatus*
+    int pad;
+    long long node;
+    long long step;
+};
+
+struct Vec9 {
+    double v[9];
+};
+
+struct Geometry {
+    int Lx, Ly;
+    long long pitch;   // elements per row
+    long long plane;   // elements per plane
+};
+
+template <class T>
+struct StepArgs {
+    const T* src;
+    T* dst;
+    Geometry geo;
+    uint32_t step;
+    double* partials;   // [gridDim.x][kSums] when sampling
+    DevError* err;
+    T ref[9];           // c = f^0(rho0, u0), subtracted before sampling
+};
+
+__device__ __forceinline__ void record_error(DevError* err, int code, long long node,
+                                             long long step) {
+    if (atomicCAS(&err->code, 0, code) == 0) {
+        err->node = node;
+        err->step = step;
+    }
+}
+
+// Accumulation type of the per-thread correlation sums: FP32 for the FP32
+// path (a thread sums a few hundred nodes at most), FP64 otherwise; per-block
+// partials and everything after them are FP64.
+template <class T>
+struct AccType { using type = T; };
+
+template <class A>
+__device__ __forceinline__ void block_reduce_sums(A (&s)[kSums], double* out) {
+    __shared__ double red[kStepThreads / 32][kSums];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < kSums; ++k) {
+        A v = s[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp][k] = (double)v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kSums) {
+        double t = 0.0;
+        for (int w = 0; w < kStepThreads / 32; ++w) t += red[w][threadIdx.x];
+        out[threadIdx.x] = t;
+    }
+}
+
+// Fused step: pull-stream, (sample), collide with noise, store.
+template <class T, int BASIS, bool SAMPLE>
+__global__ void __launch_bounds__(kStepThreads)
+step_kernel(StepArgs<T> a, CollideConst<T> cc) {
+    using A = typename AccType<T>::type;
+    const int Lx = a.geo.Lx, Ly = a.geo.Ly;
+    const long long N = (long long)Lx * Ly;
+    A s[kSums];
+    if (SAMPLE) {
+#pragma unroll
+        for (int k = 0; k < kSums; ++k) s[k] = A(0);
+    }
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
+         n += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(n / Lx);
+        const int x = (int)(n - (long long)y * Lx);
+        const int xm = x == 0 ? Lx - 1 : x - 1, xp = x == Lx - 1 ? 0 : x + 1;
+        const int ym = y == 0 ? Ly - 1 : y - 1, yp = y == Ly - 1 ? 0 : y + 1;
+        T g[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int xs = cvx(i) == 1 ? xm : (cvx(i) == -1 ? xp : x);
+            const int ys = cvy(i) == 1 ? ym : (cvy(i) == -1 ? yp : y);
+            g[i] = a.src[i * a.geo.plane + ys * a.geo.pitch + xs];
+        }
+        if (SAMPLE) {
+            A d[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) d[i] = A(g[i]) - A(a.ref[i]);
+            int k = 9;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                s[i] += d[i];
+#pragma unroll
+                for (int j = i; j < 9; ++j) s[k++] += d[i] * d[j];
+            }
+        }
+        T f[9];
+        const int st = collide<T, BASIS>(g, (uint32_t)n, a.step, cc, f);
+        if (st != kStatusOk) record_error(a.err, st, n, a.step);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) a.dst[i * a.geo.plane + y * a.geo.pitch + x] = f[i];
+    }
+    if (SAMPLE) block_reduce_sums<A>(s, a.partials + (long long)blockIdx.x * kSums);
+}
+
+// Sum the per-block partials in a fixed order into the running FP64 sums.
+__global__ void accumulate_partials_kernel(const double* partials, int nblocks, double* acc);
+
+// C = S2/n - m m^T, m = S1/n, and CM = B C B^T for the measurement basis B.
+__global__ void finalize_kernel(const double* acc, long long nsamp, const double* basis,
+                                double* out /* Cff[81], CMM[81], mean[9] */);
+
+}  // namespace flb

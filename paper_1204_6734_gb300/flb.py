@@ -1,0 +1,331 @@
+"""Python binding of the C ABI in include/flb.h (ctypes; argument marshalling only).
+
+Every function named ``flb_*`` here calls the C entry point of the same name in
+``_build/libflb.so``; every step of the method runs in that library's CUDA
+kernels. There is no fallback: if the library cannot be loaded the import of
+this module's functions raises.
+
+PyTorch is optional and only used as plumbing: a ``torch.cuda.Stream`` (or its
+raw handle) may be passed as the stream, and a CUDA ``torch.Tensor`` as the
+device workspace.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+OK = 0
+ERR_ARG, ERR_OOM, ERR_INVALID_VELOCITY, ERR_NONFINITE, ERR_TIMEOUT, ERR_CUDA, ERR_STATE = (
+    -1, -2, -3, -4, -5, -6, -7)
+BASIS = {"standard": 0, "local": 1}
+PRECISION = {"fp64": 0, "fp32": 1, "fp16dev": 2}
+
+
+class FlbError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        msg = flb_error_string(code) if _lib is not None else str(code)
+        super().__init__(f"{what}: flb error {code} ({msg})" if what else f"flb error {code} ({msg})")
+        self.code = code
+
+
+class flb_params(C.Structure):
+    _fields_ = [("Lx", C.c_int32), ("Ly", C.c_int32), ("rho0", C.c_double),
+                ("ux0", C.c_double), ("uy0", C.c_double), ("kT", C.c_double),
+                ("omega", C.c_double * 9), ("basis", C.c_int32), ("precision", C.c_int32),
+                ("seed", C.c_uint64), ("replica", C.c_uint32), ("reserved", C.c_uint32)]
+
+
+_lib = None
+_dp = C.POINTER(C.c_double)
+_i64p = C.POINTER(C.c_int64)
+_u32p = C.POINTER(C.c_uint32)
+_i32p = C.POINTER(C.c_int32)
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libflb.so (building it first if it is missing or stale and nvcc is
+    available). Raises if it cannot be loaded."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing and (not os.path.exists(path) or _build.stale()):
+        _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path}")
+    L = C.CDLL(path)
+    P = C.POINTER(flb_params)
+    h = C.c_void_p
+    sig = {
+        "flb_workspace_bytes": (C.c_size_t, [P]),
+        "flb_create": (C.c_int, [P, C.c_void_p, C.c_size_t, C.c_void_p, C.POINTER(h)]),
+        "flb_destroy": (C.c_int, [h]),
+        "flb_set_sampling": (C.c_int, [h, C.c_int64, C.c_int64]),
+        "flb_reset_statistics": (C.c_int, [h]),
+        "flb_step": (C.c_int, [h, C.c_int64]),
+        "flb_sync": (C.c_int, [h]),
+        "flb_time": (C.c_int, [h, _i64p]),
+        "flb_error_location": (C.c_int, [h, _i64p, _i64p]),
+        "flb_reset_error": (C.c_int, [h]),
+        "flb_correlations": (C.c_int, [h, C.c_int32, _dp, _dp, _dp, _i64p]),
+        "flb_raw_sums": (C.c_int, [h, _dp, _dp, _i64p]),
+        "flb_conservation": (C.c_int, [h, _dp]),
+        "flb_get_populations": (C.c_int, [h, _dp]),
+        "flb_set_populations": (C.c_int, [h, _dp]),
+        "flb_run_host": (C.c_int, [P, _dp, C.c_int64, C.c_int64, C.c_int64, _dp, _dp, _dp, _i64p]),
+        "flb_noise_draws": (C.c_int, [C.c_uint64, C.c_uint32, C.c_uint32, _u32p, C.c_int32,
+                                      C.c_int32, _u32p, _dp]),
+        "flb_collide_nodes": (C.c_int, [P, _dp, _u32p, C.c_uint32, C.c_int32, _dp, _i32p]),
+        "flb_error_string": (C.c_char_p, [C.c_int]),
+        "flb_version": (C.c_int, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def exported_symbols():
+    """Names of the C entry points this binding expects."""
+    return ["flb_workspace_bytes", "flb_create", "flb_destroy", "flb_set_sampling",
+            "flb_reset_statistics", "flb_step", "flb_sync", "flb_time", "flb_error_location",
+            "flb_reset_error", "flb_correlations", "flb_raw_sums", "flb_conservation",
+            "flb_get_populations", "flb_set_populations", "flb_run_host", "flb_noise_draws",
+            "flb_collide_nodes", "flb_error_string", "flb_version"]
+
+
+def _check(rc: int, what: str):
+    if rc != OK:
+        raise FlbError(rc, what)
+
+
+def make_params(p) -> flb_params:
+    """flb_params from any object with Lx, Ly, rho0, ux0, uy0, kT, omega, basis,
+    precision, seed and (optionally) replica attributes."""
+    s = flb_params()
+    s.Lx, s.Ly = int(p.Lx), int(p.Ly)
+    s.rho0, s.ux0, s.uy0, s.kT = float(p.rho0), float(p.ux0), float(p.uy0), float(p.kT)
+    for a, v in enumerate(p.omega):
+        s.omega[a] = float(v)
+    s.basis = BASIS[p.basis] if isinstance(p.basis, str) else int(p.basis)
+    prec = getattr(p, "precision", "fp32")
+    s.precision = PRECISION[prec] if isinstance(prec, str) else int(prec)
+    s.seed = int(p.seed) & 0xFFFFFFFFFFFFFFFF
+    s.replica = int(getattr(p, "replica", 0))
+    s.reserved = 0
+    return s
+
+
+def _ptr(a, ctype=C.c_double):
+    return None if a is None else a.ctypes.data_as(C.POINTER(ctype))
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(getattr(stream, "cuda_stream"))
+
+
+# ---------------------------------------------------------------------------
+# Same-name wrappers of the C entry points
+# ---------------------------------------------------------------------------
+
+def flb_error_string(code: int) -> str:
+    return load().flb_error_string(code).decode()
+
+
+def flb_version() -> int:
+    return load().flb_version()
+
+
+def flb_workspace_bytes(p) -> int:
+    s = make_params(p)
+    return int(load().flb_workspace_bytes(C.byref(s)))
+
+
+def flb_create(p, workspace=None, stream=None):
+    s = make_params(p)
+    h = C.c_void_p()
+    ws_ptr, ws_bytes = None, 0
+    if workspace is not None:
+        ws_ptr = int(workspace.data_ptr())
+        ws_bytes = int(workspace.numel() * workspace.element_size())
+    _check(load().flb_create(C.byref(s), ws_ptr, ws_bytes, _stream_handle(stream), C.byref(h)),
+           "flb_create")
+    return h
+
+
+def flb_destroy(h) -> None:
+    _check(load().flb_destroy(h), "flb_destroy")
+
+
+def flb_set_sampling(h, warmup: int, every: int) -> None:
+    _check(load().flb_set_sampling(h, int(warmup), int(every)), "flb_set_sampling")
+
+
+def flb_reset_statistics(h) -> None:
+    _check(load().flb_reset_statistics(h), "flb_reset_statistics")
+
+
+def flb_step(h, n: int) -> None:
+    _check(load().flb_step(h, int(n)), "flb_step")
+
+
+def flb_sync(h) -> None:
+    _check(load().flb_sync(h), "flb_sync")
+
+
+def flb_time(h) -> int:
+    t = C.c_int64()
+    _check(load().flb_time(h, C.byref(t)), "flb_time")
+    return t.value
+
+
+def flb_error_location(h):
+    n, s = C.c_int64(), C.c_int64()
+    _check(load().flb_error_location(h, C.byref(n), C.byref(s)), "flb_error_location")
+    return n.value, s.value
+
+
+def flb_reset_error(h) -> None:
+    _check(load().flb_reset_error(h), "flb_reset_error")
+
+
+def flb_correlations(h, measure_basis="local"):
+    Cff, CMM, mean = np.zeros((9, 9)), np.zeros((9, 9)), np.zeros(9)
+    n = C.c_int64()
+    mb = BASIS[measure_basis] if isinstance(measure_basis, str) else int(measure_basis)
+    _check(load().flb_correlations(h, mb, _ptr(Cff), _ptr(CMM), _ptr(mean), C.byref(n)),
+           "flb_correlations")
+    return Cff, CMM, mean, n.value
+
+
+def flb_raw_sums(h):
+    S1, S2 = np.zeros(9), np.zeros((9, 9))
+    n = C.c_int64()
+    _check(load().flb_raw_sums(h, _ptr(S1), _ptr(S2), C.byref(n)), "flb_raw_sums")
+    return S1, S2, n.value
+
+
+def flb_conservation(h):
+    out = np.zeros(3)
+    _check(load().flb_conservation(h, _ptr(out)), "flb_conservation")
+    return out
+
+
+def flb_get_populations(h, Lx: int, Ly: int, out=None):
+    if out is None:
+        out = np.empty((9, Ly, Lx))
+    assert out.dtype == np.float64 and out.flags.c_contiguous and out.size == 9 * Lx * Ly
+    _check(load().flb_get_populations(h, _ptr(out)), "flb_get_populations")
+    return out
+
+
+def flb_set_populations(h, f) -> None:
+    a = np.ascontiguousarray(f, dtype=np.float64)
+    _check(load().flb_set_populations(h, _ptr(a)), "flb_set_populations")
+
+
+def flb_run_host(p, f_in, nsteps, warmup=0, every=0, f_out=None):
+    s = make_params(p)
+    fi = None if f_in is None else np.ascontiguousarray(f_in, dtype=np.float64)
+    S1, S2 = np.zeros(9), np.zeros((9, 9))
+    n = C.c_int64()
+    _check(load().flb_run_host(C.byref(s), _ptr(fi), int(nsteps), int(warmup), int(every),
+                               _ptr(f_out), _ptr(S1), _ptr(S2), C.byref(n)), "flb_run_host")
+    return S1, S2, n.value
+
+
+def flb_noise_draws(seed, replica, step, nodes, precision="fp64"):
+    nd = np.ascontiguousarray(nodes, dtype=np.uint32)
+    n = nd.size
+    fields = np.zeros((n, 6), dtype=np.uint32)
+    normals = np.zeros((n, 6))
+    pr = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    _check(load().flb_noise_draws(int(seed) & 0xFFFFFFFFFFFFFFFF, int(replica), int(step),
+                                  _ptr(nd, C.c_uint32), n, pr, _ptr(fields, C.c_uint32),
+                                  _ptr(normals)), "flb_noise_draws")
+    return fields, normals
+
+
+def flb_collide_nodes(p, g, node_ids, step):
+    s = make_params(p)
+    gg = np.ascontiguousarray(g, dtype=np.float64).reshape(-1, 9)
+    ids = np.ascontiguousarray(node_ids, dtype=np.uint32)
+    n = gg.shape[0]
+    out = np.zeros((n, 9))
+    st = np.zeros(n, dtype=np.int32)
+    _check(load().flb_collide_nodes(C.byref(s), _ptr(gg), _ptr(ids, C.c_uint32), int(step), n,
+                                    _ptr(out), _ptr(st, C.c_int32)), "flb_collide_nodes")
+    return out, st
+
+
+# ---------------------------------------------------------------------------
+# Convenience object
+# ---------------------------------------------------------------------------
+
+class Lattice:
+    """One periodic lattice on the GPU (owns an flb_lattice handle)."""
+
+    def __init__(self, p, workspace=None, stream=None):
+        self.p = p
+        self.h = flb_create(p, workspace, stream)
+
+    def close(self):
+        if self.h is not None:
+            flb_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_sampling(self, warmup, every):
+        flb_set_sampling(self.h, warmup, every)
+
+    def step(self, n):
+        flb_step(self.h, n)
+        return self
+
+    def sync(self):
+        flb_sync(self.h)
+
+    @property
+    def t(self):
+        return flb_time(self.h)
+
+    def populations(self):
+        return flb_get_populations(self.h, self.p.Lx, self.p.Ly)
+
+    def set_populations(self, f):
+        flb_set_populations(self.h, f)
+
+    def correlations(self, measure_basis="local"):
+        return flb_correlations(self.h, measure_basis)
+
+    def raw_sums(self):
+        return flb_raw_sums(self.h)
+
+    def conservation(self):
+        return flb_conservation(self.h)
