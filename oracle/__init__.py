@@ -204,7 +204,7 @@ class Run:
         return covariance(self.S1, self.S2, self.nsamp)
 
     def moment_covariance(self, measure_basis):
-        return moment_covariance(self.covariance(), measure_basis, self.p.ux0, self.p.uy0)
+        return moment_covariance(self.covariance()[0], measure_basis, self.p.ux0, self.p.uy0)
 
 
 def covariance(S1, S2, nsamp):

@@ -250,14 +250,17 @@ static int collide_standard(const orc_params* p, const double g[9], const double
     const double uy = M[2] / (sqrt(3.0) * rho);
     double Meq[9];
     orc_hermite_meq(rho, ux, uy, Meq);
-    double Ms[9];
-    for (int a = 0; a < 3; ++a) Ms[a] = M[a];
+    /* Eq. LBEMRT in its increment form: f* - f = sum_a n^a_i dM^a with
+     * dM^a = -omega_a (M^a - M^{a,0}) + xi^a N^a for a = 3..8 and dM^a = 0 for
+     * the conserved a = 0, 1, 2. */
+    double dM[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (int a = 3; a < 9; ++a)
-        Ms[a] = M[a] - p->omega[a] * (M[a] - Meq[a]) +
+        dM[a] = -p->omega[a] * (M[a] - Meq[a]) +
                 noise_amplitude(p->kT, rho, p->omega[a]) * N[a - 3];
     for (int i = 0; i < 9; ++i) {
-        fstar[i] = 0.0;
-        for (int a = 0; a < 9; ++a) fstar[i] += n[i][a] * Ms[a];
+        double df = 0.0;
+        for (int a = 0; a < 9; ++a) df += n[i][a] * dM[a];
+        fstar[i] = g[i] + df;
     }
     return ORC_OK;
 }
@@ -267,7 +270,7 @@ static int collide_standard(const orc_params* p, const double g[9], const double
  * relaxation towards Mt^{a,0} = rho delta^{a0} (Eq. fnormmeq) plus noise for
  * a = 3..8, and the back transform with n^a_i = mt^a_i f_i^0(rho,u)/rho
  * (the choice made below Eq. fluctf2). The conserved moments a = 0, 1, 2 are
- * passed through unchanged. */
+ * passed through unchanged: their increment is zero. */
 static int collide_local(const orc_params* p, const double g[9], const double N[6],
                          double fstar[9]) {
     double rho = 0.0, jx = 0.0, jy = 0.0;
@@ -289,16 +292,17 @@ static int collide_local(const orc_params* p, const double g[9], const double N[
         Mt[a] = 0.0;
         for (int i = 0; i < 9; ++i) Mt[a] += mt[a * 9 + i] * g[i];
     }
-    double Ms[9];
-    for (int a = 0; a < 3; ++a) Ms[a] = Mt[a];
+    /* increment form of Eq. LBEMRT, as for the Hermite norm */
+    double dM[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (int a = 3; a < 9; ++a) {
         const double Meq = 0.0; /* Eq. fnormmeq */
-        Ms[a] = Mt[a] - p->omega[a] * (Mt[a] - Meq) +
+        dM[a] = -p->omega[a] * (Mt[a] - Meq) +
                 noise_amplitude(p->kT, rho, p->omega[a]) * N[a - 3];
     }
     for (int i = 0; i < 9; ++i) {
-        fstar[i] = 0.0;
-        for (int a = 0; a < 9; ++a) fstar[i] += mt[a * 9 + i] * W[i] * Ms[a];
+        double df = 0.0;
+        for (int a = 0; a < 9; ++a) df += mt[a * 9 + i] * W[i] * dM[a];
+        fstar[i] = g[i] + df;
     }
     return ORC_OK;
 }
