@@ -111,12 +111,11 @@ __global__ void __launch_bounds__(kStepThreads)
 conservation_kernel(const T* src, Geometry geo, double* partials) {
     const long long N = (long long)geo.Lx * geo.Ly;
     double r = 0.0, jx = 0.0, jy = 0.0;
-    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
-         n += (long long)gridDim.x * blockDim.x) {
-        const int y = (int)(n / geo.Lx), x = (int)(n - (long long)y * geo.Lx);
+    // the interior of the buffer is a permutation of the pre-collision state
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < (int)N; n += gridDim.x * blockDim.x) {
+        const int y = n / geo.Lx, x = n - y * geo.Lx;
         for (int i = 0; i < 9; ++i) {
-            const int xs = (x - cvx(i) + geo.Lx) % geo.Lx, ys = (y - cvy(i) + geo.Ly) % geo.Ly;
-            const double v = (double)src[i * geo.plane + ys * geo.pitch + xs];
+            const double v = (double)src[at(geo, i, x, y)];
             r += v;
             jx += v * cvx(i);
             jy += v * cvy(i);
@@ -158,12 +157,13 @@ __global__ void sum3_kernel(const double* partials, int nblocks, double* out) {
 template <class T>
 __global__ void scatter_state_kernel(const double* in, Geometry geo, T* buf) {
     const long long N = (long long)geo.Lx * geo.Ly;
-    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
-         n += (long long)gridDim.x * blockDim.x) {
-        const int y = (int)(n / geo.Lx), x = (int)(n - (long long)y * geo.Lx);
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < (int)N; n += gridDim.x * blockDim.x) {
+        const int y = n / geo.Lx, x = n - y * geo.Lx;
         for (int i = 0; i < 9; ++i) {
-            const int xd = (x + cvx(i) + geo.Lx) % geo.Lx, yd = (y + cvy(i) + geo.Ly) % geo.Ly;
-            buf[i * geo.plane + yd * geo.pitch + xd] = (T)in[i * N + n];
+            // the buffer holds f*_i(z) = f_i(z + v_i): write f_i(x) at z = x - v_i,
+            // with the ghost copy the pull of f_i(x) will read
+            const int zx = wrap(x - cvx(i), geo.Lx), zy = wrap(y - cvy(i), geo.Ly);
+            store_pop(buf, geo, i, zx, zy, (T)in[i * N + n]);
         }
     }
 }
@@ -171,12 +171,11 @@ __global__ void scatter_state_kernel(const double* in, Geometry geo, T* buf) {
 template <class T>
 __global__ void gather_state_kernel(const T* buf, Geometry geo, double* out) {
     const long long N = (long long)geo.Lx * geo.Ly;
-    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
-         n += (long long)gridDim.x * blockDim.x) {
-        const int y = (int)(n / geo.Lx), x = (int)(n - (long long)y * geo.Lx);
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < (int)N; n += gridDim.x * blockDim.x) {
+        const int y = n / geo.Lx, x = n - y * geo.Lx;
         for (int i = 0; i < 9; ++i) {
-            const int xs = (x - cvx(i) + geo.Lx) % geo.Lx, ys = (y - cvy(i) + geo.Ly) % geo.Ly;
-            out[i * N + n] = (double)buf[i * geo.plane + ys * geo.pitch + xs];
+            const int xs = wrap(x - cvx(i), geo.Lx), ys = wrap(y - cvy(i), geo.Ly);
+            out[i * N + n] = (double)buf[at(geo, i, xs, ys)];
         }
     }
 }
@@ -277,14 +276,7 @@ int valid_params(const flb_params* p) {
 
 int elem_size(int prec) { return prec == FLB_FP64 ? 8 : 4; }
 
-Geometry make_geometry(const flb_params* p) {
-    Geometry g;
-    g.Lx = p->Lx;
-    g.Ly = p->Ly;
-    g.pitch = (long long)((p->Lx + 31) / 32 * 32);   // rows start on 128-byte boundaries
-    g.plane = g.pitch * p->Ly;
-    return g;
-}
+Geometry make_geometry(const flb_params* p) { return flb::make_geometry(p->Lx, p->Ly); }
 
 int device_sms() {
     int dev = 0, sms = 0;

@@ -1,10 +1,10 @@
 // flb_kernels.cuh -- lattice kernels: fused pull-stream + collide (+ sampling),
 // correlation reduction and finalisation, conservation sums, state I/O.
 //
-// Storage: 9 SoA planes per buffer, plane i row y at base + i*plane + y*pitch.
-// A buffer holds the post-collision populations f*_i(x, t-1); the step kernel
-// pulls g_i(x) = f*_i(x - v_i) (periodic), which is the pre-collision state
-// f_i(x, t) of Eq. LBE1, collides it and writes f*_i(x, t) to the other buffer.
+// A buffer holds the post-collision populations f*_i(x, t-1) (layout and ghost
+// frame: flb_layout.cuh); the step kernel pulls g_i(x) = f*_i(x - v_i), which is
+// the pre-collision state f_i(x, t) of Eq. LBE1, collides it and writes
+// f*_i(x, t) to the other buffer.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -12,6 +12,7 @@
 #include <cstdint>
 
 #include "flb_device.cuh"
+#include "flb_layout.cuh"
 
 namespace flb {
 
@@ -27,12 +28,6 @@ struct DevError {
 
 struct Vec9 {
     double v[9];
-};
-
-struct Geometry {
-    int Lx, Ly;
-    long long pitch;   // elements per row
-    long long plane;   // elements per plane
 };
 
 template <class T>
@@ -84,26 +79,20 @@ template <class T, int BASIS, bool SAMPLE>
 __global__ void __launch_bounds__(kStepThreads)
 step_kernel(StepArgs<T> a, CollideConst<T> cc) {
     using A = typename AccType<T>::type;
-    const int Lx = a.geo.Lx, Ly = a.geo.Ly;
-    const long long N = (long long)Lx * Ly;
+    const int Lx = a.geo.Lx;
+    const long long N = (long long)Lx * a.geo.Ly;
     A s[kSums];
     if (SAMPLE) {
 #pragma unroll
         for (int k = 0; k < kSums; ++k) s[k] = A(0);
     }
-    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
-         n += (long long)gridDim.x * blockDim.x) {
-        const int y = (int)(n / Lx);
-        const int x = (int)(n - (long long)y * Lx);
-        const int xm = x == 0 ? Lx - 1 : x - 1, xp = x == Lx - 1 ? 0 : x + 1;
-        const int ym = y == 0 ? Ly - 1 : y - 1, yp = y == Ly - 1 ? 0 : y + 1;
+    // N < 2^31 (checked at creation): 32-bit node indices
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < (int)N; n += gridDim.x * blockDim.x) {
+        const int y = n / Lx;
+        const int x = n - y * Lx;
         T g[9];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const int xs = cvx(i) == 1 ? xm : (cvx(i) == -1 ? xp : x);
-            const int ys = cvy(i) == 1 ? ym : (cvy(i) == -1 ? yp : y);
-            g[i] = a.src[i * a.geo.plane + ys * a.geo.pitch + xs];
-        }
+        for (int i = 0; i < 9; ++i) g[i] = a.src[at(a.geo, i, x - cvx(i), y - cvy(i))];
         if (SAMPLE) {
             A d[9];
 #pragma unroll
@@ -119,8 +108,7 @@ step_kernel(StepArgs<T> a, CollideConst<T> cc) {
         T f[9];
         const int st = collide<T, BASIS>(g, (uint32_t)n, a.step, cc, f);
         if (st != kStatusOk) record_error(a.err, st, n, a.step);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) a.dst[i * a.geo.plane + y * a.geo.pitch + x] = f[i];
+        store_node(a.dst, a.geo, x, y, f);
     }
     if (SAMPLE) block_reduce_sums<A>(s, a.partials + (long long)blockIdx.x * kSums);
 }
