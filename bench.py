@@ -239,9 +239,12 @@ def main():
     peak, peak_kind = measured_peaks()
     algo_bytes = BYTES_PER_NODE[args.precision] * nodes
     achieved = algo_bytes / (step_ms * 1e-3) / 1e9
+    pipelined = args.precision == "fp32"
+    kname = ("step_tma_kernel<%s,sample>" % args.basis) if pipelined else \
+        ("step_kernel<f64,%s,sample>" % args.basis)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
-                "kernel": f"step_kernel<{args.precision},{args.basis},sample>"}
+                "kernel": kname}
 
     Cff, CMM, mean, ns = lat.correlations(args.basis)
     lat.close()
@@ -286,7 +289,7 @@ def main():
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": 2 * args.steps,
+            "gpu_launches": (1 if pipelined else 2) * args.steps,
             "clocks": clk.summary(),
             "mlups_roofline_frac": value / (peak * 1e9 / BYTES_PER_NODE[args.precision] / 1e6) / world,
             "n_samples": ns,

@@ -178,6 +178,21 @@ int flb_noise_draws(uint64_t seed, uint32_t replica, uint32_t step, const uint32
 int flb_collide_nodes(const flb_params* p, const double* g, const uint32_t* node_ids,
                       uint32_t step, int32_t n, double* fstar, int32_t* status);
 
+/* Tuning and testing options of a lattice handle.
+ *  FLB_OPT_KERNEL: which step kernel runs -- FLB_KERNEL_AUTO (default: the
+ *    pipelined TMA kernel for FP32, the generic kernel for FP64),
+ *    FLB_KERNEL_GENERIC (one node per thread, plain loads) or
+ *    FLB_KERNEL_PIPELINED (FP32 only). All give the same results up to rounding.
+ *  FLB_OPT_PIPELINE_WARPS: consumer warps per CTA of the pipelined kernel
+ *    (4 or 8; the tile is 128 x value/2 nodes). FP32 only.
+ * Errors: FLB_ERR_ARG for an unknown option or value. */
+#define FLB_OPT_KERNEL 0
+#define FLB_OPT_PIPELINE_WARPS 1
+#define FLB_KERNEL_AUTO 0
+#define FLB_KERNEL_GENERIC 1
+#define FLB_KERNEL_PIPELINED 2
+int flb_set_option(flb_lattice h, int32_t option, int32_t value);
+
 const char* flb_error_string(int code);
 
 /* Library version as major*10000 + minor*100 + patch. */

@@ -8,6 +8,7 @@
 #include <new>
 
 #include "../../include/flb.h"
+#include "flb_internal.h"
 #include "flb_kernels.cuh"
 
 namespace flb {
@@ -32,11 +33,13 @@ __global__ void measure_basis_kernel(int basis, double ux0, double uy0, double* 
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     double P[9][9];
     {
-        double D[9];
+        // row a of P = P^T applied to the unit vector e_a (D_1 = -K1, D_2 = -K2)
         for (int a = 0; a < 9; ++a) {
-            for (int b = 0; b < 9; ++b) D[b] = (a == b) ? 1.0 : 0.0;
+            double Dn[6];
+            for (int b = 0; b < 6; ++b) Dn[b] = (a == 3 + b) ? 1.0 : 0.0;
             double h[9];
-            hermite_back<double>(D, h);     // column a of P^T = row a of P
+            hermite_back<double, true>(a == 0 ? 1.0 : 0.0, a == 1 ? -1.0 : 0.0,
+                                       a == 2 ? -1.0 : 0.0, Dn, h);
             for (int i = 0; i < 9; ++i) P[a][i] = h[i];
         }
     }
@@ -198,8 +201,9 @@ __global__ void noise_draws_kernel(uint64_t seed, uint32_t replica, uint32_t ste
                                    double* normals) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
+    const NoiseKey key = make_noise_key(seed, replica);   // per-thread copy, test hook only
     uint32_t f[6];
-    draw_fields(node_draw(seed, replica, nodes[k], step), f);
+    node_fields(key, nodes[k], step, f);
     T z[6];
     box_muller(f, z);
     for (int q = 0; q < 6; ++q) {
@@ -215,7 +219,9 @@ __global__ void collide_nodes_kernel(const double* g, const uint32_t* ids, uint3
     if (k >= n) return;
     T gg[9], ff[9];
     for (int i = 0; i < 9; ++i) gg[i] = (T)g[k * 9 + i];
-    const int st = collide<T, BASIS>(gg, ids[k], step, cc, ff);
+    const uint32_t id = ids[k];
+    const int st = (int)(collide<T, BASIS>(
+        gg, [&](T* N) { node_normals(cc.key, id, step, N); }, cc, ff) & 0xFF);
     for (int i = 0; i < 9; ++i) fs[k * 9 + i] = (double)ff[i];
     status[k] = st;
 }
@@ -242,9 +248,12 @@ struct flb_lattice_s {
     double* acc;         // kSums running sums
     double* small;       // basis (81) + finalize output (171) + conservation (3)
     DevError* err;
+    unsigned int* ticket;  // CTA completion counter of the pipelined kernel
     cudaStream_t stream;
     int64_t t, warmup, every, nsamp;
     int sticky;
+    int variant;           // FLB_KERNEL_*
+    TmaPlan tma;           // pipelined FP32 kernel (tensor maps, launch shape)
     double ref[9];
 };
 
@@ -294,8 +303,8 @@ int step_grid(const Geometry& g, int sms) {
 }
 
 struct Layout {
-    size_t buf_bytes, partial_off, acc_off, small_off, err_off, total;
-    int nblocks;
+    size_t buf_bytes, partial_off, acc_off, small_off, err_off, ticket_off, total;
+    int nblocks, npartials;
 };
 
 Layout layout(const flb_params* p, int sms) {
@@ -304,14 +313,17 @@ Layout layout(const flb_params* p, int sms) {
     L.nblocks = step_grid(g, sms);
     L.buf_bytes = align_up((size_t)(9 * g.plane) * elem_size(p->precision));
     size_t off = 2 * L.buf_bytes;
+    L.npartials = L.nblocks > tma_max_grid(sms) ? L.nblocks : tma_max_grid(sms);
     L.partial_off = off;
-    off += align_up(sizeof(double) * (size_t)L.nblocks * kSums);
+    off += align_up(sizeof(double) * (size_t)L.npartials * kSums);
     L.acc_off = off;
     off += align_up(sizeof(double) * kSums);
     L.small_off = off;
     off += align_up(sizeof(double) * (81 + 171 + 3 + 3 * (size_t)L.nblocks));
     L.err_off = off;
     off += align_up(sizeof(DevError));
+    L.ticket_off = off;
+    off += align_up(sizeof(unsigned int));
     L.total = off;
     return L;
 }
@@ -330,12 +342,11 @@ CollideConst<T> collide_const(const flb_params* p) {
     CollideConst<T> cc;
     for (int a = 0; a < 6; ++a) {
         const double om = p->omega[3 + a];
-        cc.omega[a] = (T)om;
+        cc.nomega[a] = (T)(-om);
         const double v = p->kT * om * (2.0 - om);
         cc.amp[a] = (T)(v > 0 ? std::sqrt(v) : 0.0);
     }
-    cc.seed = p->seed;
-    cc.replica = p->replica;
+    cc.key = make_noise_key(p->seed, p->replica);
     return cc;
 }
 
@@ -344,6 +355,7 @@ int cuda_rc(cudaError_t e) { return e == cudaSuccess ? FLB_OK : FLB_ERR_CUDA; }
 int map_status(int code) {
     if (code == kStatusInvalidVelocity) return FLB_ERR_INVALID_VELOCITY;
     if (code == kStatusNonfinite) return FLB_ERR_NONFINITE;
+    if (code == kStatusTimeout) return FLB_ERR_TIMEOUT;
     return code ? FLB_ERR_STATE : FLB_OK;
 }
 
@@ -375,8 +387,28 @@ cudaError_t launch_step_p(flb_lattice h, bool sample) {
     return sample ? launch_step_t<T, 1, true>(h) : launch_step_t<T, 1, false>(h);
 }
 
+// Pipelined FP32 kernel: also reduces the sampled sums into h->acc itself.
+cudaError_t launch_step_tma(flb_lattice h, bool sample) {
+    TmaArgs a;
+    a.dst = (float*)h->buf[h->cur ^ 1];
+    a.geo = h->geo;
+    a.step = (uint32_t)h->t;
+    a.tiles_x = a.ntiles = 0;
+    a.partials = h->partials;
+    a.acc = h->acc;
+    a.ticket = h->ticket;
+    a.err = h->err;
+    for (int i = 0; i < 9; ++i) a.ref[i] = (float)h->ref[i];
+    return tma_step(h->tma, h->cur, a, collide_const<float>(&h->p), h->p.basis, sample, h->stream);
+}
+
+bool uses_tma(flb_lattice h) {
+    return h->p.precision == FLB_FP32 && h->variant != FLB_KERNEL_GENERIC;
+}
+
 cudaError_t launch_step(flb_lattice h, bool sample) {
     if (h->p.precision == FLB_FP64) return launch_step_p<double>(h, sample);
+    if (uses_tma(h)) return launch_step_tma(h, sample);
     return launch_step_p<float>(h, sample);
 }
 
@@ -452,7 +484,9 @@ int flb_create(const flb_params* p, void* dev_workspace, size_t workspace_bytes,
     h->acc = (double*)(h->ws + L.acc_off);
     h->small = (double*)(h->ws + L.small_off);
     h->err = (DevError*)(h->ws + L.err_off);
+    h->ticket = (unsigned int*)(h->ws + L.ticket_off);
     h->nblocks = L.nblocks;
+    h->variant = FLB_KERNEL_AUTO;
     h->cur = 0;
     feq_host(p->rho0, p->ux0, p->uy0, h->ref);
 
@@ -469,7 +503,10 @@ int flb_create(const flb_params* p, void* dev_workspace, size_t workspace_bytes,
         ce = cudaGetLastError();
     }
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
+    if (ce == cudaSuccess && p->precision == FLB_FP32)
+        ce = tma_plan(&h->tma, h->buf[0], h->buf[1], h->geo, 0);
     if (ce != cudaSuccess) {
+        cudaGetLastError();
         if (h->own_ws) cudaFree(h->ws);
         delete h;
         return FLB_ERR_CUDA;
@@ -510,16 +547,39 @@ int flb_step(flb_lattice h, int64_t n) {
         const bool sample =
             h->every > 0 && h->t >= h->warmup && ((h->t - h->warmup) % h->every) == 0;
         cudaError_t ce = launch_step(h, sample);
-        if (ce == cudaSuccess && sample) {
+        if (ce == cudaSuccess && sample && !uses_tma(h)) {
             accumulate_partials_kernel<<<1, 64, 0, h->stream>>>(h->partials, h->nblocks, h->acc);
             ce = cudaGetLastError();
-            h->nsamp += N;
         }
+        if (sample) h->nsamp += N;
         if (ce != cudaSuccess) return FLB_ERR_CUDA;
         h->t += 1;
         h->cur ^= 1;
     }
     return FLB_OK;
+}
+
+int flb_set_option(flb_lattice h, int32_t option, int32_t value) {
+    if (!h) return FLB_ERR_ARG;
+    if (option == FLB_OPT_KERNEL) {
+        if (value != FLB_KERNEL_AUTO && value != FLB_KERNEL_GENERIC && value != FLB_KERNEL_PIPELINED)
+            return FLB_ERR_ARG;
+        if (value == FLB_KERNEL_PIPELINED && h->p.precision != FLB_FP32) return FLB_ERR_ARG;
+        h->variant = value;
+        return FLB_OK;
+    }
+    if (option == FLB_OPT_PIPELINE_WARPS) {
+        if (h->p.precision != FLB_FP32) return FLB_ERR_ARG;
+        TmaPlan plan;
+        const cudaError_t ce = tma_plan(&plan, h->buf[0], h->buf[1], h->geo, value);
+        if (ce != cudaSuccess) {
+            cudaGetLastError();
+            return FLB_ERR_ARG;
+        }
+        h->tma = plan;
+        return FLB_OK;
+    }
+    return FLB_ERR_ARG;
 }
 
 int flb_sync(flb_lattice h) {

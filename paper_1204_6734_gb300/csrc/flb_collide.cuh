@@ -1,0 +1,327 @@
+// flb_collide.cuh -- the collision of Eq. LBEMRT for one node (V = double,
+// float) or two nodes (V = f2), in the Hermite norm (BASIS 0) or the f-norm
+// (BASIS 1). The algebra is described at the top of flb_device.cuh; here it is
+// arranged so that every subtraction folds into a fused multiply-add:
+//  * the Gram matrix is evaluated negated (Gn = -G_NN) and so is the Schur
+//    complement (Sn = -S = Gn + e e^T + k1 k1^T + k2 k2^T);
+//  * the Cholesky factor is stored negated (Ln = -L'): the products Ln Ln = L L
+//    keep their sign, so the factorisation and both triangular solves are
+//    chains of fma(Ln, ., .) followed by one scaling with 1/L'_jj.
+// Validity (Fig. 11): the Gram matrix P diag(W) P^T is positive definite iff
+// every W_i = f_i^0(1,u) > 0; its leading 3x3 block is always positive definite,
+// so this holds iff every pivot of S is positive, i.e. iff all six 1/sqrt(pivot)
+// are finite. The kernel checks their sum.
+#pragma once
+
+#include "flb_device.cuh"
+#include "flb_vec.cuh"
+
+namespace flb {
+
+// Philox4x32-10 (Salmon et al., SC'11) with the round keys precomputed.
+__device__ __forceinline__ Draw philox_rk(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                          const NoiseKey& key) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+        const uint32_t y0 = (uint32_t)(p1 >> 32) ^ c1 ^ key.rk[2 * r];
+        const uint32_t y2 = (uint32_t)(p0 >> 32) ^ c3 ^ key.rk[2 * r + 1];
+        c0 = y0;
+        c1 = (uint32_t)p1;
+        c2 = y2;
+        c3 = (uint32_t)p0;
+    }
+    return Draw{c0, c1, c2, c3};
+}
+
+// Counter (node, step, replica, 0), key = seed.
+__device__ __forceinline__ void node_fields(const NoiseKey& key, uint32_t node, uint32_t step,
+                                            uint32_t k[6]) {
+    draw_fields(philox_rk(node, step, key.replica, 0u, key), k);
+}
+
+template <class T>
+__device__ __forceinline__ void node_normals(const NoiseKey& key, uint32_t node, uint32_t step,
+                                             T n[6]) {
+    uint32_t k[6];
+    node_fields(key, node, step, k);
+    box_muller(k, n);
+}
+
+__device__ __forceinline__ void node_normals(const NoiseKey& key, uint32_t nodeA, uint32_t nodeB,
+                                             uint32_t step, f2 n[6]) {
+    float a[6], b[6];
+    node_normals(key, nodeA, step, a);
+    node_normals(key, nodeB, step, b);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) n[q] = f2(a[q], b[q]);
+}
+
+// Status per lane: bits [8k, 8k+8) hold the kStatus* code of lane k.
+__device__ __forceinline__ double rsq_neg(double x) { return rsq(-x); }
+__device__ __forceinline__ float rsq_neg(float x) { return rsq(-x); }
+__device__ __forceinline__ f2 rsq_neg(f2 a) { return f2(rsq(-a.v.x), rsq(-a.v.y)); }
+
+template <class V>
+__device__ __forceinline__ uint32_t lane_status(V rho, V invsum, bool local) {
+    uint32_t st = 0;
+#pragma unroll
+    for (int k = 0; k < Lanes<V>::n; ++k) {
+        const auto r = lane(rho, k);
+        uint32_t s = kStatusOk;
+        if (!(r > 0) || !isfinite(r)) {
+            s = kStatusNonfinite;
+        } else if (local) {
+            const auto q = lane(invsum, k);
+            if (!isfinite(q)) s = kStatusInvalidVelocity;
+        }
+        st |= s << (8 * k);
+    }
+    return st;
+}
+
+// Lanes whose status is not ok keep their pre-collision populations.
+__device__ __forceinline__ void keep_invalid(uint32_t st, const double g[9], double f[9]) {
+    if (st)
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f[i] = g[i];
+}
+__device__ __forceinline__ void keep_invalid(uint32_t st, const float g[9], float f[9]) {
+    if (st)
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f[i] = g[i];
+}
+__device__ __forceinline__ void keep_invalid(uint32_t st, const f2 g[9], f2 f[9]) {
+    if (st) {
+        const bool a = (st & 0xFF) != 0, b = (st >> 8) != 0;
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+            f[i] = f2(a ? g[i].v.x : f[i].v.x, b ? g[i].v.y : f[i].v.y);
+    }
+}
+
+// f* - g for the given non-conserved increments (Hermite coefficients D of
+// P^T D, with D_1 = -K1, D_2 = -K2 folded into the constants).
+template <class V, bool CONS>
+__device__ __forceinline__ void hermite_back(V D0, V K1, V K2, const V Dn[6], V h[9]) {
+    using S = typename Elem<V>::type;
+    const V D3 = Dn[0], D4 = Dn[1], D5 = Dn[2], D6 = Dn[3], D7 = Dn[4], D8 = Dn[5];
+    V base0, axis, diag, jxt, jyt;
+    if (CONS) {
+        base0 = mad(D8, V(S(0.5)), D0 - D5);
+        axis = mad(D5, V(S(0.5)), D0 - D8);
+        diag = mad(D5 + D8, V(S(2)), D0);
+        jxt = K1 * V(S(-kSqrt3));
+        jyt = K2 * V(S(-kSqrt3));
+    } else {   // D0 = D1 = D2 = 0
+        base0 = mad(D8, V(S(0.5)), V(S(0)) - D5);
+        axis = mad(D5, V(S(0.5)), V(S(0)) - D8);
+        diag = (D5 + D8) * V(S(2));
+    }
+    const V px = D3 * V(S(1.5)), pxy = D4 * V(S(3));
+    const V qxa = D6 * V(S(kSqrt3h)), qya = D7 * V(S(kSqrt3h));
+    const V ap = axis + px, am = axis - px;
+    const V jq = CONS ? jxt - qxa : V(S(0)) - qxa;
+    const V jqy = CONS ? jyt - qya : V(S(0)) - qya;
+    h[0] = base0;
+    h[1] = ap + jq;
+    h[3] = ap - jq;
+    h[2] = am + jqy;
+    h[4] = am - jqy;
+    const V a = diag + pxy, b = diag - pxy;
+    // sqrt6 = 2 sqrt(3/2)
+    const V ex = CONS ? mad(qxa, V(S(2)), jxt) : qxa * V(S(2));
+    const V ey = CONS ? mad(qya, V(S(2)), jyt) : qya * V(S(2));
+    const V xpy = ex + ey, xmy = ex - ey;
+    h[5] = a + xpy;
+    h[7] = a - xpy;
+    h[8] = b + xmy;
+    h[6] = b - xmy;
+}
+
+// One collision. g: pre-collision populations; noise(N) fills the normals
+// N^3..N^8 (called once, after the basis is built, to keep registers free);
+// f: output.
+template <class V, int BASIS, class Noise>
+__device__ __forceinline__ uint32_t collide(const V g[9], Noise noise,
+                                            const CollideConst<typename Elem<V>::type>& cc,
+                                            V f[9]) {
+    using S = typename Elem<V>::type;
+    // density, momentum, velocity
+    const V s13 = g[1] + g[3], s24 = g[2] + g[4];
+    const V d13 = g[1] - g[3], d24 = g[2] - g[4];
+    const V c58 = g[5] + g[8], c67 = g[6] + g[7];
+    const V c56 = g[5] + g[6], c78 = g[7] + g[8];
+    const V cx = c58 - c67, cy = c56 - c78;
+    const V c = c58 + c67;
+    const V s1234 = s13 + s24;
+    const V rho = (g[0] + s1234) + c;
+    const V jx = d13 + cx, jy = d24 + cy;
+    const V ir = rcp(rho);
+    const V ux = jx * ir, uy = jy * ir;
+    const V uxx = ux * ux, uyy = uy * uy, uxy = ux * uy;
+    const V usq = uxx + uyy;
+    const V t3 = uxx - uyy;
+    // Hermite equilibrium moments at rho = 1 (Eq. d2q94), negated: ne_a = -e_a
+    const V ne3 = t3 * V(S(-1.5)), ne4 = uxy * V(S(-3)), ne5 = usq * V(S(-1.5));
+    // non-equilibrium Hermite moments M^a - rho e_a, a = 3..8
+    V M[6];
+    M[0] = mad(rho, ne3, (s13 - s24) * V(S(1.5)));
+    M[1] = mad(rho, ne4, ((g[5] - g[6]) + (g[7] - g[8])) * V(S(3)));
+    M[2] = mad(rho, ne5, mad(s1234, V(S(0.5)), c * V(S(2))) - g[0]);
+    M[3] = mad(cx, V(S(kSqrt6)), d13 * V(S(-kSqrt3h)));
+    M[4] = mad(cy, V(S(kSqrt6)), d24 * V(S(-kSqrt3h)));
+    M[5] = mad(g[0], V(S(0.5)), c * V(S(2))) - s1234;
+    const V sr = sqr(rho);
+
+    if (BASIS == 0) {
+        // Hermite norm: D_a = -omega_a (M^a - M^{a,0}) + xi^a N^a, f* = g + w (.) P^T D
+        V N[6];
+        noise(N);
+        V Dn[6];
+#pragma unroll
+        for (int a = 0; a < 6; ++a) Dn[a] = mad(V(cc.nomega[a]), M[a], (sr * N[a]) * V(cc.amp[a]));
+        V h[9];
+        hermite_back<V, false>(V(S(0)), V(S(0)), V(S(0)), Dn, h);
+        f[0] = mad(h[0], V(S(4.0 / 9.0)), g[0]);
+#pragma unroll
+        for (int i = 1; i <= 4; ++i) f[i] = mad(h[i], V(S(1.0 / 9.0)), g[i]);
+#pragma unroll
+        for (int i = 5; i <= 8; ++i) f[i] = mad(h[i], V(S(1.0 / 36.0)), g[i]);
+        const uint32_t st = lane_status(rho, rho, false);
+        keep_invalid(st, g, f);
+        return st;
+    }
+
+    // rows of L below the conserved block: e, k1, k2 (zero entries omitted)
+    const V s3x = ux * V(S(kSqrt3)), s3y = uy * V(S(kSqrt3));
+    const V base = mad(usq, V(S(-1.5)), V(S(1)));   // 1 - e5
+    const V k1_0 = s3x * mad(t3, V(S(-1.5)), V(S(1)));
+    const V k1_1 = s3y * mad(uxx, V(S(-3)), V(S(1)));
+    const V k1_2 = s3x * base;
+    const V k1_3 = uyy * V(S(kSqrt2x3h));
+    const V k1_4 = uxy * V(S(kSqrt2x3));
+    const V k2_0 = s3y * mad(t3, V(S(-1.5)), V(S(-1)));
+    const V k2_1 = s3x * mad(uyy, V(S(-3)), V(S(1)));
+    const V k2_2 = s3y * base;
+    const V k2_3 = k1_4;
+    const V k2_4 = uxx * V(S(kSqrt2x3h));
+
+    // Sn = -(G_NN - e e^T - k1 k1^T - k2 k2^T), upper triangle
+    V Sn[6][6];
+    {
+        const V r6x = ux * V(S(kSqrt6h));
+        const V n6x = ux * V(S(-kSqrt6)), n6y = uy * V(S(-kSqrt6));
+        const V g00 = mad(usq, V(S(-0.75)), V(S(-1)));
+        const V n6xy = uxy * V(S(-6));
+        Sn[0][0] = g00;
+        Sn[0][1] = V(S(0));
+        Sn[0][2] = t3 * V(S(-0.75));
+        Sn[0][3] = r6x;
+        Sn[0][4] = uy * V(S(-kSqrt6h));
+        Sn[0][5] = t3 * V(S(1.5));
+        Sn[1][1] = mad(usq, V(S(-3)), V(S(-1)));
+        Sn[1][2] = n6xy;
+        Sn[1][3] = n6y;
+        Sn[1][4] = n6x;
+        Sn[1][5] = n6xy;
+        Sn[2][2] = g00;
+        Sn[2][3] = ux * V(S(-kSqrt6h));
+        Sn[2][4] = Sn[0][4];
+        Sn[2][5] = ne5;
+        Sn[3][3] = mad(uxx, V(S(-3)), mad(uyy, V(S(-1.5)), V(S(-1))));
+        Sn[3][4] = n6xy;
+        Sn[3][5] = n6x;
+        Sn[4][4] = mad(uxx, V(S(-1.5)), mad(uyy, V(S(-3)), V(S(-1))));
+        Sn[4][5] = n6y;
+        Sn[5][5] = mad(usq, V(S(-1.5)), V(S(-1)));
+        const V e[3] = {ne3, ne4, ne5};   // e_a e_b = ne_a ne_b
+        const V k1[5] = {k1_0, k1_1, k1_2, k1_3, k1_4};
+        const V k2[5] = {k2_0, k2_1, k2_2, k2_3, k2_4};
+#pragma unroll
+        for (int a = 0; a < 5; ++a)
+#pragma unroll
+            for (int b = a; b < 5; ++b) {
+                V s = mad(k1[a], k1[b], mad(k2[a], k2[b], Sn[a][b]));
+                if (b < 3) s = mad(e[a], e[b], s);
+                Sn[a][b] = s;
+            }
+    }
+
+    // Cholesky of S with the factor stored negated: Ln = -L'
+    V Ln[6][6], inv[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        V dn = Sn[j][j];                       // -(pivot)
+#pragma unroll
+        for (int k = 0; k < j; ++k) dn = mad(Ln[j][k], Ln[j][k], dn);
+        inv[j] = rsq_neg(dn);
+#pragma unroll
+        for (int i = j + 1; i < 6; ++i) {
+            V s = Sn[j][i];
+#pragma unroll
+            for (int k = 0; k < j; ++k) s = mad(Ln[i][k], Ln[j][k], s);
+            Ln[i][j] = s * inv[j];
+        }
+    }
+    const V invsum = ((inv[0] + inv[1]) + (inv[2] + inv[3])) + (inv[4] + inv[5]);
+
+    // M~_N = L'^{-1} (M_N - rho e_N)
+    V y[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        V s = M[j];
+#pragma unroll
+        for (int k = 0; k < j; ++k) s = mad(Ln[j][k], y[k], s);
+        y[j] = s * inv[j];
+    }
+    // increments: relaxation towards M~^{a,0} = 0 (Eq. fnormmeq) plus noise
+    V N[6];
+    noise(N);
+    V z[6];
+#pragma unroll
+    for (int a = 0; a < 6; ++a) z[a] = mad(V(cc.nomega[a]), y[a], (sr * N[a]) * V(cc.amp[a]));
+    // D_N = L'^{-T} z
+#pragma unroll
+    for (int j = 5; j >= 0; --j) {
+        V s = z[j];
+#pragma unroll
+        for (int k = j + 1; k < 6; ++k) s = mad(Ln[k][j], z[k], s);
+        z[j] = s * inv[j];
+    }
+    const V nE = mad(ne3, z[0], mad(ne4, z[1], ne5 * z[2]));
+    const V K1 = mad(k1_0, z[0], mad(k1_1, z[1], mad(k1_2, z[2], mad(k1_3, z[3], k1_4 * z[4]))));
+    const V K2 = mad(k2_0, z[0], mad(k2_1, z[1], mad(k2_2, z[2], mad(k2_3, z[3], k2_4 * z[4]))));
+    const V D0 = mad(s3x, K1, mad(s3y, K2, nE));
+    V h[9];
+    hermite_back<V, true>(D0, K1, K2, z, h);
+    // W_i = f_i^0(1, u) (Eq. d2q9f0)
+    V W[9];
+    {
+        const V base = mad(usq, V(S(-1.5)), V(S(1)));
+        const V b45 = mad(usq, V(S(4.5)), base);
+        const V ax = mad(uxx, V(S(4.5)), base), ay = mad(uyy, V(S(4.5)), base);
+        const V dp = mad(uxy, V(S(9)), b45), dm = mad(uxy, V(S(-9)), b45);
+        const V spy = ux + uy, smy = ux - uy;
+        W[0] = base * V(S(4.0 / 9.0));
+        const V tx = ax * V(S(1.0 / 9.0)), ty = ay * V(S(1.0 / 9.0));
+        W[1] = mad(ux, V(S(1.0 / 3.0)), tx);
+        W[3] = mad(ux, V(S(-1.0 / 3.0)), tx);
+        W[2] = mad(uy, V(S(1.0 / 3.0)), ty);
+        W[4] = mad(uy, V(S(-1.0 / 3.0)), ty);
+        const V tp = dp * V(S(1.0 / 36.0)), tm = dm * V(S(1.0 / 36.0));
+        W[5] = mad(spy, V(S(1.0 / 12.0)), tp);
+        W[7] = mad(spy, V(S(-1.0 / 12.0)), tp);
+        W[8] = mad(smy, V(S(1.0 / 12.0)), tm);
+        W[6] = mad(smy, V(S(-1.0 / 12.0)), tm);
+    }
+
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i] = mad(W[i], h[i], g[i]);
+    const uint32_t st = lane_status(rho, invsum, true);
+    keep_invalid(st, g, f);
+    return st;
+}
+
+}  // namespace flb

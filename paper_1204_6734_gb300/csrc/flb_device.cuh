@@ -31,6 +31,8 @@
 
 #include <cstdint>
 
+#include "flb_vec.cuh"
+
 namespace flb {
 
 // ---------------------------------------------------------------------------
@@ -61,26 +63,6 @@ struct Draw {
     uint32_t x0, x1, x2, x3;
 };
 
-__device__ __forceinline__ Draw philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2,
-                                              uint32_t c3, uint32_t k0, uint32_t k1) {
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const uint32_t lo0 = 0xD2511F53u * c0;
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c0);
-        const uint32_t lo1 = 0xCD9E8D57u * c2;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2);
-        const uint32_t y0 = hi1 ^ c1 ^ k0;
-        const uint32_t y2 = hi0 ^ c3 ^ k1;
-        c0 = y0;
-        c1 = lo1;
-        c2 = y2;
-        c3 = lo0;
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
-    }
-    return Draw{c0, c1, c2, c3};
-}
-
 // The six 21-bit fields k_q = (X >> 21q) mod 2^21 of X = x0 + 2^32 x1 + 2^64 x2 + 2^96 x3.
 __device__ __forceinline__ void draw_fields(const Draw& d, uint32_t k[6]) {
     const uint32_t m = 0x1FFFFFu;
@@ -90,11 +72,6 @@ __device__ __forceinline__ void draw_fields(const Draw& d, uint32_t k[6]) {
     k[3] = (d.x1 >> 31) | ((d.x2 & 0xFFFFFu) << 1);
     k[4] = (d.x2 >> 20) | ((d.x3 & 0x1FFu) << 12);
     k[5] = (d.x3 >> 9) & m;
-}
-
-__device__ __forceinline__ Draw node_draw(uint64_t seed, uint32_t replica, uint32_t node,
-                                          uint32_t step) {
-    return philox4x32_10(node, step, replica, 0u, (uint32_t)seed, (uint32_t)(seed >> 32));
 }
 
 // Box-Muller: u1 = (k_{2p}+1) 2^-21 in (0,1], u2 = k_{2p+1} 2^-21 in [0,1),
@@ -132,284 +109,35 @@ __device__ __forceinline__ void box_muller(const uint32_t k[6], float n[6]) {
 }
 
 // ---------------------------------------------------------------------------
-// Precision-dependent helpers
+// Per-launch constants
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
-__device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
-__device__ __forceinline__ double rsq(double x) { return 1.0 / sqrt(x); }
-__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
-__device__ __forceinline__ double sqr_root(double x) { return sqrt(x); }
-__device__ __forceinline__ float sqr_root(float x) {
-    float r;
-    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-
-// Per-launch collision constants (a = 3..8 stored at [a-3]).
-template <class T>
-struct CollideConst {
-    T omega[6];   // omega_a
-    T amp[6];     // sqrt(kT omega_a (2 - omega_a)); times sqrt(rho) gives xi^a
-    uint64_t seed;
-    uint32_t replica;
+// Noise key of one lattice: Philox round keys precomputed from the seed.
+struct NoiseKey {
+    uint32_t rk[20];   // (k0 + r W0, k1 + r W1) mod 2^32, r = 0..9; (k0, k1) = seed
+    uint32_t replica;  // third counter word
 };
 
-enum : int { kStatusOk = 0, kStatusInvalidVelocity = 1, kStatusNonfinite = 2 };
-
-// ---------------------------------------------------------------------------
-// Hermite transforms (Eq. d2q93a rows, Eq. d2q93b = w (.) P^T)
-// ---------------------------------------------------------------------------
-
-// Non-conserved Hermite moments M^3..M^8 of g.
 template <class T>
-__device__ __forceinline__ void hermite_moments_N(const T g[9], T M[6]) {
-    const T s13 = g[1] + g[3], s24 = g[2] + g[4];
-    const T d13 = g[3] - g[1], d42 = g[4] - g[2];
-    const T c = g[5] + g[6] + g[7] + g[8];
-    const T p58 = g[5] + g[8], p67 = g[6] + g[7];
-    const T p56 = g[5] + g[6], p78 = g[7] + g[8];
-    M[0] = T(1.5) * (s13 - s24);                                  // Pi_xx-yy
-    M[1] = T(3) * ((g[5] + g[7]) - (g[6] + g[8]));                // Pi_xy
-    M[2] = -g[0] + T(0.5) * (s13 + s24) + T(2) * c;               // Pi_xx+yy
-    M[3] = T(kSqrt3h) * d13 + T(kSqrt6) * (p58 - p67);            // q_x
-    M[4] = T(kSqrt3h) * d42 + T(kSqrt6) * (p56 - p78);            // q_y
-    M[5] = T(0.5) * g[0] - (s13 + s24) + T(2) * c;                // epsilon
+struct CollideConst {
+    T nomega[6];   // -omega_a, a = 3..8
+    T amp[6];      // sqrt(kT omega_a (2 - omega_a)); times sqrt(rho) gives xi^a
+    NoiseKey key;
+};
+
+__host__ __device__ inline NoiseKey make_noise_key(uint64_t seed, uint32_t replica) {
+    NoiseKey k;
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        k.rk[2 * r] = k0;
+        k.rk[2 * r + 1] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    k.replica = replica;
+    return k;
 }
 
-// h = P^T D: h_i = sum_a p^a_i D_a.
-template <class T>
-__device__ __forceinline__ void hermite_back(const T D[9], T h[9]) {
-    const T base0 = D[0] - D[5] + T(0.5) * D[8];
-    const T axis = D[0] + T(0.5) * D[5] - D[8];          // common to i = 1..4
-    const T diag = D[0] + T(2) * D[5] + T(2) * D[8];     // common to i = 5..8
-    const T jx = T(kSqrt3) * D[1], jy = T(kSqrt3) * D[2];
-    const T px = T(1.5) * D[3], pxy = T(3) * D[4];
-    const T qxa = T(kSqrt3h) * D[6], qya = T(kSqrt3h) * D[7];
-    const T qxd = T(kSqrt6) * D[6], qyd = T(kSqrt6) * D[7];
-    h[0] = base0;
-    h[1] = axis + jx + px - qxa;
-    h[3] = axis - jx + px + qxa;
-    h[2] = axis + jy - px - qya;
-    h[4] = axis - jy - px + qya;
-    const T a = diag + pxy, b = diag - pxy;
-    const T xpy = jx + jy + qxd + qyd;   // +x+y corner
-    const T xmy = jx - jy + qxd - qyd;   // +x-y corner
-    h[5] = a + xpy;
-    h[7] = a - xpy;
-    h[8] = b + xmy;
-    h[6] = b - xmy;
-}
-
-// ---------------------------------------------------------------------------
-// Collision of one node (Eq. LBEMRT)
-// ---------------------------------------------------------------------------
-
-// Hermite norm: relaxation of M^a - M^{a,0} (Eq. d2q94) at rate omega_a plus
-// noise xi^a N^a on a = 3..8, back transform with n = w (.) P^T.
-template <class T>
-__device__ __forceinline__ int collide_standard(const T g[9], const T N[6],
-                                                const CollideConst<T>& cc, T f[9]) {
-    const T rho = ((g[0] + (g[1] + g[3])) + (g[2] + g[4])) + ((g[5] + g[7]) + (g[6] + g[8]));
-    if (!(rho > T(0)) || !isfinite(rho)) {
-#pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] = g[i];
-        return kStatusNonfinite;
-    }
-    const T jx = (g[1] - g[3]) + ((g[5] + g[8]) - (g[6] + g[7]));
-    const T jy = (g[2] - g[4]) + ((g[5] + g[6]) - (g[7] + g[8]));
-    const T ir = rcp(rho);
-    const T ux = jx * ir, uy = jy * ir;
-    const T uxx = ux * ux, uyy = uy * uy;
-    T M[6];
-    hermite_moments_N(g, M);
-    M[0] -= rho * T(1.5) * (uxx - uyy);
-    M[1] -= rho * T(3) * (ux * uy);
-    M[2] -= rho * T(1.5) * (uxx + uyy);
-    const T sr = sqr_root(rho);
-    T D[9];
-    D[0] = D[1] = D[2] = T(0);
-#pragma unroll
-    for (int a = 0; a < 6; ++a) D[3 + a] = -cc.omega[a] * M[a] + cc.amp[a] * sr * N[a];
-    T h[9];
-    hermite_back(D, h);
-    const T w0 = T(4.0 / 9.0), w1 = T(1.0 / 9.0), w5 = T(1.0 / 36.0);
-    f[0] = g[0] + w0 * h[0];
-#pragma unroll
-    for (int i = 1; i <= 4; ++i) f[i] = g[i] + w1 * h[i];
-#pragma unroll
-    for (int i = 5; i <= 8; ++i) f[i] = g[i] + w5 * h[i];
-    return kStatusOk;
-}
-
-// f-norm (Section 4): basis orthonormal under W = f^0(1,u) of this node.
-template <class T>
-__device__ __forceinline__ int collide_local(const T g[9], const T N[6],
-                                             const CollideConst<T>& cc, T f[9]) {
-    const T rho = ((g[0] + (g[1] + g[3])) + (g[2] + g[4])) + ((g[5] + g[7]) + (g[6] + g[8]));
-    if (!(rho > T(0)) || !isfinite(rho)) {
-#pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] = g[i];
-        return kStatusNonfinite;
-    }
-    const T jx = (g[1] - g[3]) + ((g[5] + g[8]) - (g[6] + g[7]));
-    const T jy = (g[2] - g[4]) + ((g[5] + g[6]) - (g[7] + g[8]));
-    const T ir = rcp(rho);
-    const T ux = jx * ir, uy = jy * ir;
-    const T uxx = ux * ux, uyy = uy * uy, uxy = ux * uy;
-    const T usq = uxx + uyy;
-
-    // W_i = f_i^0(1, u) (Eq. d2q9f0)
-    T W[9];
-    {
-        const T base = T(1) - T(1.5) * usq;
-        const T ax = base + T(4.5) * uxx, ay = base + T(4.5) * uyy;
-        const T dp = base + T(4.5) * (usq + T(2) * uxy);   // (u.v)^2 for v = +-(1,1)
-        const T dm = base + T(4.5) * (usq - T(2) * uxy);   // v = +-(1,-1)
-        const T sx = T(3) * ux, sy = T(3) * uy;
-        W[0] = T(4.0 / 9.0) * base;
-        W[1] = T(1.0 / 9.0) * (ax + sx);
-        W[3] = T(1.0 / 9.0) * (ax - sx);
-        W[2] = T(1.0 / 9.0) * (ay + sy);
-        W[4] = T(1.0 / 9.0) * (ay - sy);
-        W[5] = T(1.0 / 36.0) * (dp + (sx + sy));
-        W[7] = T(1.0 / 36.0) * (dp - (sx + sy));
-        W[8] = T(1.0 / 36.0) * (dm + (sx - sy));
-        W[6] = T(1.0 / 36.0) * (dm - (sx - sy));
-    }
-    bool valid = true;
-#pragma unroll
-    for (int i = 0; i < 9; ++i) valid = valid && (W[i] > T(0));
-
-    // conserved block of L: rows l_a = (e_a, k1_a, k2_a), a = 3..8
-    const T e3 = T(1.5) * (uxx - uyy), e4 = T(3) * uxy, e5 = T(1.5) * usq;
-    const T s3x = T(kSqrt3) * ux, s3y = T(kSqrt3) * uy;
-    T k1[6], k2[6];
-    k1[0] = s3x * (T(1) - e3);
-    k1[1] = s3y * (T(1) - T(3) * uxx);
-    k1[2] = s3x * (T(1) - e5);
-    k1[3] = T(kSqrt2x3h) * uyy;
-    k1[4] = T(kSqrt2x3) * uxy;
-    k1[5] = T(0);
-    k2[0] = -s3y * (T(1) + e3);
-    k2[1] = s3x * (T(1) - T(3) * uyy);
-    k2[2] = s3y * (T(1) - e5);
-    k2[3] = T(kSqrt2x3) * uxy;
-    k2[4] = T(kSqrt2x3h) * uxx;
-    k2[5] = T(0);
-    const T e[6] = {e3, e4, e5, T(0), T(0), T(0)};
-
-    // Gram matrix G_NN(u) = sum_i p^a_i p^b_i W_i, a, b = 3..8 (upper triangle)
-    T S[6][6];
-    {
-        const T r6x = T(kSqrt6h) * ux, r6y = T(kSqrt6h) * uy;     // sqrt6/2 u
-        S[0][0] = T(1) + T(0.75) * usq;
-        S[0][1] = T(0);
-        S[0][2] = T(0.75) * (uxx - uyy);
-        S[0][3] = -r6x;
-        S[0][4] = r6y;
-        S[0][5] = -T(1.5) * (uxx - uyy);
-        S[1][1] = T(1) + T(3) * usq;
-        S[1][2] = T(6) * uxy;
-        S[1][3] = T(kSqrt6) * uy;
-        S[1][4] = T(kSqrt6) * ux;
-        S[1][5] = T(6) * uxy;
-        S[2][2] = T(1) + T(0.75) * usq;
-        S[2][3] = r6x;
-        S[2][4] = r6y;
-        S[2][5] = T(1.5) * usq;
-        S[3][3] = T(1) + T(3) * uxx + T(1.5) * uyy;
-        S[3][4] = T(6) * uxy;
-        S[3][5] = T(kSqrt6) * ux;
-        S[4][4] = T(1) + T(1.5) * uxx + T(3) * uyy;
-        S[4][5] = T(kSqrt6) * uy;
-        S[5][5] = T(1) + T(1.5) * usq;
-    }
-    // Schur complement S = G_NN - e e^T - k1 k1^T - k2 k2^T
-#pragma unroll
-    for (int a = 0; a < 6; ++a)
-#pragma unroll
-        for (int b = a; b < 6; ++b) S[a][b] -= e[a] * e[b] + k1[a] * k1[b] + k2[a] * k2[b];
-
-    // Cholesky S = L' L'^T (lower factor stored in the lower triangle of L)
-    T L[6][6], inv[6];
-#pragma unroll
-    for (int j = 0; j < 6; ++j) {
-        T d = S[j][j];
-#pragma unroll
-        for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
-        valid = valid && (d > T(0));
-        inv[j] = rsq(d);
-#pragma unroll
-        for (int i = j + 1; i < 6; ++i) {
-            T s = S[j][i];
-#pragma unroll
-            for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
-            L[i][j] = s * inv[j];
-        }
-    }
-    if (!valid) {
-#pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] = g[i];
-        return kStatusInvalidVelocity;
-    }
-
-    // non-conserved f-norm moments M~_N = L'^{-1} (M_N - rho e_N)
-    T M[6];
-    hermite_moments_N(g, M);
-    M[0] -= rho * e3;
-    M[1] -= rho * e4;
-    M[2] -= rho * e5;
-    T y[6];
-#pragma unroll
-    for (int j = 0; j < 6; ++j) {
-        T s = M[j];
-#pragma unroll
-        for (int k = 0; k < j; ++k) s -= L[j][k] * y[k];
-        y[j] = s * inv[j];
-    }
-    // change of each moment: relaxation towards M~^{a,0} = 0 (Eq. fnormmeq) + noise
-    const T sr = sqr_root(rho);
-    T z[6];
-#pragma unroll
-    for (int a = 0; a < 6; ++a) z[a] = -cc.omega[a] * y[a] + cc.amp[a] * sr * N[a];
-    // D_N = L'^{-T} z
-#pragma unroll
-    for (int j = 5; j >= 0; --j) {
-        T s = z[j];
-#pragma unroll
-        for (int k = j + 1; k < 6; ++k) s -= L[k][j] * z[k];
-        z[j] = s * inv[j];
-    }
-    T E = T(0), K1 = T(0), K2 = T(0);
-#pragma unroll
-    for (int a = 0; a < 6; ++a) {
-        E += e[a] * z[a];
-        K1 += k1[a] * z[a];
-        K2 += k2[a] * z[a];
-    }
-    T D[9];
-    D[0] = -E + (s3x * K1 + s3y * K2);
-    D[1] = -K1;
-    D[2] = -K2;
-#pragma unroll
-    for (int a = 0; a < 6; ++a) D[3 + a] = z[a];
-    T h[9];
-    hermite_back(D, h);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) f[i] = g[i] + W[i] * h[i];
-    return kStatusOk;
-}
-
-template <class T, int BASIS>
-__device__ __forceinline__ int collide(const T g[9], uint32_t node, uint32_t step,
-                                       const CollideConst<T>& cc, T f[9]) {
-    uint32_t k[6];
-    draw_fields(node_draw(cc.seed, cc.replica, node, step), k);
-    T N[6];
-    box_muller(k, N);
-    if (BASIS == 0) return collide_standard<T>(g, N, cc, f);
-    return collide_local<T>(g, N, cc, f);
-}
+enum : int { kStatusOk = 0, kStatusInvalidVelocity = 1, kStatusNonfinite = 2, kStatusTimeout = 3 };
 
 }  // namespace flb

@@ -1,0 +1,46 @@
+// flb_internal.h -- interface between the C-ABI translation unit and the
+// pipelined FP32 step kernel (flb_step_tma.cu).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "flb_kernels.cuh"
+
+namespace flb {
+
+struct TmaArgs {
+    float* dst;             // buffer receiving f*(t)
+    Geometry geo;
+    uint32_t step;
+    int tiles_x, ntiles;    // 128 x TH tiles of the lattice
+    double* partials;       // [grid][kSums] per-CTA FP64 sums (sampling)
+    double* acc;            // running FP64 sums (sampling)
+    unsigned int* ticket;   // CTA completion counter, zero between launches
+    DevError* err;
+    float ref[9];           // f^0(rho0, u0) subtracted before sampling
+};
+
+struct TmaPlan {
+    CUtensorMap map[2];     // source tensor maps of buffer 0 and buffer 1
+    int nw;                 // consumer warps per CTA (tile = 128 x nw/2 nodes)
+    int grid;               // persistent CTAs
+    size_t smem;            // dynamic shared memory per CTA
+    int tiles_x, ntiles;
+    bool ready;
+};
+
+// Encode the tensor maps and choose the launch shape for a lattice whose two
+// population buffers are buf0 and buf1. nw = 0 picks the default. Returns
+// cudaSuccess or the error that prevents the pipelined kernel.
+cudaError_t tma_plan(TmaPlan* plan, void* buf0, void* buf1, const Geometry& g, int nw);
+
+// Grid (CTAs) the plan launches with the given consumer-warp count, for sizing
+// the per-CTA partial sums before the buffers exist.
+int tma_max_grid(int sms);
+
+// One fused step from buffer `src` into a.dst. basis: 0 Hermite, 1 f-norm.
+cudaError_t tma_step(const TmaPlan& plan, int src, const TmaArgs& a,
+                     const CollideConst<float>& cc, int basis, bool sample, cudaStream_t s);
+
+}  // namespace flb

@@ -11,6 +11,7 @@
 
 #include <cstdint>
 
+#include "flb_collide.cuh"
 #include "flb_device.cuh"
 #include "flb_layout.cuh"
 
@@ -106,8 +107,9 @@ step_kernel(StepArgs<T> a, CollideConst<T> cc) {
             }
         }
         T f[9];
-        const int st = collide<T, BASIS>(g, (uint32_t)n, a.step, cc, f);
-        if (st != kStatusOk) record_error(a.err, st, n, a.step);
+        const uint32_t st = collide<T, BASIS>(
+            g, [&](T* N) { node_normals(cc.key, (uint32_t)n, a.step, N); }, cc, f);
+        if (st != kStatusOk) record_error(a.err, (int)(st & 0xFF), n, a.step);
         store_node(a.dst, a.geo, x, y, f);
     }
     if (SAMPLE) block_reduce_sums<A>(s, a.partials + (long long)blockIdx.x * kSums);

@@ -23,6 +23,8 @@ OK = 0
 ERR_ARG, ERR_OOM, ERR_INVALID_VELOCITY, ERR_NONFINITE, ERR_TIMEOUT, ERR_CUDA, ERR_STATE = (
     -1, -2, -3, -4, -5, -6, -7)
 BASIS = {"standard": 0, "local": 1}
+OPT_KERNEL, OPT_PIPELINE_WARPS = 0, 1
+KERNEL = {"auto": 0, "generic": 1, "pipelined": 2}
 PRECISION = {"fp64": 0, "fp32": 1, "fp16dev": 2}
 
 
@@ -85,6 +87,7 @@ def load(build_if_missing: bool = True):
         "flb_noise_draws": (C.c_int, [C.c_uint64, C.c_uint32, C.c_uint32, _u32p, C.c_int32,
                                       C.c_int32, _u32p, _dp]),
         "flb_collide_nodes": (C.c_int, [P, _dp, _u32p, C.c_uint32, C.c_int32, _dp, _i32p]),
+        "flb_set_option": (C.c_int, [h, C.c_int32, C.c_int32]),
         "flb_error_string": (C.c_char_p, [C.c_int]),
         "flb_version": (C.c_int, []),
     }
@@ -102,7 +105,7 @@ def exported_symbols():
             "flb_reset_statistics", "flb_step", "flb_sync", "flb_time", "flb_error_location",
             "flb_reset_error", "flb_correlations", "flb_raw_sums", "flb_conservation",
             "flb_get_populations", "flb_set_populations", "flb_run_host", "flb_noise_draws",
-            "flb_collide_nodes", "flb_error_string", "flb_version"]
+            "flb_collide_nodes", "flb_set_option", "flb_error_string", "flb_version"]
 
 
 def _check(rc: int, what: str):
@@ -194,6 +197,10 @@ def flb_time(h) -> int:
     return t.value
 
 
+def flb_set_option(h, option: int, value: int) -> None:
+    _check(load().flb_set_option(h, int(option), int(value)), "flb_set_option")
+
+
 def flb_error_location(h):
     n, s = C.c_int64(), C.c_int64()
     _check(load().flb_error_location(h, C.byref(n), C.byref(s)), "flb_error_location")
@@ -280,9 +287,11 @@ def flb_collide_nodes(p, g, node_ids, step):
 class Lattice:
     """One periodic lattice on the GPU (owns an flb_lattice handle)."""
 
-    def __init__(self, p, workspace=None, stream=None):
+    def __init__(self, p, workspace=None, stream=None, kernel=None):
         self.p = p
         self.h = flb_create(p, workspace, stream)
+        if kernel is not None:
+            flb_set_option(self.h, OPT_KERNEL, KERNEL[kernel] if isinstance(kernel, str) else kernel)
 
     def close(self):
         if self.h is not None:

@@ -165,14 +165,18 @@ def test_fp64_parity_lattice_full_run():
     np.testing.assert_allclose(mean, mean_ref, atol=1e-12)
 
 
+KERNELS = ["generic", "pipelined"]
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("basis", BASES)
-def test_fp32_trajectory(basis):
+def test_fp32_trajectory(basis, kernel):
     """FP32 state and arithmetic against the FP64 oracle, same noise draws."""
-    p = inputs.LatticeParams(64, 48, 1.0, 0.2, 0.0, 1e-4, inputs.omega_groups(1.0, 0.8, 1.0),
+    p = inputs.LatticeParams(200, 48, 1.0, 0.2, 0.0, 1e-4, inputs.omega_groups(1.0, 0.8, 1.0),
                              basis, "fp32", seed=12)
-    nsteps = 1500
+    nsteps = 600
     run = oracle.Run(p, warmup=100, every=1).step(nsteps)
-    with flb.Lattice(p) as lat:
+    with flb.Lattice(p, kernel=kernel) as lat:
         lat.set_sampling(100, 1)
         lat.step(nsteps)
         lat.sync()
@@ -200,6 +204,47 @@ def test_correlation_api_matches_oracle_reduction(basis):
             np.testing.assert_allclose(Cff, C_ref, rtol=1e-8, atol=1e-16)
             np.testing.assert_allclose(CMM, run.moment_covariance(mb), rtol=1e-8, atol=1e-15)
             np.testing.assert_allclose(mean, mean_ref, rtol=1e-8, atol=1e-15)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("shape", [(1, 1), (5, 3), (37, 19), (128, 4), (129, 5), (300, 9)])
+@pytest.mark.parametrize("basis", BASES)
+def test_fp32_kernels_agree_with_oracle_step_by_step(shape, basis, kernel):
+    """Ragged and tiny lattices (partial tiles, ghost frame on every side): a few
+    steps of either FP32 kernel against the oracle from a perturbed state, with
+    sampling on every step."""
+    Lx, Ly = shape
+    p = inputs.LatticeParams(Lx, Ly, 1.0, 0.15, -0.1, 1e-3, inputs.omega_groups(1.3, 0.8, 1.6),
+                             basis, "fp32", seed=40 + Lx)
+    f_init = _perturbed_state(p, seed=Lx + 7 * Ly)
+    run = oracle.Run(p, f=f_init, warmup=0, every=1).step(5)
+    with flb.Lattice(p, kernel=kernel) as lat:
+        lat.set_populations(f_init)
+        lat.set_sampling(0, 1)
+        lat.step(5)
+        lat.sync()
+        f = lat.populations()
+        S1, S2, n = lat.raw_sums()
+    assert np.abs(f - run.f).max() < 2e-6
+    assert n == run.nsamp
+    np.testing.assert_allclose(S2, run.S2, rtol=2e-4, atol=1e-9 * n)
+    np.testing.assert_allclose(S1, run.S1, rtol=2e-4, atol=1e-7 * n)
+
+
+@pytest.mark.parametrize("basis", BASES)
+def test_pipelined_equals_generic_fp32(basis):
+    """Both FP32 kernels compute the same thing (same draws, same algebra) on a
+    lattice of many tiles with a ragged edge: populations agree to FP32 rounding."""
+    p = inputs.LatticeParams(1000, 77, 1.0, 0.1, 0.02, 1e-4, inputs.omega_groups(1.0, 0.8, 1.0),
+                             basis, "fp32", seed=9)
+    out = {}
+    for kernel in KERNELS:
+        with flb.Lattice(p, kernel=kernel) as lat:
+            lat.set_sampling(2, 1)
+            lat.step(30)
+            out[kernel] = (lat.populations(), lat.raw_sums())
+    assert np.abs(out["generic"][0] - out["pipelined"][0]).max() < 1e-6
+    np.testing.assert_allclose(out["generic"][1][1], out["pipelined"][1][1], rtol=1e-4)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
@@ -254,14 +299,15 @@ def test_run_host_matches_handle_path():
     np.testing.assert_allclose(S2, run.S2, rtol=1e-9, atol=1e-20)
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("basis", BASES)
-def test_full_size_sampled_nodes(basis):
+def test_full_size_sampled_nodes(basis, kernel):
     """4096^2 FP32, the benchmark's configuration and launch: after 20 steps one
     more step is checked at sampled nodes against the oracle's collision of the
     same pre-collision populations (pull streaming checked by position)."""
     p = inputs.single_lattice(0.1, basis)
     Lx, Ly = p.Lx, p.Ly
-    with flb.Lattice(p) as lat:
+    with flb.Lattice(p, kernel=kernel) as lat:
         lat.step(20)
         F0 = lat.populations()
         lat.step(1)
