@@ -33,7 +33,7 @@ BYTES_PER_NODE = {"fp32": 72, "fp64": 144}
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--basis", default="local", choices=["local", "standard"])
@@ -42,6 +42,12 @@ def parse():
     ap.add_argument("--side", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--pipeline-warps", type=int, default=0,
+                    help="consumer warps of the pipelined FP32 kernel (8 or 12; 0 = library default)")
+    ap.add_argument("--pipeline-sampling", type=int, default=0,
+                    help="1: sampler warps, 2: sums fused into the colliding warps (0 = default)")
+    ap.add_argument("--sample-every", type=int, default=1,
+                    help="sample the correlations every k steps (1 = every step, the workload)")
     return ap.parse_args()
 
 
@@ -201,8 +207,10 @@ def main():
     p.seed = p.seed + 7919 * rank
     nodes = p.Lx * p.Ly
     stream = torch.cuda.Stream(device=dev)
-    lat = flb.Lattice(p, stream=stream)
-    lat.set_sampling(0, 1)                # sample (and reduce) every step
+    lat = flb.Lattice(p, stream=stream,
+                      pipeline_warps=args.pipeline_warps if args.pipeline_warps else None,
+                      pipeline_sampling=args.pipeline_sampling if args.pipeline_sampling else None)
+    lat.set_sampling(0, args.sample_every)   # sample (and reduce) every step by default
 
     # warm-up
     lat.step(args.warmup)

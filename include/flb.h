@@ -184,10 +184,14 @@ int flb_collide_nodes(const flb_params* p, const double* g, const uint32_t* node
  *    FLB_KERNEL_GENERIC (one node per thread, plain loads) or
  *    FLB_KERNEL_PIPELINED (FP32 only). All give the same results up to rounding.
  *  FLB_OPT_PIPELINE_WARPS: consumer warps per CTA of the pipelined kernel
- *    (4 or 8; the tile is 128 x value/2 nodes). FP32 only.
+ *    (8 or 12; the tile is 128 x value/2 nodes). FP32 only.
+ *  FLB_OPT_PIPELINE_SAMPLING: how the pipelined kernel accumulates the
+ *    correlation sums on sampling steps -- 1 (default): dedicated sampler warps
+ *    read the staged tile; 2: the colliding warps accumulate their own nodes.
  * Errors: FLB_ERR_ARG for an unknown option or value. */
 #define FLB_OPT_KERNEL 0
 #define FLB_OPT_PIPELINE_WARPS 1
+#define FLB_OPT_PIPELINE_SAMPLING 2
 #define FLB_KERNEL_AUTO 0
 #define FLB_KERNEL_GENERIC 1
 #define FLB_KERNEL_PIPELINED 2

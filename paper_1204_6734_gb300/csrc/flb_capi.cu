@@ -18,12 +18,8 @@ namespace flb {
 // ---------------------------------------------------------------------------
 
 __global__ void accumulate_partials_kernel(const double* partials, int nblocks, double* acc) {
-    // one thread per sum, blocks summed in index order: deterministic
-    const int k = threadIdx.x;
-    if (k >= kSums) return;
-    double t = 0.0;
-    for (int b = 0; b < nblocks; ++b) t += partials[(long long)b * kSums + k];
-    acc[k] += t;
+    const double v = reduce_partials(partials, blockIdx.x, nblocks, threadIdx.x);
+    if (threadIdx.x == 0) acc[blockIdx.x] += v;
 }
 
 // Rows of the basis the correlations are measured in: the Hermite rows
@@ -503,6 +499,7 @@ int flb_create(const flb_params* p, void* dev_workspace, size_t workspace_bytes,
         ce = cudaGetLastError();
     }
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
+    h->tma.sample_mode = 0;   // library default
     if (ce == cudaSuccess && p->precision == FLB_FP32)
         ce = tma_plan(&h->tma, h->buf[0], h->buf[1], h->geo, 0);
     if (ce != cudaSuccess) {
@@ -548,7 +545,8 @@ int flb_step(flb_lattice h, int64_t n) {
             h->every > 0 && h->t >= h->warmup && ((h->t - h->warmup) % h->every) == 0;
         cudaError_t ce = launch_step(h, sample);
         if (ce == cudaSuccess && sample && !uses_tma(h)) {
-            accumulate_partials_kernel<<<1, 64, 0, h->stream>>>(h->partials, h->nblocks, h->acc);
+            accumulate_partials_kernel<<<kSums, 32, 0, h->stream>>>(h->partials, h->nblocks,
+                                                                     h->acc);
             ce = cudaGetLastError();
         }
         if (sample) h->nsamp += N;
@@ -568,9 +566,15 @@ int flb_set_option(flb_lattice h, int32_t option, int32_t value) {
         h->variant = value;
         return FLB_OK;
     }
+    if (option == FLB_OPT_PIPELINE_SAMPLING) {
+        if (h->p.precision != FLB_FP32 || (value != 1 && value != 2)) return FLB_ERR_ARG;
+        h->tma.sample_mode = value;
+        return FLB_OK;
+    }
     if (option == FLB_OPT_PIPELINE_WARPS) {
         if (h->p.precision != FLB_FP32) return FLB_ERR_ARG;
         TmaPlan plan;
+        plan.sample_mode = h->tma.sample_mode;
         const cudaError_t ce = tma_plan(&plan, h->buf[0], h->buf[1], h->geo, value);
         if (ce != cudaSuccess) {
             cudaGetLastError();

@@ -147,6 +147,19 @@ template <class V, int BASIS, class Noise>
 __device__ __forceinline__ uint32_t collide(const V g[9], Noise noise,
                                             const CollideConst<typename Elem<V>::type>& cc,
                                             V f[9]) {
+    return collide<V, BASIS>(g, noise, [&](V* gg) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) gg[i] = g[i];
+    }, cc, f);
+}
+
+// As above; refetch(gg) supplies g again for the final f = g + W h, so the
+// caller may drop g from registers in between (the pipelined kernel re-reads
+// it from shared memory).
+template <class V, int BASIS, class Noise, class Refetch>
+__device__ __forceinline__ uint32_t collide(const V g[9], Noise noise, Refetch refetch,
+                                            const CollideConst<typename Elem<V>::type>& cc,
+                                            V f[9]) {
     using S = typename Elem<V>::type;
     // density, momentum, velocity
     const V s13 = g[1] + g[3], s24 = g[2] + g[4];
@@ -184,29 +197,35 @@ __device__ __forceinline__ uint32_t collide(const V g[9], Noise noise,
         for (int a = 0; a < 6; ++a) Dn[a] = mad(V(cc.nomega[a]), M[a], (sr * N[a]) * V(cc.amp[a]));
         V h[9];
         hermite_back<V, false>(V(S(0)), V(S(0)), V(S(0)), Dn, h);
-        f[0] = mad(h[0], V(S(4.0 / 9.0)), g[0]);
+        V gg[9];
+        refetch(gg);
+        f[0] = mad(h[0], V(S(4.0 / 9.0)), gg[0]);
 #pragma unroll
-        for (int i = 1; i <= 4; ++i) f[i] = mad(h[i], V(S(1.0 / 9.0)), g[i]);
+        for (int i = 1; i <= 4; ++i) f[i] = mad(h[i], V(S(1.0 / 9.0)), gg[i]);
 #pragma unroll
-        for (int i = 5; i <= 8; ++i) f[i] = mad(h[i], V(S(1.0 / 36.0)), g[i]);
+        for (int i = 5; i <= 8; ++i) f[i] = mad(h[i], V(S(1.0 / 36.0)), gg[i]);
         const uint32_t st = lane_status(rho, rho, false);
-        keep_invalid(st, g, f);
+        keep_invalid(st, gg, f);
         return st;
     }
 
-    // rows of L below the conserved block: e, k1, k2 (zero entries omitted)
+    // rows of L below the conserved block: -e, k1, k2 (zero entries omitted);
+    // cheap to rebuild from u, so they are recomputed where needed instead of
+    // being kept in registers across the factorisation
     const V s3x = ux * V(S(kSqrt3)), s3y = uy * V(S(kSqrt3));
-    const V base = mad(usq, V(S(-1.5)), V(S(1)));   // 1 - e5
-    const V k1_0 = s3x * mad(t3, V(S(-1.5)), V(S(1)));
-    const V k1_1 = s3y * mad(uxx, V(S(-3)), V(S(1)));
-    const V k1_2 = s3x * base;
-    const V k1_3 = uyy * V(S(kSqrt2x3h));
-    const V k1_4 = uxy * V(S(kSqrt2x3));
-    const V k2_0 = s3y * mad(t3, V(S(-1.5)), V(S(-1)));
-    const V k2_1 = s3x * mad(uyy, V(S(-3)), V(S(1)));
-    const V k2_2 = s3y * base;
-    const V k2_3 = k1_4;
-    const V k2_4 = uxx * V(S(kSqrt2x3h));
+    auto rows = [&](V k1[5], V k2[5]) {
+        const V base = mad(usq, V(S(-1.5)), V(S(1)));   // 1 - e5
+        k1[0] = s3x * mad(t3, V(S(-1.5)), V(S(1)));
+        k1[1] = s3y * mad(uxx, V(S(-3)), V(S(1)));
+        k1[2] = s3x * base;
+        k1[3] = uyy * V(S(kSqrt2x3h));
+        k1[4] = uxy * V(S(kSqrt2x3));
+        k2[0] = s3y * mad(t3, V(S(-1.5)), V(S(-1)));
+        k2[1] = s3x * mad(uyy, V(S(-3)), V(S(1)));
+        k2[2] = s3y * base;
+        k2[3] = k1[4];
+        k2[4] = uxx * V(S(kSqrt2x3h));
+    };
 
     // Sn = -(G_NN - e e^T - k1 k1^T - k2 k2^T), upper triangle
     V Sn[6][6];
@@ -237,8 +256,8 @@ __device__ __forceinline__ uint32_t collide(const V g[9], Noise noise,
         Sn[4][5] = n6y;
         Sn[5][5] = mad(usq, V(S(-1.5)), V(S(-1)));
         const V e[3] = {ne3, ne4, ne5};   // e_a e_b = ne_a ne_b
-        const V k1[5] = {k1_0, k1_1, k1_2, k1_3, k1_4};
-        const V k2[5] = {k2_0, k2_1, k2_2, k2_3, k2_4};
+        V k1[5], k2[5];
+        rows(k1, k2);
 #pragma unroll
         for (int a = 0; a < 5; ++a)
 #pragma unroll
@@ -291,8 +310,10 @@ __device__ __forceinline__ uint32_t collide(const V g[9], Noise noise,
         z[j] = s * inv[j];
     }
     const V nE = mad(ne3, z[0], mad(ne4, z[1], ne5 * z[2]));
-    const V K1 = mad(k1_0, z[0], mad(k1_1, z[1], mad(k1_2, z[2], mad(k1_3, z[3], k1_4 * z[4]))));
-    const V K2 = mad(k2_0, z[0], mad(k2_1, z[1], mad(k2_2, z[2], mad(k2_3, z[3], k2_4 * z[4]))));
+    V k1[5], k2[5];
+    rows(k1, k2);
+    const V K1 = mad(k1[0], z[0], mad(k1[1], z[1], mad(k1[2], z[2], mad(k1[3], z[3], k1[4] * z[4]))));
+    const V K2 = mad(k2[0], z[0], mad(k2[1], z[1], mad(k2[2], z[2], mad(k2[3], z[3], k2[4] * z[4]))));
     const V D0 = mad(s3x, K1, mad(s3y, K2, nE));
     V h[9];
     hermite_back<V, true>(D0, K1, K2, z, h);
@@ -317,10 +338,12 @@ __device__ __forceinline__ uint32_t collide(const V g[9], Noise noise,
         W[6] = mad(smy, V(S(-1.0 / 12.0)), tm);
     }
 
+    V gg[9];
+    refetch(gg);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) f[i] = mad(W[i], h[i], g[i]);
+    for (int i = 0; i < 9; ++i) f[i] = mad(W[i], h[i], gg[i]);
     const uint32_t st = lane_status(rho, invsum, true);
-    keep_invalid(st, g, f);
+    keep_invalid(st, gg, f);
     return st;
 }
 

@@ -27,6 +27,7 @@ struct TmaPlan {
     int grid;               // persistent CTAs
     size_t smem;            // dynamic shared memory per CTA
     int tiles_x, ntiles;
+    int sample_mode;        // sampling steps: 1 sampler warps, 2 fused into the consumers
     bool ready;
 };
 

@@ -115,7 +115,20 @@ step_kernel(StepArgs<T> a, CollideConst<T> cc) {
     if (SAMPLE) block_reduce_sums<A>(s, a.partials + (long long)blockIdx.x * kSums);
 }
 
-// Sum the per-block partials in a fixed order into the running FP64 sums.
+// Sum over blocks of partials[b * kSums + q], computed by one warp: lane l adds
+// blocks l, l + 32, ... in order, then a fixed butterfly combines the lanes, so
+// the result does not depend on timing. All lanes return the total.
+__device__ __forceinline__ double reduce_partials(const double* partials, int q, int nblocks,
+                                                  int lane) {
+    double s = 0.0;
+    for (int b = lane; b < nblocks; b += 32) s += __ldcg(&partials[(size_t)b * kSums + q]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+// Adds the per-block partials into the running FP64 sums; block q, one warp,
+// handles sum q.
 __global__ void accumulate_partials_kernel(const double* partials, int nblocks, double* acc);
 
 // C = S2/n - m m^T, m = S1/n, and CM = B C B^T for the measurement basis B.

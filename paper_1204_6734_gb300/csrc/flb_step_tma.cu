@@ -30,17 +30,23 @@ namespace flb {
 
 constexpr int kTW = 128;               // tile width (nodes)
 constexpr int kBoxW = kTW + 8;         // TMA box width: x0 - 4 .. x0 + 131
-constexpr int kStages = 4;
 constexpr int kDefaultNW = 8;
+constexpr int kSamplers = 4;   // sampler warps: one per SM sub-partition
+constexpr int kDefaultSampling = 1;   // kSamplerWarps
 
+// Tile of 128 x TH nodes, TH = NW / 2; the ring holds STAGES tiles. The ring
+// must be deep: a stage is in flight from HBM only between its refill and its
+// arrival, and consumers keep their stage until they have finished the tile.
 template <int NW>
 struct TileShape {
     static constexpr int TH = NW / 2;                                  // rows per tile
     static constexpr int SPLANE = (TH * kBoxW + 31) / 32 * 32;         // floats per plane box
     static constexpr int STAGE = 9 * SPLANE;                           // floats per stage
+    static constexpr int STAGES = NW <= 8 ? 8 : 6;                     // 157 / 176 KB
+    static constexpr int RED = NW > kSamplers ? NW : kSamplers;        // warps reducing
     static constexpr size_t smem_bytes() {
-        return sizeof(float) * (size_t)kStages * STAGE + 2 * kStages * sizeof(uint64_t) +
-               sizeof(double) * TH * kSums + 16;
+        return sizeof(float) * (size_t)STAGES * STAGE + 2 * STAGES * sizeof(uint64_t) +
+               sizeof(double) * RED * kSums + 16;
     }
 };
 
@@ -65,28 +71,126 @@ __device__ __forceinline__ void issue_tile(float* smem, const CUtensorMap* map, 
                     i * (a.geo.Ly + 2) + y0 + 1 - cvy(i), &full[s]);
 }
 
-// Warp roles: warps [0, NW) collide (consumers); warps [NW, NW + NS) are the
-// producer (NS = 1, no sampling) or, with sampling, NS = TH sampler warps --
-// sampler w accumulates the correlation sums of row w of every tile -- whose
-// first lane is also the producer.
-template <int BASIS, bool SAMPLE, int NW>
-__global__ void __launch_bounds__((NW + (SAMPLE ? NW / 2 : 1)) * 32, 1)
+// Producer state of an elected thread that refills each stage once every warp
+// has released it. Stage s holds tiles s, s + STAGES, ... of this CTA.
+template <int NW>
+struct Producer {
+    int issued = 0;
+    bool ok = true;
+
+    __device__ __forceinline__ void prologue(float* smem, const CUtensorMap* map,
+                                             const TmaArgs& a, uint64_t* full) {
+        prefetch_tensormap(map);
+        for (int t = blockIdx.x; t < a.ntiles && issued < TileShape<NW>::STAGES;
+             t += gridDim.x, ++issued)
+            issue_tile<NW>(smem, map, a, t, issued, full);
+    }
+    // after this CTA's k-th tile (stage s, use n) was released by the caller
+    __device__ __forceinline__ void refill(float* smem, const CUtensorMap* map, const TmaArgs& a,
+                                           uint64_t* full, uint64_t* empty, int s, int n) {
+        if (!ok) return;
+        const int tn = blockIdx.x + issued * gridDim.x;
+        if (tn >= a.ntiles) return;
+        if (!mbar_wait(&empty[s], n & 1)) {
+            record_error(a.err, kStatusTimeout, -1, a.step);
+            ok = false;
+            return;
+        }
+        issue_tile<NW>(smem, map, a, tn, s, full);
+        ++issued;
+    }
+    // no copy may be in flight when the CTA exits: wait for tiles issued but not
+    // consumed by the caller's loop (only after a timeout)
+    __device__ __forceinline__ void drain(const TmaArgs& a, uint64_t* full, int consumed) {
+        constexpr int S = TileShape<NW>::STAGES;
+        for (int j = issued > S ? issued - S : 0; j < issued; ++j)
+            if (j >= consumed && !mbar_wait(&full[j % S], (j / S) & 1)) {
+                record_error(a.err, kStatusTimeout, -1, a.step);
+                break;
+            }
+    }
+};
+
+// CTA and grid reduction of per-thread correlation sums held by `group`
+// threads (warps [w0, w0 + group/32)): warp shuffles, FP64 across warps into
+// this CTA's partials, then the last CTA to finish adds all CTA partials in a
+// fixed order to the running sums.
+__device__ __forceinline__ void publish_sums(const float (&v)[kSums], int w0, int group,
+                                             double* red, int* flag, const TmaArgs& a) {
+    const int warp = threadIdx.x >> 5, lane_id = threadIdx.x & 31;
+    const int nw = group / 32, c = threadIdx.x - 32 * w0;
+#pragma unroll
+    for (int q = 0; q < kSums; ++q) {
+        float x = v[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane_id == 0) red[(warp - w0) * kSums + q] = (double)x;
+    }
+    named_sync(1, group);
+    if (c < kSums) {
+        double tot = 0.0;
+        for (int w = 0; w < nw; ++w) tot += red[w * kSums + c];
+        a.partials[(size_t)blockIdx.x * kSums + c] = tot;
+    }
+    __threadfence();
+    named_sync(1, group);
+    if (c == 0) *flag = (atomicAdd(a.ticket, 1u) == gridDim.x - 1) ? 1 : 0;
+    named_sync(1, group);
+    if (*flag) {
+        __threadfence();
+        for (int q = warp - w0; q < kSums; q += nw) {
+            const double s = reduce_partials(a.partials, q, gridDim.x, lane_id);
+            if (lane_id == 0) a.acc[q] += s;
+        }
+        if (c == 0) *a.ticket = 0u;
+    }
+}
+
+// Correlation sums of two nodes (lanes of d, already centred and masked).
+__device__ __forceinline__ void add_sums(float (&v)[kSums], const f2 (&d)[9]) {
+    int q = 9;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        v[i] += d[i].v.x + d[i].v.y;
+#pragma unroll
+        for (int j = i; j < 9; ++j, ++q) v[q] = fmaf(d[i].v.x, d[j].v.x, fmaf(d[i].v.y, d[j].v.y, v[q]));
+    }
+}
+
+// Sampling modes of the pipelined step.
+enum : int { kNoSampling = 0, kSamplerWarps = 1, kFusedSampling = 2 };
+
+template <int MODE>
+struct WarpCount {
+    template <int NW>
+    static constexpr int extra() { return MODE == kSamplerWarps ? kSamplers : (MODE == kFusedSampling ? 0 : 1); }
+};
+
+// Warp roles. kNoSampling: NW consumer warps + one producer warp.
+// kSamplerWarps: NW consumers + kSamplers sampler warps (sampler w reads rows
+// w, w + kSamplers, ... of each tile from the same stage and accumulates the
+// sums in packed registers); the first sampler lane produces.
+// kFusedSampling: NW consumers that also accumulate the sums of their own
+// nodes; lane 0 of warp 0 produces.
+template <int BASIS, int MODE, int NW>
+__global__ void __launch_bounds__((NW + WarpCount<MODE>::template extra<NW>()) * 32, 1)
 step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
                 const CollideConst<float> cc) {
     using TS = TileShape<NW>;
     constexpr int TH = TS::TH;
-    constexpr int NS = SAMPLE ? TH : 1;
+    constexpr int kStages = TS::STAGES;
+    constexpr int NX = WarpCount<MODE>::template extra<NW>();
     extern __shared__ __align__(128) float smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * TS::STAGE);
     uint64_t* empty = full + kStages;
     double* red = reinterpret_cast<double*>(empty + kStages);
-    int* flag = reinterpret_cast<int*>(red + TH * kSums);
+    int* flag = reinterpret_cast<int*>(red + TS::RED * kSums);
 
     const int warp = threadIdx.x >> 5, lane_id = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], NW + (SAMPLE ? NS : 0));
+            mbar_init(&empty[s], NW + (MODE == kSamplerWarps ? NX : 0));
         }
         fence_mbar_init();
     }
@@ -94,40 +198,25 @@ step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
 
     const int Lx = a.geo.Lx, Ly = a.geo.Ly;
 
-    if (!SAMPLE && warp == NW) {
+    if (MODE == kNoSampling && warp == NW) {
         // ---------------- producer warp
         if (lane_id == 0) {
-            prefetch_tensormap(&map);
+            Producer<NW> prod;
+            prod.prologue(smem, &map, a, full);
             int k = 0;
-            for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++k) {
-                const int s = k % kStages, n = k / kStages;
-                if (n > 0 && !mbar_wait(&empty[s], (n - 1) & 1)) {
-                    record_error(a.err, kStatusTimeout, -1, a.step);
-                    break;
-                }
-                issue_tile<NW>(smem, &map, a, t, s, full);
-            }
-            // no copy may still be in flight when the CTA exits
-            for (int j = k > kStages ? k - kStages : 0; j < k; ++j)
-                if (!mbar_wait(&full[j % kStages], (j / kStages) & 1)) {
-                    record_error(a.err, kStatusTimeout, -1, a.step);
-                    break;
-                }
+            for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++k)
+                prod.refill(smem, &map, a, full, empty, k % kStages, k / kStages);
+            prod.drain(a, full, prod.issued);
         }
         return;
     }
 
-    if (SAMPLE && warp >= NW) {
-        // ---------------- samplers (first lane of the first one also produces)
-        const int row = warp - NW;
-        const bool producer = row == 0 && lane_id == 0;
-        int issued = 0;
-        bool ok = true;
-        if (producer) {
-            prefetch_tensormap(&map);
-            for (int t = blockIdx.x; t < a.ntiles && issued < kStages; t += gridDim.x, ++issued)
-                issue_tile<NW>(smem, &map, a, t, issued, full);
-        }
+    if (MODE == kSamplerWarps && warp >= NW) {
+        // ---------------- sampler warps
+        const int sw = warp - NW;
+        const bool producer = sw == 0 && lane_id == 0;
+        Producer<NW> prod;
+        if (producer) prod.prologue(smem, &map, a, full);
         f2 s1[9], s2[45];
 #pragma unroll
         for (int q = 0; q < 9; ++q) s1[q] = f2(0.f);
@@ -138,94 +227,72 @@ step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
             const int s = k % kStages, n = k / kStages;
             if (!mbar_wait(&full[s], n & 1)) {
                 record_error(a.err, kStatusTimeout, -1, a.step);
-                ok = false;
                 break;
             }
-            const int x0 = (t % a.tiles_x) * kTW, y = (t / a.tiles_x) * TH + row;
-            const float* st = smem + s * TS::STAGE + row * kBoxW + 4 + lane_id;
+            const int x0 = (t % a.tiles_x) * kTW;
+            for (int row = sw; row < TH; row += NX) {
+                const int y = (t / a.tiles_x) * TH + row;
+                const float* st = smem + s * TS::STAGE + row * kBoxW + 4 + lane_id;
+                f2 d[2][9];
 #pragma unroll
-            for (int p = 0; p < 2; ++p) {
-                const int xA = x0 + lane_id + 64 * p;
-                const bool inA = xA < Lx && y < Ly, inB = xA + 32 < Lx && y < Ly;
-                f2 d[9];
+                for (int p = 0; p < 2; ++p)
 #pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    const float* q = st + i * TS::SPLANE - cvx(i) + 64 * p;
-                    d[i] = f2(q[0], q[32]) - f2(a.ref[i]);
+                    for (int i = 0; i < 9; ++i) {
+                        const float* q = st + i * TS::SPLANE - cvx(i) + 64 * p;
+                        d[p][i] = f2(q[0], q[32]);
+                    }
+                if (row + NX >= TH) {   // last row: release before the arithmetic
+                    __syncwarp();
+                    if (lane_id == 0) mbar_arrive(&empty[s]);
                 }
-                if (!(inA && inB)) {
 #pragma unroll
-                    for (int i = 0; i < 9; ++i)
-                        d[i] = f2(inA ? d[i].v.x : 0.f, inB ? d[i].v.y : 0.f);
-                }
-                int q = 0;
+                for (int p = 0; p < 2; ++p) {
+                    const int xA = x0 + lane_id + 64 * p;
+                    const bool inA = xA < Lx && y < Ly, inB = xA + 32 < Lx && y < Ly;
 #pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    s1[i] += d[i];
+                    for (int i = 0; i < 9; ++i) {
+                        f2 e = d[p][i] - f2(a.ref[i]);
+                        if (!(inA && inB)) e = f2(inA ? e.v.x : 0.f, inB ? e.v.y : 0.f);
+                        d[p][i] = e;
+                    }
+                    int q = 0;
 #pragma unroll
-                    for (int j = i; j < 9; ++j, ++q) s2[q] = mad(d[i], d[j], s2[q]);
-                }
-            }
-            __syncwarp();
-            if (lane_id == 0) mbar_arrive(&empty[s]);
-            if (producer && ok) {
-                // refill this stage with the tile kStages ahead once every warp released it
-                const int tn = blockIdx.x + issued * gridDim.x;
-                if (tn < a.ntiles) {
-                    if (!mbar_wait(&empty[s], n & 1)) {
-                        record_error(a.err, kStatusTimeout, -1, a.step);
-                        ok = false;
-                    } else {
-                        issue_tile<NW>(smem, &map, a, tn, s, full);
-                        ++issued;
+                    for (int i = 0; i < 9; ++i) {
+                        s1[i] += d[p][i];
+#pragma unroll
+                        for (int j = i; j < 9; ++j, ++q) s2[q] = mad(d[p][i], d[p][j], s2[q]);
                     }
                 }
             }
+            if (sw >= TH) {   // a sampler without a row in this tile
+                __syncwarp();
+                if (lane_id == 0) mbar_arrive(&empty[s]);
+            }
+            if (producer) prod.refill(smem, &map, a, full, empty, s, n);
         }
-        if (producer)   // no copy may still be in flight when the CTA exits
-            for (int j = issued > kStages ? issued - kStages : 0; j < issued; ++j)
-                if (j >= k && !mbar_wait(&full[j % kStages], (j / kStages) & 1)) {
-                    record_error(a.err, kStatusTimeout, -1, a.step);
-                    break;
-                }
-
-        // CTA reduction: lanes (warp shuffles), then samplers in FP64
+        if (producer) prod.drain(a, full, k);
+        float v[kSums];
 #pragma unroll
         for (int q = 0; q < kSums; ++q) {
-            const f2 v2 = q < 9 ? s1[q] : s2[q - 9];
-            float v = v2.v.x + v2.v.y;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane_id == 0) red[row * kSums + q] = (double)v;
+            const f2 x = q < 9 ? s1[q] : s2[q - 9];
+            v[q] = x.v.x + x.v.y;
         }
-        const int c = threadIdx.x - NW * 32;   // 0 .. 32 NS - 1
-        named_sync(1, NS * 32);
-        if (c < kSums) {
-            double tot = 0.0;
-            for (int w = 0; w < NS; ++w) tot += red[w * kSums + c];
-            a.partials[(size_t)blockIdx.x * kSums + c] = tot;
-        }
-        // grid: the last CTA to finish adds every CTA's partial, in CTA order
-        __threadfence();
-        named_sync(1, NS * 32);
-        if (c == 0) *flag = (atomicAdd(a.ticket, 1u) == gridDim.x - 1) ? 1 : 0;
-        named_sync(1, NS * 32);
-        if (*flag) {
-            __threadfence();
-            if (c < kSums) {
-                double tot = 0.0;
-                for (unsigned b = 0; b < gridDim.x; ++b)
-                    tot += __ldcg(&a.partials[(size_t)b * kSums + c]);
-                a.acc[c] += tot;
-            }
-            if (c == 0) *a.ticket = 0u;
-        }
+        publish_sums(v, NW, NX * 32, red, flag, a);
         return;
     }
 
     // ---------------- consumers: two nodes per thread, packed FP32x2
     const int c = threadIdx.x;          // 0 .. 32 NW - 1
     const int ty = c >> 6, r = c & 63;
+    constexpr bool kFused = MODE == kFusedSampling;
+    const bool producer = kFused && c == 0;
+    Producer<NW> prod;
+    if (producer) prod.prologue(smem, &map, a, full);
+    float v[kFused ? kSums : 1];
+    if (kFused) {
+#pragma unroll
+        for (int q = 0; q < kSums; ++q) v[q] = 0.f;
+    }
     int k = 0;
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++k) {
         const int s = k % kStages, n = k / kStages;
@@ -234,22 +301,36 @@ step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
             break;
         }
         const float* st = smem + s * TS::STAGE + ty * kBoxW + 4 + r;
-        f2 g[9];
+        auto load = [&](f2* g) {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const float* p = st + i * TS::SPLANE - cvx(i);
-            g[i] = f2(p[0], p[64]);
-        }
-        __syncwarp();
-        if (lane_id == 0) mbar_arrive(&empty[s]);
+            for (int i = 0; i < 9; ++i) {
+                const float* p = st + i * TS::SPLANE - cvx(i);
+                g[i] = f2(p[0], p[64]);
+            }
+        };
+        f2 g[9];
+        load(g);
 
         const int x0 = (t % a.tiles_x) * kTW, y = (t / a.tiles_x) * TH + ty;
         const int xA = x0 + r, xB = xA + 64;
         const bool inA = xA < Lx && y < Ly, inB = xB < Lx && y < Ly;
+        if (kFused) {
+            f2 d[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                f2 e = g[i] - f2(a.ref[i]);
+                if (!(inA && inB)) e = f2(inA ? e.v.x : 0.f, inB ? e.v.y : 0.f);
+                d[i] = e;
+            }
+            add_sums(reinterpret_cast<float(&)[kSums]>(v), d);
+        }
         const uint32_t nodeA = (uint32_t)xA + (uint32_t)Lx * (uint32_t)y;
         f2 f[9];
         const uint32_t stt = collide<f2, BASIS>(
-            g, [&](f2* N) { node_normals(cc.key, nodeA, nodeA + 64u, a.step, N); }, cc, f);
+            g, [&](f2* N) { node_normals(cc.key, nodeA, nodeA + 64u, a.step, N); }, load, cc, f);
+        // the stage is held until g was read the second time
+        __syncwarp();
+        if (lane_id == 0) mbar_arrive(&empty[s]);
         if (inA) {
             if (stt & 0xFF) record_error(a.err, (int)(stt & 0xFF), nodeA, a.step);
             store_lane(a, xA, y, f, 0);
@@ -258,6 +339,11 @@ step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
             if (stt >> 8) record_error(a.err, (int)(stt >> 8), nodeA + 64u, a.step);
             store_lane(a, xB, y, f, 1);
         }
+        if (producer) prod.refill(smem, &map, a, full, empty, s, n);
+    }
+    if (kFused) {
+        if (producer) prod.drain(a, full, k);
+        publish_sums(reinterpret_cast<float(&)[kSums]>(v), 0, NW * 32, red, flag, a);
     }
 }
 
@@ -289,27 +375,35 @@ EncodeFn encode_fn() {
     return fn;
 }
 
-template <int NW>
-const void* kernel_ptr(int basis, bool sample) {
-    if (basis == 0)
-        return sample ? (const void*)step_tma_kernel<0, true, NW>
-                      : (const void*)step_tma_kernel<0, false, NW>;
-    return sample ? (const void*)step_tma_kernel<1, true, NW>
-                  : (const void*)step_tma_kernel<1, false, NW>;
+template <int NW, int MODE>
+const void* kernel_ptr_m(int basis) {
+    return basis == 0 ? (const void*)step_tma_kernel<0, MODE, NW>
+                      : (const void*)step_tma_kernel<1, MODE, NW>;
 }
 
-const void* kernel_for(int nw, int basis, bool sample) {
+template <int NW>
+const void* kernel_ptr(int basis, int mode) {
+    if (mode == kSamplerWarps) return kernel_ptr_m<NW, kSamplerWarps>(basis);
+    if (mode == kFusedSampling) return kernel_ptr_m<NW, kFusedSampling>(basis);
+    return kernel_ptr_m<NW, kNoSampling>(basis);
+}
+
+const void* kernel_for(int nw, int basis, int mode) {
     switch (nw) {
-        case 4: return kernel_ptr<4>(basis, sample);
-        case 8: return kernel_ptr<8>(basis, sample);
+        case 8: return kernel_ptr<8>(basis, mode);
+        case 12: return kernel_ptr<12>(basis, mode);
         default: return nullptr;
     }
 }
 
+int warps_for(int nw, int mode) {
+    return nw + (mode == kSamplerWarps ? kSamplers : (mode == kFusedSampling ? 0 : 1));
+}
+
 size_t smem_for(int nw) {
     switch (nw) {
-        case 4: return TileShape<4>::smem_bytes();
         case 8: return TileShape<8>::smem_bytes();
+        case 12: return TileShape<12>::smem_bytes();
         default: return 0;
     }
 }
@@ -321,7 +415,7 @@ int tma_max_grid(int sms) { return sms * 2; }
 cudaError_t tma_plan(TmaPlan* plan, void* buf0, void* buf1, const Geometry& g, int nw) {
     plan->ready = false;
     if (nw == 0) nw = kDefaultNW;
-    if (!kernel_for(nw, 0, false)) return cudaErrorInvalidValue;
+    if (!kernel_for(nw, 0, kNoSampling)) return cudaErrorInvalidValue;
     EncodeFn enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
     const int th = nw / 2;
@@ -341,17 +435,19 @@ cudaError_t tma_plan(TmaPlan* plan, void* buf0, void* buf1, const Geometry& g, i
     int dev = 0, sms = 0;
     cudaError_t ce = cudaGetDevice(&dev);
     if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int per_sm = 2;
     for (int basis = 0; basis < 2 && ce == cudaSuccess; ++basis)
-        for (int sample = 0; sample < 2 && ce == cudaSuccess; ++sample)
-            ce = cudaFuncSetAttribute(kernel_for(nw, basis, sample != 0),
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int per_sm = 0;
-    if (ce == cudaSuccess)
-        ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel_for(nw, 1, true),
-                                                           (nw + nw / 2) * 32, smem);
+        for (int mode = 0; mode < 3 && ce == cudaSuccess; ++mode) {
+            const void* fn = kernel_for(nw, basis, mode);
+            ce = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            int n = 0;
+            if (ce == cudaSuccess)
+                ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, warps_for(nw, mode) * 32,
+                                                                   smem);
+            if (n < per_sm) per_sm = n;
+        }
     if (ce != cudaSuccess) return ce;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    if (per_sm > 2) per_sm = 2;
     plan->nw = nw;
     plan->smem = smem;
     plan->tiles_x = (g.Lx + kTW - 1) / kTW;
@@ -359,20 +455,23 @@ cudaError_t tma_plan(TmaPlan* plan, void* buf0, void* buf1, const Geometry& g, i
     int grid = sms * per_sm;
     if (grid > plan->ntiles) grid = plan->ntiles;
     plan->grid = grid < 1 ? 1 : grid;
+    if (plan->sample_mode != kSamplerWarps && plan->sample_mode != kFusedSampling)
+        plan->sample_mode = kDefaultSampling;
     plan->ready = true;
     return cudaSuccess;
 }
 
 cudaError_t tma_step(const TmaPlan& plan, int src, const TmaArgs& a,
                      const CollideConst<float>& cc, int basis, bool sample, cudaStream_t s) {
-    const void* fn = kernel_for(plan.nw, basis, sample);
+    const int mode = sample ? plan.sample_mode : kNoSampling;
+    const void* fn = kernel_for(plan.nw, basis, mode);
     if (!fn || !plan.ready) return cudaErrorInvalidValue;
     TmaArgs args = a;
     args.tiles_x = plan.tiles_x;
     args.ntiles = plan.ntiles;
     void* params[3] = {(void*)&plan.map[src], (void*)&args, (void*)&cc};
-    const int warps = plan.nw + (sample ? plan.nw / 2 : 1);
-    return cudaLaunchKernel(fn, dim3(plan.grid), dim3(warps * 32), params, plan.smem, s);
+    return cudaLaunchKernel(fn, dim3(plan.grid), dim3(warps_for(plan.nw, mode) * 32), params,
+                            plan.smem, s);
 }
 
 }  // namespace flb

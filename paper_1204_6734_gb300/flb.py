@@ -23,7 +23,7 @@ OK = 0
 ERR_ARG, ERR_OOM, ERR_INVALID_VELOCITY, ERR_NONFINITE, ERR_TIMEOUT, ERR_CUDA, ERR_STATE = (
     -1, -2, -3, -4, -5, -6, -7)
 BASIS = {"standard": 0, "local": 1}
-OPT_KERNEL, OPT_PIPELINE_WARPS = 0, 1
+OPT_KERNEL, OPT_PIPELINE_WARPS, OPT_PIPELINE_SAMPLING = 0, 1, 2
 KERNEL = {"auto": 0, "generic": 1, "pipelined": 2}
 PRECISION = {"fp64": 0, "fp32": 1, "fp16dev": 2}
 
@@ -287,11 +287,16 @@ def flb_collide_nodes(p, g, node_ids, step):
 class Lattice:
     """One periodic lattice on the GPU (owns an flb_lattice handle)."""
 
-    def __init__(self, p, workspace=None, stream=None, kernel=None):
+    def __init__(self, p, workspace=None, stream=None, kernel=None, pipeline_warps=None,
+                 pipeline_sampling=None):
         self.p = p
         self.h = flb_create(p, workspace, stream)
         if kernel is not None:
             flb_set_option(self.h, OPT_KERNEL, KERNEL[kernel] if isinstance(kernel, str) else kernel)
+        if pipeline_sampling is not None:
+            flb_set_option(self.h, OPT_PIPELINE_SAMPLING, pipeline_sampling)
+        if pipeline_warps is not None:
+            flb_set_option(self.h, OPT_PIPELINE_WARPS, pipeline_warps)
 
     def close(self):
         if self.h is not None:

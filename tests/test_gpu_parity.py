@@ -165,7 +165,18 @@ def test_fp64_parity_lattice_full_run():
     np.testing.assert_allclose(mean, mean_ref, atol=1e-12)
 
 
-KERNELS = ["generic", "pipelined"]
+KERNELS = ["generic", "pipelined", "pipelined-samplers", "pipelined12"]
+
+
+def lattice(p, kernel):
+    """A lattice with the given FP32 step kernel: the generic one, or the
+    pipelined one (8 consumer warps with fused sampling by default; sampler
+    warps; 12 consumer warps)."""
+    if kernel == "pipelined12":
+        return flb.Lattice(p, kernel="pipelined", pipeline_warps=12)
+    if kernel == "pipelined-samplers":
+        return flb.Lattice(p, kernel="pipelined", pipeline_sampling=1)
+    return flb.Lattice(p, kernel=kernel)
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
@@ -176,7 +187,7 @@ def test_fp32_trajectory(basis, kernel):
                              basis, "fp32", seed=12)
     nsteps = 600
     run = oracle.Run(p, warmup=100, every=1).step(nsteps)
-    with flb.Lattice(p, kernel=kernel) as lat:
+    with lattice(p, kernel) as lat:
         lat.set_sampling(100, 1)
         lat.step(nsteps)
         lat.sync()
@@ -218,7 +229,7 @@ def test_fp32_kernels_agree_with_oracle_step_by_step(shape, basis, kernel):
                              basis, "fp32", seed=40 + Lx)
     f_init = _perturbed_state(p, seed=Lx + 7 * Ly)
     run = oracle.Run(p, f=f_init, warmup=0, every=1).step(5)
-    with flb.Lattice(p, kernel=kernel) as lat:
+    with lattice(p, kernel) as lat:
         lat.set_populations(f_init)
         lat.set_sampling(0, 1)
         lat.step(5)
@@ -239,12 +250,13 @@ def test_pipelined_equals_generic_fp32(basis):
                              basis, "fp32", seed=9)
     out = {}
     for kernel in KERNELS:
-        with flb.Lattice(p, kernel=kernel) as lat:
+        with lattice(p, kernel) as lat:
             lat.set_sampling(2, 1)
             lat.step(30)
             out[kernel] = (lat.populations(), lat.raw_sums())
-    assert np.abs(out["generic"][0] - out["pipelined"][0]).max() < 1e-6
-    np.testing.assert_allclose(out["generic"][1][1], out["pipelined"][1][1], rtol=1e-4)
+    for k in ("pipelined", "pipelined-samplers", "pipelined12"):
+        assert np.abs(out["generic"][0] - out[k][0]).max() < 1e-6
+        np.testing.assert_allclose(out["generic"][1][1], out[k][1][1], rtol=1e-4)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
@@ -307,7 +319,7 @@ def test_full_size_sampled_nodes(basis, kernel):
     same pre-collision populations (pull streaming checked by position)."""
     p = inputs.single_lattice(0.1, basis)
     Lx, Ly = p.Lx, p.Ly
-    with flb.Lattice(p, kernel=kernel) as lat:
+    with lattice(p, kernel) as lat:
         lat.step(20)
         F0 = lat.populations()
         lat.step(1)
