@@ -197,6 +197,38 @@ int flb_collide_nodes(const flb_params* p, const double* g, const uint32_t* node
 #define FLB_KERNEL_PIPELINED 2
 int flb_set_option(flb_lattice h, int32_t option, int32_t value);
 
+/* The FP64 fused step with correlation sampling, for callers that cannot
+ * allocate device memory. (The paper has no counterpart: this is an interface
+ * for such callers.) Code that runs while a CUDA graph is being captured,
+ * plugins whose host application owns every device allocation, and loops that
+ * plan their memory ahead and cannot take the synchronisation of cudaMalloc
+ * all fall in this group. The entry point calls no cudaMalloc, cudaFree or
+ * allocating library routine.
+ *  p        parameters; precision must be FLB_FP64; Lx*Ly <= 262144 nodes
+ *           (larger lattices are rejected with FLB_ERR_ARG: the scratch below
+ *           holds the partial sums of at most 1024 blocks of 256 nodes).
+ *  dev_f    device array of 9*Lx*Ly doubles: on entry the pre-collision state
+ *           f_i(x, t0) in the layout f[i][y][x] above; on return f_i(x, t0+nsteps).
+ *  dev_work device array of the same size, overwritten (the caller's second
+ *           buffer; distinct from dev_f).
+ *  t0       time of the state in dev_f (the noise counter of the first step).
+ *  nsteps   number of steps; the pre-collision state of every one of them is
+ *           sampled.
+ *  host_S1, host_S2  (may be NULL) host arrays of 9 and 81 doubles receiving the
+ *           sums of f_i - c_i and (f_i - c_i)(f_j - c_j), c = f^0(rho0, u0), over
+ *           the nodes and steps of this call only (as flb_raw_sums).
+ *  stream   cudaStream_t (as void*) or NULL; the call synchronises it.
+ * Scratch: a fixed array of about 432 KB in this library's device memory, held
+ * by every GPU that loads the library until the process exits. The first call
+ * on a device looks up its address there (cudaGetSymbolAddress), so make that
+ * first call before any stream capture. Every call shares the array and clears
+ * the sums it needs at its start; calls that overlap on the GPU (other streams,
+ * other host threads) race on it and must not be issued.
+ * Errors: FLB_ERR_ARG, FLB_ERR_INVALID_VELOCITY / FLB_ERR_NONFINITE (a node
+ * left the valid region; it was not collided), FLB_ERR_CUDA. */
+int flb_step_noalloc(const flb_params* p, double* dev_f, double* dev_work, int64_t t0,
+                     int64_t nsteps, double* host_S1, double* host_S2, void* stream);
+
 const char* flb_error_string(int code);
 
 /* Library version as major*10000 + minor*100 + patch. */

@@ -88,6 +88,8 @@ def load(build_if_missing: bool = True):
                                       C.c_int32, _u32p, _dp]),
         "flb_collide_nodes": (C.c_int, [P, _dp, _u32p, C.c_uint32, C.c_int32, _dp, _i32p]),
         "flb_set_option": (C.c_int, [h, C.c_int32, C.c_int32]),
+        "flb_step_noalloc": (C.c_int, [P, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, _dp, _dp,
+                                       C.c_void_p]),
         "flb_error_string": (C.c_char_p, [C.c_int]),
         "flb_version": (C.c_int, []),
     }
@@ -105,7 +107,8 @@ def exported_symbols():
             "flb_reset_statistics", "flb_step", "flb_sync", "flb_time", "flb_error_location",
             "flb_reset_error", "flb_correlations", "flb_raw_sums", "flb_conservation",
             "flb_get_populations", "flb_set_populations", "flb_run_host", "flb_noise_draws",
-            "flb_collide_nodes", "flb_set_option", "flb_error_string", "flb_version"]
+            "flb_collide_nodes", "flb_set_option", "flb_step_noalloc", "flb_error_string",
+            "flb_version"]
 
 
 def _check(rc: int, what: str):
@@ -278,6 +281,19 @@ def flb_collide_nodes(p, g, node_ids, step):
     _check(load().flb_collide_nodes(C.byref(s), _ptr(gg), _ptr(ids, C.c_uint32), int(step), n,
                                     _ptr(out), _ptr(st, C.c_int32)), "flb_collide_nodes")
     return out, st
+
+
+def flb_step_noalloc(p, dev_f, dev_work, t0, nsteps, stream=None):
+    """FP64 steps on caller-owned device buffers (CUDA tensors or raw device
+    pointers) without any device allocation; returns the sampled sums
+    (S1[9], S2[9,9]) of this call."""
+    s = make_params(p)
+    S1, S2 = np.zeros(9), np.zeros((9, 9))
+    f = dev_f if isinstance(dev_f, int) else int(dev_f.data_ptr())
+    w = dev_work if isinstance(dev_work, int) else int(dev_work.data_ptr())
+    _check(load().flb_step_noalloc(C.byref(s), f, w, int(t0), int(nsteps), _ptr(S1), _ptr(S2),
+                                   _stream_handle(stream)), "flb_step_noalloc")
+    return S1, S2
 
 
 # ---------------------------------------------------------------------------
