@@ -48,6 +48,10 @@ def parse():
                     help="1: sampler warps, 2: sums fused into the colliding warps (0 = default)")
     ap.add_argument("--sample-every", type=int, default=1,
                     help="sample the correlations every k steps (1 = every step, the workload)")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched-ensemble comparison added to the JSON line")
+    ap.add_argument("--batched-steps", type=int, default=200)
+    ap.add_argument("--graph-steps", type=int, default=25)
     return ap.parse_args()
 
 
@@ -150,6 +154,75 @@ def oracle_mlups(p, max_seconds=10.0, side=512):
     run.step(n)
     dt = time.perf_counter() - t0
     return side * side * n / dt / 1e6, f"{side}x{side} lattice, {n} steps (sampling on), same parameters", 1
+
+
+def bench_batched(args, stream):
+    """The uneven-replica ensemble (256 lattices, sides log-uniform in
+    [64, 1024], FP32, f-norm basis, correlations sampled every step) two ways:
+    one persistent launch per step for the whole batch (CUDA graph, tile shape
+    chosen by the autotuner), and one launch per lattice per step (a lattice
+    handle each). Replica-steps per second of both, on the same stream."""
+    import torch
+
+    from paper_1204_6734_gb300 import flb, inputs
+    ps = inputs.replica_ensemble()
+    nodes = sum(p.Lx * p.Ly for p in ps)
+    out = {"workload": f"{len(ps)} periodic replicas, sides log-uniform in [64, 1024], u_x0 ~ U[0, 0.3], "
+                       "kT in {1e-5, 1e-4, 1e-3}, shear rate ~ U[0.6, 1.8], FP32, local basis, "
+                       "sampled every step",
+           "replicas": len(ps), "nodes": nodes}
+
+    def timed(fn, k):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fn(k)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) * 1e-3
+
+    with flb.Batch(ps, stream=stream) as b:
+        b.set_sampling(0, 1)
+        tile, ms = b.autotune(trial_steps=10)
+        b.set_graph(args.graph_steps)
+        b.step(args.graph_steps)          # capture + warm
+        b.sync()
+        k = max(args.graph_steps, args.batched_steps // args.graph_steps * args.graph_steps)
+        dt = timed(b.step, k)
+        b.sync()
+        out.update({"replica_steps_per_s": len(ps) * k / dt, "mlups": nodes * k / dt / 1e6,
+                    "steps": k, "ms_per_step": dt / k * 1e3, "graph_steps": args.graph_steps,
+                    "tile": [t for t, v in flb.TILE.items() if v == tile][0],
+                    "autotune_ms_per_step": dict(zip(flb.TILE, [float(x) for x in ms])),
+                    "gpu_launches_per_step": 1})
+    peak, kind = measured_peaks()
+    achieved = BYTES_PER_NODE["fp32"] * nodes / (dt / k) / 1e9
+    out["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                       "frac": achieved / peak, "peak_kind": kind,
+                       "kernel": "batch_step_kernel<local,sample>"}
+
+    lats = [flb.Lattice(p, stream=stream, kernel="pipelined") for p in ps]
+    try:
+        for lat in lats:
+            lat.set_sampling(0, 1)
+
+        def per_lattice(k):
+            for _ in range(k):
+                for lat in lats:
+                    flb.flb_step(lat.h, 1)
+        per_lattice(2)
+        k1 = max(5, args.batched_steps // 10)
+        dt1 = timed(per_lattice, k1)
+        for lat in lats:
+            lat.sync()
+    finally:
+        for lat in lats:
+            lat.close()
+    out["one_lattice_per_launch"] = {"replica_steps_per_s": len(ps) * k1 / dt1,
+                                     "mlups": nodes * k1 / dt1 / 1e6, "steps": k1,
+                                     "ms_per_step": dt1 / k1 * 1e3, "gpu_launches_per_step": len(ps)}
+    out["speedup"] = out["replica_steps_per_s"] / out["one_lattice_per_launch"]["replica_steps_per_s"]
+    return out
 
 
 def run_reference(args):
@@ -277,6 +350,10 @@ def main():
                "d2h_bytes_per_step": (state_bytes + 8 * 90) / args.steps,
                "what": "flb_run_host: pinned host state in, steps with sampling, state + sums out"}
 
+    batched = None
+    if rank == 0 and world == 1 and not args.no_batched and args.precision == "fp32":
+        batched = bench_batched(args, stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, sample, cores = oracle_mlups(p)
@@ -301,6 +378,7 @@ def main():
             "clocks": clk.summary(),
             "mlups_roofline_frac": value / (peak * 1e9 / BYTES_PER_NODE[args.precision] / 1e6) / world,
             "n_samples": ns,
+            "batched": batched,
         }
         print(json.dumps(out))
     if dist is not None:

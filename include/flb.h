@@ -178,6 +178,113 @@ int flb_noise_draws(uint64_t seed, uint32_t replica, uint32_t step, const uint32
 int flb_collide_nodes(const flb_params* p, const double* g, const uint32_t* node_ids,
                       uint32_t step, int32_t n, double* fstar, int32_t* status);
 
+/* ---------------------------------------------------------------------------
+ * Batches: many independent FP32 lattices ("replicas") of different sizes and
+ * parameters, stepped together by one persistent launch per step of the
+ * pipelined kernel (the tiles of all replicas in one table). Each replica has
+ * its own state, noise stream (its seed and replica id), time, sampling
+ * schedule and sums, and error record; its populations are those of a lattice
+ * handle created with the same parameters and stepped as often, and its sums
+ * equal the handle's up to the summation order. The paper runs one lattice at
+ * a time and has no counterpart of batches: they exist to fill the GPU with
+ * many small lattices.
+ *
+ * Replicas join and leave between steps: flb_batch_add takes a slot and pool
+ * memory, flb_batch_remove gives them back. All replicas of a batch share the
+ * basis given at open time. Population buffers come from one device pool
+ * allocated at open time (its size is the batch's HBM budget); adding and
+ * removing replicas never allocates device memory. Threading: one thread per
+ * batch. All calls are asynchronous on the batch's stream unless noted.
+ * ------------------------------------------------------------------------- */
+typedef struct flb_batch_s* flb_batch;
+
+/* Tile shapes of the batched kernel (flb_batch_set_tile, flb_batch_autotune):
+ * 128 x 4 nodes, 8 colliding warps, 2 nodes per thread (default);
+ * 128 x 6 nodes, 12 colliding warps, 2 nodes per thread;
+ * 128 x 2 nodes, 8 colliding warps, 1 node per thread. */
+#define FLB_TILE_128x4 0
+#define FLB_TILE_128x6 1
+#define FLB_TILE_128x2 2
+#define FLB_TILE_COUNT 3
+
+/* Open an empty batch for replicas in `basis` (flb_basis): at most
+ * max_replicas (1 .. 16384) at a time, population buffers carved from one
+ * device pool of pool_bytes. stream as for flb_create. Synchronous.
+ * Errors: FLB_ERR_ARG, FLB_ERR_OOM (the pool cannot be allocated), FLB_ERR_CUDA. */
+int flb_batch_open(int32_t basis, int32_t max_replicas, size_t pool_bytes, void* stream,
+                   flb_batch* out);
+
+/* Pool bytes one replica takes (its two FP32 buffers); 0 if p is not valid
+ * for a batch (flb_create's rules, FP32, each side <= 8192). */
+size_t flb_batch_replica_bytes(const flb_params* p);
+
+/* Add a replica at its equilibrium f^0(rho0, u0) and time 0; it runs for
+ * nsteps steps (0 = until removed) and then stays at time nsteps, skipped by
+ * the kernel, until removed. Sampling is off until flb_batch_set_sampling.
+ * *slot receives its index (the lowest free one). Errors: FLB_ERR_ARG
+ * (parameters, basis differs from the batch's), FLB_ERR_OOM (no free slot or
+ * no pool range large enough: retry after a removal), FLB_ERR_CUDA. */
+int flb_batch_add(flb_batch b, const flb_params* p, int64_t nsteps, int32_t* slot);
+
+/* Free a slot and its pool memory. Steps already enqueued still complete. */
+int flb_batch_remove(flb_batch b, int32_t slot);
+
+/* Convenience: open a batch sized for the n replicas p[0..n-1] (one basis)
+ * and add them as slots 0..n-1 with no step limit. Synchronous. */
+int flb_batch_create(const flb_params* p, int32_t n, void* stream, flb_batch* out);
+
+/* Pool bytes flb_batch_create needs for these replicas; 0 if any is invalid. */
+size_t flb_batch_workspace_bytes(const flb_params* p, int32_t n);
+
+/* Waits for the stream, frees all device memory of the batch. */
+int flb_batch_destroy(flb_batch b);
+
+/* Sampling schedule of one slot (slot = -1: every slot), as flb_set_sampling
+ * with times counted from the replica's time 0; clears its sums. */
+int flb_batch_set_sampling(flb_batch b, int32_t slot, int64_t warmup, int64_t every);
+
+/* Enqueue n steps of the batch (one launch each): every live replica below
+ * its step limit advances by one time step per launch. With graphs on
+ * (flb_batch_set_graph), whole chunks are replayed from a captured CUDA graph.
+ * Errors: FLB_ERR_ARG, FLB_ERR_CUDA. Device errors surface in sync/status. */
+int flb_batch_step(flb_batch b, int64_t n);
+
+/* Capture chunks of `steps` launches into a CUDA graph, replayed by
+ * flb_batch_step (0 = launch every step directly; at most 100000). The graph
+ * stays valid across membership changes. Must not be called while the
+ * batch's stream is being captured by the caller. */
+int flb_batch_set_graph(flb_batch b, int32_t steps);
+
+/* Tile shape (FLB_TILE_*), and the autotuner: runs trial_steps real steps of
+ * the batch in every shape (plus 2 warm-up steps each), times them with CUDA
+ * events, keeps the fastest and reports it in *tile (may be NULL) and the
+ * milliseconds per step of each shape in ms_per_step[FLB_TILE_COUNT] (may be
+ * NULL). The trial steps advance the replicas like any others. Synchronous. */
+int flb_batch_set_tile(flb_batch b, int32_t tile);
+int flb_batch_get_tile(flb_batch b, int32_t* tile);
+int flb_batch_autotune(flb_batch b, int32_t trial_steps, int32_t* tile, double* ms_per_step);
+
+/* Wait for the batch's stream; FLB_OK or the error of the lowest slot that
+ * recorded one. flb_batch_status: the same for one slot. Synchronous. */
+int flb_batch_sync(flb_batch b);
+int flb_batch_status(flb_batch b, int32_t slot);
+
+/* Steps enqueued on the batch so far, and the time of one replica. */
+int flb_batch_time(flb_batch b, int64_t* step);
+int flb_batch_replica_time(flb_batch b, int32_t slot, int64_t* t);
+
+/* Live replicas, their tiles in the current shape, pool bytes in use and the
+ * pool size (any pointer may be NULL). */
+int flb_batch_info(flb_batch b, int32_t* replicas, int64_t* tiles, size_t* pool_used,
+                   size_t* pool_size);
+
+/* Per-replica results and state, as their lattice-handle counterparts
+ * (flb_raw_sums, flb_get_populations, flb_set_populations: 9 * Lx * Ly
+ * doubles of that slot's lattice). Synchronous. */
+int flb_batch_raw_sums(flb_batch b, int32_t slot, double* S1, double* S2, int64_t* n_samples);
+int flb_batch_get_populations(flb_batch b, int32_t slot, double* host_out);
+int flb_batch_set_populations(flb_batch b, int32_t slot, const double* host_in);
+
 /* Tuning and testing options of a lattice handle.
  *  FLB_OPT_KERNEL: which step kernel runs -- FLB_KERNEL_AUTO (default: the
  *    pipelined TMA kernel for FP32, the generic kernel for FP64),

@@ -1,0 +1,36 @@
+// flb_batch_k0.cu -- instantiations of the batched step kernel for the
+// Hermite-norm (standard) basis (one translation unit per basis, compiled in parallel).
+#include "flb_batch_kernel.cuh"
+
+namespace flb {
+
+const void* batch_kernel_std(int variant, bool sample) {
+    switch (variant) {
+        case 0:
+            return sample ? (const void*)batch_step_kernel<0, true, 128, 2>
+                          : (const void*)batch_step_kernel<0, false, 128, 2>;
+        case 1:
+            return sample ? (const void*)batch_step_kernel<0, true, 64, 2>
+                          : (const void*)batch_step_kernel<0, false, 64, 2>;
+        case 2:
+            return sample ? (const void*)batch_step_kernel<0, true, 128, 1>
+                          : (const void*)batch_step_kernel<0, false, 128, 1>;
+        default:
+            return nullptr;
+    }
+}
+
+}  // namespace flb
+
+namespace flb {
+
+size_t batch_smem_bytes(int variant) {
+    switch (variant) {
+        case 0: return BatchShape<128, 2>::smem_bytes();
+        case 1: return BatchShape<64, 2>::smem_bytes();
+        case 2: return BatchShape<128, 1>::smem_bytes();
+        default: return 0;
+    }
+}
+
+}  // namespace flb

@@ -1,0 +1,391 @@
+// flb_batch_kernel.cuh -- the pipelined FP32 fused step over many independent
+// lattices ("replicas") of different sizes and parameters in one launch.
+//
+// Every replica has its own two population buffers (ghost-frame layout,
+// flb_layout.cuh) and a descriptor in device memory: the TMA tensor maps of
+// its two buffers and a 256-byte "hot" block (collision constants, reference
+// equilibrium, geometry, pointers, time and sampling schedule). The tiles of
+// all replicas form one table; CTA b walks the contiguous range
+// [b T / G, (b + 1) T / G) of it, so it meets each replica in one run.
+//
+// For every tile the producer thread reads the tile's code and its replica's
+// time from global memory, writes a small tile record (origin, time, live) into
+// the stage and loads the nine population boxes plus the hot block into the
+// same stage; consumers and samplers take everything they need from the stage.
+// A replica whose time has reached its end (tend) is skipped: its stage gets
+// only the record. The batch step counter and the tile count live in device
+// memory (BatchCtl) and the last CTA to finish advances the step, so a CUDA
+// graph of k launches can be replayed while the host changes the membership
+// between replays: replica r is at time t_r = t0_r + (step - join_r).
+//
+// Tile shapes (the autotuner's choices): TW x TH nodes, 8 consumer warps,
+// NPT nodes per consumer thread (2: packed FP32x2 pairs at columns r and
+// r + TW/2; 1: scalar), TH = 8 * 32 * NPT / TW. The register file bounds the
+// warp count: a consumer needs about 160 registers in the f-norm, a sampler
+// 108 for its packed sums, and 8 consumers + 4 samplers fill the SM.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "flb_pipeline.cuh"
+
+namespace flb {
+
+struct __align__(16) ReplicaHot {
+    CollideConst<float> cc;   // -omega, amplitudes, Philox round keys
+    float ref[9];             // f^0(rho0, u0), subtracted before sampling
+    int Lx, Ly, tiles_x, pad0;
+    int t0, join;             // replica time t0 at batch step `join`
+    int warmup, every;        // sampling schedule (every = 0: off)
+    long long pitch, plane;
+    float* buf[2];            // buffer (t & 1) holds f*(t - 1), the source of step t
+    double* acc;              // kSums running sums
+    DevError* err;
+    int tend;                 // the replica stops before time tend
+    int pad1;
+};
+static_assert(sizeof(ReplicaHot) == 256, "the hot block is copied as 256 bytes");
+
+struct __align__(128) ReplicaDesc {
+    CUtensorMap map[2];       // tensor maps of buffer 0 and buffer 1
+    ReplicaHot hot;
+};
+
+struct BatchCtl {
+    unsigned int step;        // launches completed
+    unsigned int ticket;      // CTAs finished in the current launch
+    int ntiles;               // entries of the tile table in use
+    int pad;
+};
+
+struct BatchArgs {
+    const ReplicaDesc* desc;
+    const uint32_t* tiles;    // (replica << kLocalBits) | tile index within the replica
+    BatchCtl* ctl;
+};
+
+constexpr int kLocalBits = 18;
+constexpr uint32_t kLocalMask = (1u << kLocalBits) - 1u;
+constexpr int kMaxBatchReplicas = 1 << (32 - kLocalBits);
+
+constexpr int kBatchNW = 8;   // consumer warps
+
+template <int TW, int NPT>
+struct BatchShape {
+    static constexpr int NW = kBatchNW;
+    static constexpr int TH = NW * 32 * NPT / TW;                // rows per tile
+    static constexpr int BW = TW + 8;                            // box width: x0 - 4 .. x0 + TW + 3
+    static constexpr int RW = TW / NPT;                          // consumer threads per row
+    static constexpr int PAIRS = TW / 64;                        // node pairs per sampler lane and row
+    static constexpr int SPLANE = (TH * BW + 31) / 32 * 32;      // floats per plane box
+    static constexpr int HOT = 64;                               // ReplicaHot
+    static constexpr int INFO = 32;                              // tile record, padded to 128 B
+    static constexpr int STAGE = 9 * SPLANE + HOT + INFO;
+    static constexpr int FIT = 163840 / (4 * STAGE);             // about 160 KB of stages
+    static constexpr int STAGES = FIT < 16 ? FIT : 16;
+    static constexpr size_t smem_bytes() {
+        return sizeof(float) * (size_t)STAGES * STAGE + 2 * STAGES * sizeof(uint64_t) + 16;
+    }
+};
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes,
+                                          uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool sampled_at(const ReplicaHot& h, int t) {
+    return h.every > 0 && t >= h.warmup && ((t - h.warmup) % h.every) == 0;
+}
+
+// Fill stage s with global tile t (one thread). The tile record {x0, y0, t_r,
+// live} is written with a plain shared store before the arrival on the full
+// barrier, whose release makes it visible to the waiting warps.
+template <int TW, int NPT>
+__device__ __forceinline__ void batch_issue(float* smem, const BatchArgs& a, unsigned step, int t,
+                                            int s, uint64_t* full) {
+    using BS = BatchShape<TW, NPT>;
+    const uint32_t code = __ldg(&a.tiles[t]);
+    const ReplicaDesc* d = a.desc + (code >> kLocalBits);
+    const int local = (int)(code & kLocalMask);
+    const int tr = __ldg(&d->hot.t0) + (int)(step - (unsigned)__ldg(&d->hot.join));
+    const int tiles_x = __ldg(&d->hot.tiles_x), Ly = __ldg(&d->hot.Ly);
+    const bool live = tr < __ldg(&d->hot.tend);
+    const int ty = local / tiles_x;
+    const int x0 = (local - ty * tiles_x) * TW, y0 = ty * BS::TH;
+    float* st = smem + s * BS::STAGE;
+    *reinterpret_cast<int4*>(st + 9 * BS::SPLANE + BS::HOT) = make_int4(x0, y0, tr, live ? 1 : 0);
+    if (!live) {
+        mbar_arrive(&full[s]);
+        return;
+    }
+    mbar_arrive_expect_tx(&full[s], 9u * BS::TH * BS::BW * sizeof(float) + sizeof(ReplicaHot));
+    const CUtensorMap* map = &d->map[tr & 1];
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+        tma_load_2d(st + i * BS::SPLANE, map, x0 + kXO - 4, i * (Ly + 2) + y0 + 1 - cvy(i),
+                    &full[s]);
+    bulk_load(st + 9 * BS::SPLANE, &d->hot, sizeof(ReplicaHot), &full[s]);
+}
+
+// Warp roles: NW consumer warps, then one producer warp (SAMPLE = false) or
+// kSamplers sampler warps whose first lane also produces (SAMPLE = true).
+template <int BASIS, bool SAMPLE, int TW, int NPT>
+__global__ void __launch_bounds__((kBatchNW + (SAMPLE ? kSamplers : 1)) * 32, 1)
+batch_step_kernel(const BatchArgs a) {
+    using BS = BatchShape<TW, NPT>;
+    constexpr int NW = kBatchNW;
+    constexpr int BW = BS::BW;
+    constexpr int TH = BS::TH;
+    constexpr int S = BS::STAGES;
+    constexpr int NX = SAMPLE ? kSamplers : 1;
+    extern __shared__ __align__(128) float smem[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * BS::STAGE);
+    uint64_t* empty = full + S;
+
+    const int warp = threadIdx.x >> 5, lane_id = threadIdx.x & 31;
+    const unsigned step = __ldcg(&a.ctl->step);
+    const int ntiles = __ldcg(&a.ctl->ntiles);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], NW + (SAMPLE ? NX : 0));
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    const int tbeg = (int)((long long)blockIdx.x * ntiles / gridDim.x);
+    const int ntile = (int)((long long)(blockIdx.x + 1) * ntiles / gridDim.x) - tbeg;
+    // the replica an error without a node belongs to
+    auto first_err = [&]() { return a.desc[__ldg(&a.tiles[tbeg]) >> kLocalBits].hot.err; };
+
+    if (warp >= NW) {
+        const bool producer = warp == NW && lane_id == 0;
+        int issued = 0, k = 0;
+        bool ok = true;
+        if (producer)
+            for (; issued < S && issued < ntile; ++issued)
+                batch_issue<TW, NPT>(smem, a, step, tbeg + issued, issued, full);
+        if (!SAMPLE) {
+            if (producer) {
+                for (; k < ntile && issued < ntile; ++k) {
+                    const int s = k % S;
+                    if (!mbar_wait(&empty[s], (k / S) & 1)) {
+                        ok = false;
+                        break;
+                    }
+                    batch_issue<TW, NPT>(smem, a, step, tbeg + issued, s, full);
+                    ++issued;
+                }
+                if (!ok) {
+                    record_error(first_err(), kStatusTimeout, -1, step);
+                    // let the copies still in flight land before the CTA exits
+                    for (int j = issued > S ? issued - S : 0; j < issued; ++j)
+                        if (!mbar_wait(&full[j % S], (j / S) & 1)) break;
+                }
+            }
+            return;
+        }
+        // ---------------- samplers: warp sw takes rows sw, sw + kSamplers, ...
+        const int sw = warp - NW;
+        f2 s1[9], s2[45];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) s1[q] = f2(0.f);
+#pragma unroll
+        for (int q = 0; q < 45; ++q) s2[q] = f2(0.f);
+        double* run_acc = nullptr;   // replica whose sums the registers hold
+        auto flush = [&]() {
+            if (!run_acc) return;
+#pragma unroll
+            for (int q = 0; q < kSums; ++q) {
+                f2& x2 = q < 9 ? s1[q] : s2[q - 9];
+                float v = x2.v.x + x2.v.y;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane_id == 0) atomicAdd(&run_acc[q], (double)v);
+                x2 = f2(0.f);
+            }
+            run_acc = nullptr;
+        };
+        for (; k < ntile && ok; ++k) {
+            const int s = k % S, n = k / S;
+            if (!mbar_wait(&full[s], n & 1)) {
+                ok = false;
+                break;
+            }
+            const float* stg = smem + s * BS::STAGE;
+            const int4 info = *reinterpret_cast<const int4*>(stg + 9 * BS::SPLANE + BS::HOT);
+            const ReplicaHot& h = *reinterpret_cast<const ReplicaHot*>(stg + 9 * BS::SPLANE);
+            bool released = false;
+            if (info.w && sampled_at(h, info.z)) {
+                double* acc = h.acc;
+                float ref[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) ref[i] = h.ref[i];
+                const int Lx = h.Lx, Ly = h.Ly;
+                if (run_acc != acc) flush();
+                run_acc = acc;
+                for (int row = sw; row < TH; row += kSamplers) {
+                    const int y = info.y + row;
+                    const float* st = stg + row * BW + 4 + lane_id;
+#pragma unroll
+                    for (int p = 0; p < BS::PAIRS; ++p) {
+                        f2 d[9];
+#pragma unroll
+                        for (int i = 0; i < 9; ++i) {
+                            const float* q = st + i * BS::SPLANE - cvx(i) + 64 * p;
+                            d[i] = f2(q[0], q[32]);
+                        }
+                        if (row + kSamplers >= TH && p == BS::PAIRS - 1) {
+                            // last read of the stage: release before the arithmetic
+                            __syncwarp();
+                            if (lane_id == 0) mbar_arrive(&empty[s]);
+                            released = true;
+                        }
+                        const int xA = info.x + lane_id + 64 * p;
+                        const bool inA = xA < Lx && y < Ly, inB = xA + 32 < Lx && y < Ly;
+#pragma unroll
+                        for (int i = 0; i < 9; ++i) {
+                            f2 e = d[i] - f2(ref[i]);
+                            if (!(inA && inB)) e = f2(inA ? e.v.x : 0.f, inB ? e.v.y : 0.f);
+                            d[i] = e;
+                        }
+                        int q = 0;
+#pragma unroll
+                        for (int i = 0; i < 9; ++i) {
+                            s1[i] += d[i];
+#pragma unroll
+                            for (int j = i; j < 9; ++j, ++q) s2[q] = mad(d[i], d[j], s2[q]);
+                        }
+                    }
+                }
+            }
+            if (!released) {
+                __syncwarp();
+                if (lane_id == 0) mbar_arrive(&empty[s]);
+            }
+            if (producer && issued < ntile) {
+                if (!mbar_wait(&empty[s], n & 1)) {
+                    ok = false;
+                    break;
+                }
+                batch_issue<TW, NPT>(smem, a, step, tbeg + issued, s, full);
+                ++issued;
+            }
+        }
+        flush();
+        if (!ok) {
+            record_error(first_err(), kStatusTimeout, -1, step);
+            if (producer)
+                for (int j = k; j < issued; ++j)
+                    if (!mbar_wait(&full[j % S], (j / S) & 1)) break;
+        }
+        return;
+    }
+
+    // ---------------- consumers
+    const int c = threadIdx.x;
+    const int ty = c / BS::RW, r = c % BS::RW;
+    for (int k = 0; k < ntile; ++k) {
+        const int s = k % S;
+        if (!mbar_wait(&full[s], (k / S) & 1)) {
+            record_error(first_err(), kStatusTimeout, -1, step);
+            break;
+        }
+        const float* stg = smem + s * BS::STAGE;
+        const int4 info = *reinterpret_cast<const int4*>(stg + 9 * BS::SPLANE + BS::HOT);
+        if (!info.w) {
+            __syncwarp();
+            if (lane_id == 0) mbar_arrive(&empty[s]);
+            continue;
+        }
+        const ReplicaHot& hs = *reinterpret_cast<const ReplicaHot*>(stg + 9 * BS::SPLANE);
+        Geometry geo;
+        geo.Lx = hs.Lx;
+        geo.Ly = hs.Ly;
+        geo.pitch = hs.pitch;
+        geo.plane = hs.plane;
+        const uint32_t tr = (uint32_t)info.z;
+        float* dst = hs.buf[(tr + 1u) & 1u];
+        DevError* err = hs.err;
+        const int y = info.y + ty;
+        const float* st = stg + ty * BW + 4 + r;
+        if (NPT == 2) {
+            auto load = [&](f2* g) {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    const float* p = st + i * BS::SPLANE - cvx(i);
+                    g[i] = f2(p[0], p[TW / 2]);
+                }
+            };
+            f2 g[9];
+            load(g);
+            const int xA = info.x + r, xB = xA + TW / 2;
+            const bool inA = xA < geo.Lx && y < geo.Ly, inB = xB < geo.Lx && y < geo.Ly;
+            const uint32_t nodeA = (uint32_t)xA + (uint32_t)geo.Lx * (uint32_t)y;
+            f2 f[9];
+            const uint32_t stt = collide<f2, BASIS>(
+                g, [&](f2* N) { node_normals(hs.cc.key, nodeA, nodeA + TW / 2, tr, N); }, load,
+                hs.cc, f);
+            __syncwarp();
+            if (lane_id == 0) mbar_arrive(&empty[s]);
+            if (inA) {
+                if (stt & 0xFF) record_error(err, (int)(stt & 0xFF), nodeA, tr);
+                store_lane(dst, geo, xA, y, f, 0);
+            }
+            if (inB) {
+                if (stt >> 8) record_error(err, (int)(stt >> 8), nodeA + TW / 2, tr);
+                store_lane(dst, geo, xB, y, f, 1);
+            }
+        } else {
+            auto load = [&](float* g) {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) g[i] = st[i * BS::SPLANE - cvx(i)];
+            };
+            float g[9];
+            load(g);
+            const int x = info.x + r;
+            const bool in = x < geo.Lx && y < geo.Ly;
+            const uint32_t node = (uint32_t)x + (uint32_t)geo.Lx * (uint32_t)y;
+            float f[9];
+            const uint32_t stt = collide<float, BASIS>(
+                g, [&](float* N) { node_normals(hs.cc.key, node, tr, N); }, load, hs.cc, f);
+            __syncwarp();
+            if (lane_id == 0) mbar_arrive(&empty[s]);
+            if (in) {
+                if (stt & 0xFF) record_error(err, (int)(stt & 0xFF), node, tr);
+                store_node(dst, geo, x, y, f);
+            }
+        }
+    }
+    // the last CTA to finish advances the batch step (every CTA read it at its start)
+    if (c == 0) {
+        __threadfence();
+        if (atomicAdd(&a.ctl->ticket, 1u) == gridDim.x - 1) {
+            a.ctl->step = step + 1u;
+            a.ctl->ticket = 0u;
+        }
+    }
+}
+
+// Tile shapes the batch can run; index = FLB_TILE_* of flb.h.
+struct BatchVariant {
+    int tw, npt;
+    __host__ __device__ constexpr int th() const { return kBatchNW * 32 * npt / tw; }
+};
+constexpr BatchVariant kBatchVariants[3] = {{128, 2}, {64, 2}, {128, 1}};
+constexpr int kNumBatchVariants = 3;
+
+// Kernel of (variant, basis, sampling), instantiated in flb_batch_k<basis>.cu.
+const void* batch_kernel_std(int variant, bool sample);
+const void* batch_kernel_loc(int variant, bool sample);
+size_t batch_smem_bytes(int variant);
+
+}  // namespace flb

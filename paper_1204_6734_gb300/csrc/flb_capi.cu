@@ -8,7 +8,9 @@
 #include <new>
 
 #include "../../include/flb.h"
+#include "flb_host.h"
 #include "flb_internal.h"
+#include "flb_io.cuh"
 #include "flb_kernels.cuh"
 
 namespace flb {
@@ -149,45 +151,6 @@ __global__ void sum3_kernel(const double* partials, int nblocks, double* out) {
 }
 
 // ---------------------------------------------------------------------------
-// State I/O: host layout f[i][y][x] (pre-collision) <-> device buffer holding
-// f*_i(x) = f_i(x + v_i).
-// ---------------------------------------------------------------------------
-
-template <class T>
-__global__ void scatter_state_kernel(const double* in, Geometry geo, T* buf) {
-    const long long N = (long long)geo.Lx * geo.Ly;
-    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < (int)N; n += gridDim.x * blockDim.x) {
-        const int y = n / geo.Lx, x = n - y * geo.Lx;
-        for (int i = 0; i < 9; ++i) {
-            // the buffer holds f*_i(z) = f_i(z + v_i): write f_i(x) at z = x - v_i,
-            // with the ghost copy the pull of f_i(x) will read
-            const int zx = wrap(x - cvx(i), geo.Lx), zy = wrap(y - cvy(i), geo.Ly);
-            store_pop(buf, geo, i, zx, zy, (T)in[i * N + n]);
-        }
-    }
-}
-
-template <class T>
-__global__ void gather_state_kernel(const T* buf, Geometry geo, double* out) {
-    const long long N = (long long)geo.Lx * geo.Ly;
-    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < (int)N; n += gridDim.x * blockDim.x) {
-        const int y = n / geo.Lx, x = n - y * geo.Lx;
-        for (int i = 0; i < 9; ++i) {
-            const int xs = wrap(x - cvx(i), geo.Lx), ys = wrap(y - cvy(i), geo.Ly);
-            out[i * N + n] = (double)buf[at(geo, i, xs, ys)];
-        }
-    }
-}
-
-template <class T>
-__global__ void fill_kernel(T* buf, Geometry geo, Vec9 v) {
-    const long long total = 9 * geo.plane;
-    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < total;
-         k += (long long)gridDim.x * blockDim.x)
-        buf[k] = (T)v.v[k / geo.plane];
-}
-
-// ---------------------------------------------------------------------------
 // Test hooks
 // ---------------------------------------------------------------------------
 
@@ -258,27 +221,6 @@ namespace {
 constexpr size_t kAlign = 256;
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
-int valid_params(const flb_params* p) {
-    if (!p) return 0;
-    if (p->Lx < 1 || p->Ly < 1) return 0;
-    if ((long long)p->Lx * p->Ly >= (1LL << 31)) return 0;
-    if (!(p->rho0 > 0) || !std::isfinite(p->rho0)) return 0;
-    if (!(p->kT >= 0) || !std::isfinite(p->kT)) return 0;
-    if (!std::isfinite(p->ux0) || !std::isfinite(p->uy0)) return 0;
-    for (int a = 3; a < 9; ++a)
-        if (!(p->omega[a] > 0 && p->omega[a] < 2)) return 0;
-    if (p->basis != FLB_BASIS_STANDARD && p->basis != FLB_BASIS_LOCAL) return 0;
-    if (p->precision != FLB_FP64 && p->precision != FLB_FP32) return 0;
-    if (p->reserved != 0) return 0;
-    // the mean velocity must leave every f_i^0(1,u0) > 0 (Fig. 11)
-    const double usq = p->ux0 * p->ux0 + p->uy0 * p->uy0;
-    for (int i = 0; i < 9; ++i) {
-        const double uv = p->ux0 * cvx(i) + p->uy0 * cvy(i);
-        if (!(1.0 + 3.0 * uv + 4.5 * uv * uv - 1.5 * usq > 0.0)) return 0;
-    }
-    return 1;
-}
-
 int elem_size(int prec) { return prec == FLB_FP64 ? 8 : 4; }
 
 Geometry make_geometry(const flb_params* p) { return flb::make_geometry(p->Lx, p->Ly); }
@@ -324,42 +266,8 @@ Layout layout(const flb_params* p, int sms) {
     return L;
 }
 
-void feq_host(double rho, double ux, double uy, double f[9]) {
-    const double usq = ux * ux + uy * uy;
-    for (int i = 0; i < 9; ++i) {
-        const double uv = ux * cvx(i) + uy * cvy(i);
-        const double wi = i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
-        f[i] = rho * wi * (1.0 + 3.0 * uv + 4.5 * uv * uv - 1.5 * usq);
-    }
-}
-
-template <class T>
-CollideConst<T> collide_const(const flb_params* p) {
-    CollideConst<T> cc;
-    for (int a = 0; a < 6; ++a) {
-        const double om = p->omega[3 + a];
-        cc.nomega[a] = (T)(-om);
-        const double v = p->kT * om * (2.0 - om);
-        cc.amp[a] = (T)(v > 0 ? std::sqrt(v) : 0.0);
-    }
-    cc.key = make_noise_key(p->seed, p->replica);
-    return cc;
-}
-
 int cuda_rc(cudaError_t e) { return e == cudaSuccess ? FLB_OK : FLB_ERR_CUDA; }
 
-int map_status(int code) {
-    if (code == kStatusInvalidVelocity) return FLB_ERR_INVALID_VELOCITY;
-    if (code == kStatusNonfinite) return FLB_ERR_NONFINITE;
-    if (code == kStatusTimeout) return FLB_ERR_TIMEOUT;
-    return code ? FLB_ERR_STATE : FLB_OK;
-}
-
-int grid_for(long long n) {
-    long long b = (n + 255) / 256;
-    if (b > 4096) b = 4096;
-    return (int)(b < 1 ? 1 : b);
-}
 
 template <class T, int BASIS, bool SAMPLE>
 cudaError_t launch_step_t(flb_lattice h) {

@@ -36,6 +36,10 @@ struct TmaPlan {
 // cudaSuccess or the error that prevents the pipelined kernel.
 cudaError_t tma_plan(TmaPlan* plan, void* buf0, void* buf1, const Geometry& g, int nw);
 
+// Tensor map of the nine planes of one FP32 buffer (ghost-frame layout), seen
+// as one 2D array of pitch x 9 (Ly + 2) elements, for boxes of box_w x th.
+cudaError_t tma_encode_planes(CUtensorMap* map, void* buf, const Geometry& g, int box_w, int th);
+
 // Grid (CTAs) the plan launches with the given consumer-warp count, for sizing
 // the per-CTA partial sums before the buffers exist.
 int tma_max_grid(int sms);

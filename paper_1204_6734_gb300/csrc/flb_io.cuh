@@ -1,0 +1,47 @@
+// flb_io.cuh -- state I/O between the public host layout f[i][y][x]
+// (pre-collision f_i(x, t)) and a device buffer in the ghost-frame layout,
+// which holds f*_i(z) = f_i(z + v_i) for the next pull; and a uniform fill.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "flb_kernels.cuh"
+#include "flb_layout.cuh"
+
+namespace flb {
+
+template <class T>
+__global__ void scatter_state_kernel(const double* in, Geometry geo, T* buf) {
+    const long long N = (long long)geo.Lx * geo.Ly;
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < (int)N; n += gridDim.x * blockDim.x) {
+        const int y = n / geo.Lx, x = n - y * geo.Lx;
+        for (int i = 0; i < 9; ++i) {
+            // the buffer holds f*_i(z) = f_i(z + v_i): write f_i(x) at z = x - v_i,
+            // with the ghost copy the pull of f_i(x) will read
+            const int zx = wrap(x - cvx(i), geo.Lx), zy = wrap(y - cvy(i), geo.Ly);
+            store_pop(buf, geo, i, zx, zy, (T)in[i * N + n]);
+        }
+    }
+}
+
+template <class T>
+__global__ void gather_state_kernel(const T* buf, Geometry geo, double* out) {
+    const long long N = (long long)geo.Lx * geo.Ly;
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < (int)N; n += gridDim.x * blockDim.x) {
+        const int y = n / geo.Lx, x = n - y * geo.Lx;
+        for (int i = 0; i < 9; ++i) {
+            const int xs = wrap(x - cvx(i), geo.Lx), ys = wrap(y - cvy(i), geo.Ly);
+            out[i * N + n] = (double)buf[at(geo, i, xs, ys)];
+        }
+    }
+}
+
+template <class T>
+__global__ void fill_kernel(T* buf, Geometry geo, Vec9 v) {
+    const long long total = 9 * geo.plane;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < total;
+         k += (long long)gridDim.x * blockDim.x)
+        buf[k] = (T)v.v[k / geo.plane];
+}
+
+}  // namespace flb

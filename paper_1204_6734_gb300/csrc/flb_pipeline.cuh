@@ -1,0 +1,82 @@
+// flb_pipeline.cuh -- pieces shared by the pipelined FP32 step kernels (one
+// lattice: flb_step_tma.cu; many lattices: flb_batch.cu): tile shape of the
+// shared-memory ring, storing a packed node pair, and the CTA/grid reduction of
+// correlation sums.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "flb_collide.cuh"
+#include "flb_internal.h"
+#include "flb_kernels.cuh"
+#include "flb_layout.cuh"
+#include "flb_tma.cuh"
+
+namespace flb {
+
+constexpr int kTW = 128;               // tile width (nodes)
+constexpr int kBoxW = kTW + 8;         // TMA box width: x0 - 4 .. x0 + 131
+constexpr int kDefaultNW = 8;
+constexpr int kSamplers = 4;   // sampler warps: one per SM sub-partition
+constexpr int kDefaultSampling = 1;   // kSamplerWarps
+
+// Tile of 128 x TH nodes, TH = NW / 2; the ring holds STAGES tiles. The ring
+// must be deep: a stage is in flight from HBM only between its refill and its
+// arrival, and consumers keep their stage until they have finished the tile.
+template <int NW>
+struct TileShape {
+    static constexpr int TH = NW / 2;                                  // rows per tile
+    static constexpr int SPLANE = (TH * kBoxW + 31) / 32 * 32;         // floats per plane box
+    static constexpr int STAGE = 9 * SPLANE;                           // floats per stage
+    static constexpr int STAGES = NW <= 8 ? 8 : 6;                     // 157 / 176 KB
+    static constexpr int RED = NW > kSamplers ? NW : kSamplers;        // warps reducing
+    static constexpr size_t smem_bytes() {
+        return sizeof(float) * (size_t)STAGES * STAGE + 2 * STAGES * sizeof(uint64_t) +
+               sizeof(double) * RED * kSums + 16;
+    }
+};
+
+__device__ __forceinline__ void store_lane(float* dst, const Geometry& geo, int x, int y,
+                                           const f2 f[9], int k) {
+    float v[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) v[i] = lane(f[i], k);
+    store_node(dst, geo, x, y, v);
+}
+
+// CTA and grid reduction of per-thread correlation sums held by `group`
+// threads (warps [w0, w0 + group/32)): warp shuffles, FP64 across warps into
+// this CTA's partials, then the last CTA to finish adds all CTA partials in a
+// fixed order to the running sums.
+__device__ __forceinline__ void publish_sums(const float (&v)[kSums], int w0, int group,
+                                             double* red, int* flag, const TmaArgs& a) {
+    const int warp = threadIdx.x >> 5, lane_id = threadIdx.x & 31;
+    const int nw = group / 32, c = threadIdx.x - 32 * w0;
+#pragma unroll
+    for (int q = 0; q < kSums; ++q) {
+        float x = v[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane_id == 0) red[(warp - w0) * kSums + q] = (double)x;
+    }
+    named_sync(1, group);
+    if (c < kSums) {
+        double tot = 0.0;
+        for (int w = 0; w < nw; ++w) tot += red[w * kSums + c];
+        a.partials[(size_t)blockIdx.x * kSums + c] = tot;
+    }
+    __threadfence();
+    named_sync(1, group);
+    if (c == 0) *flag = (atomicAdd(a.ticket, 1u) == gridDim.x - 1) ? 1 : 0;
+    named_sync(1, group);
+    if (*flag) {
+        __threadfence();
+        for (int q = warp - w0; q < kSums; q += nw) {
+            const double s = reduce_partials(a.partials, q, gridDim.x, lane_id);
+            if (lane_id == 0) a.acc[q] += s;
+        }
+        if (c == 0) *a.ticket = 0u;
+    }
+}
+
+}  // namespace flb

@@ -24,38 +24,10 @@
 
 #include "flb_collide.cuh"
 #include "flb_internal.h"
+#include "flb_pipeline.cuh"
 #include "flb_tma.cuh"
 
 namespace flb {
-
-constexpr int kTW = 128;               // tile width (nodes)
-constexpr int kBoxW = kTW + 8;         // TMA box width: x0 - 4 .. x0 + 131
-constexpr int kDefaultNW = 8;
-constexpr int kSamplers = 4;   // sampler warps: one per SM sub-partition
-constexpr int kDefaultSampling = 1;   // kSamplerWarps
-
-// Tile of 128 x TH nodes, TH = NW / 2; the ring holds STAGES tiles. The ring
-// must be deep: a stage is in flight from HBM only between its refill and its
-// arrival, and consumers keep their stage until they have finished the tile.
-template <int NW>
-struct TileShape {
-    static constexpr int TH = NW / 2;                                  // rows per tile
-    static constexpr int SPLANE = (TH * kBoxW + 31) / 32 * 32;         // floats per plane box
-    static constexpr int STAGE = 9 * SPLANE;                           // floats per stage
-    static constexpr int STAGES = NW <= 8 ? 8 : 6;                     // 157 / 176 KB
-    static constexpr int RED = NW > kSamplers ? NW : kSamplers;        // warps reducing
-    static constexpr size_t smem_bytes() {
-        return sizeof(float) * (size_t)STAGES * STAGE + 2 * STAGES * sizeof(uint64_t) +
-               sizeof(double) * RED * kSums + 16;
-    }
-};
-
-__device__ __forceinline__ void store_lane(const TmaArgs& a, int x, int y, const f2 f[9], int k) {
-    float v[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) v[i] = lane(f[i], k);
-    store_node(a.dst, a.geo, x, y, v);
-}
 
 // Issue the nine TMA box loads of tile t into stage s (one thread).
 template <int NW>
@@ -110,41 +82,6 @@ struct Producer {
             }
     }
 };
-
-// CTA and grid reduction of per-thread correlation sums held by `group`
-// threads (warps [w0, w0 + group/32)): warp shuffles, FP64 across warps into
-// this CTA's partials, then the last CTA to finish adds all CTA partials in a
-// fixed order to the running sums.
-__device__ __forceinline__ void publish_sums(const float (&v)[kSums], int w0, int group,
-                                             double* red, int* flag, const TmaArgs& a) {
-    const int warp = threadIdx.x >> 5, lane_id = threadIdx.x & 31;
-    const int nw = group / 32, c = threadIdx.x - 32 * w0;
-#pragma unroll
-    for (int q = 0; q < kSums; ++q) {
-        float x = v[q];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-        if (lane_id == 0) red[(warp - w0) * kSums + q] = (double)x;
-    }
-    named_sync(1, group);
-    if (c < kSums) {
-        double tot = 0.0;
-        for (int w = 0; w < nw; ++w) tot += red[w * kSums + c];
-        a.partials[(size_t)blockIdx.x * kSums + c] = tot;
-    }
-    __threadfence();
-    named_sync(1, group);
-    if (c == 0) *flag = (atomicAdd(a.ticket, 1u) == gridDim.x - 1) ? 1 : 0;
-    named_sync(1, group);
-    if (*flag) {
-        __threadfence();
-        for (int q = warp - w0; q < kSums; q += nw) {
-            const double s = reduce_partials(a.partials, q, gridDim.x, lane_id);
-            if (lane_id == 0) a.acc[q] += s;
-        }
-        if (c == 0) *a.ticket = 0u;
-    }
-}
 
 // Correlation sums of two nodes (lanes of d, already centred and masked).
 __device__ __forceinline__ void add_sums(float (&v)[kSums], const f2 (&d)[9]) {
@@ -333,11 +270,11 @@ step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
         if (lane_id == 0) mbar_arrive(&empty[s]);
         if (inA) {
             if (stt & 0xFF) record_error(a.err, (int)(stt & 0xFF), nodeA, a.step);
-            store_lane(a, xA, y, f, 0);
+            store_lane(a.dst, a.geo, xA, y, f, 0);
         }
         if (inB) {
             if (stt >> 8) record_error(a.err, (int)(stt >> 8), nodeA + 64u, a.step);
-            store_lane(a, xB, y, f, 1);
+            store_lane(a.dst, a.geo, xB, y, f, 1);
         }
         if (producer) prod.refill(smem, &map, a, full, empty, s, n);
     }
@@ -412,24 +349,28 @@ size_t smem_for(int nw) {
 
 int tma_max_grid(int sms) { return sms * 2; }
 
+cudaError_t tma_encode_planes(CUtensorMap* map, void* buf, const Geometry& g, int box_w, int th) {
+    EncodeFn enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    const cuuint64_t dims[2] = {(cuuint64_t)g.pitch, (cuuint64_t)(9 * (long long)(g.Ly + 2))};
+    const cuuint64_t strides[1] = {(cuuint64_t)g.pitch * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)th};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult rc = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, buf, dims, strides, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return rc == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 cudaError_t tma_plan(TmaPlan* plan, void* buf0, void* buf1, const Geometry& g, int nw) {
     plan->ready = false;
     if (nw == 0) nw = kDefaultNW;
     if (!kernel_for(nw, 0, kNoSampling)) return cudaErrorInvalidValue;
-    EncodeFn enc = encode_fn();
-    if (!enc) return cudaErrorNotSupported;
     const int th = nw / 2;
-    const cuuint64_t dims[2] = {(cuuint64_t)g.pitch, (cuuint64_t)(9 * (long long)(g.Ly + 2))};
-    const cuuint64_t strides[1] = {(cuuint64_t)g.pitch * sizeof(float)};
-    const cuuint32_t box[2] = {(cuuint32_t)kBoxW, (cuuint32_t)th};
-    const cuuint32_t estr[2] = {1, 1};
     void* bufs[2] = {buf0, buf1};
     for (int b = 0; b < 2; ++b) {
-        const CUresult rc = enc(&plan->map[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, bufs[b], dims,
-                                strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (rc != CUDA_SUCCESS) return cudaErrorInvalidValue;
+        const cudaError_t e = tma_encode_planes(&plan->map[b], bufs[b], g, kBoxW, th);
+        if (e != cudaSuccess) return e;
     }
     const size_t smem = smem_for(nw);
     int dev = 0, sms = 0;

@@ -26,6 +26,8 @@ BASIS = {"standard": 0, "local": 1}
 OPT_KERNEL, OPT_PIPELINE_WARPS, OPT_PIPELINE_SAMPLING = 0, 1, 2
 KERNEL = {"auto": 0, "generic": 1, "pipelined": 2}
 PRECISION = {"fp64": 0, "fp32": 1, "fp16dev": 2}
+TILE = {"128x4": 0, "64x8": 1, "128x2": 2}   # tile shapes of the batched kernel
+TILE_COUNT = 3
 
 
 class FlbError(RuntimeError):
@@ -90,6 +92,28 @@ def load(build_if_missing: bool = True):
         "flb_set_option": (C.c_int, [h, C.c_int32, C.c_int32]),
         "flb_step_noalloc": (C.c_int, [P, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, _dp, _dp,
                                        C.c_void_p]),
+        "flb_batch_open": (C.c_int, [C.c_int32, C.c_int32, C.c_size_t, C.c_void_p, C.POINTER(h)]),
+        "flb_batch_replica_bytes": (C.c_size_t, [P]),
+        "flb_batch_add": (C.c_int, [h, P, C.c_int64, _i32p]),
+        "flb_batch_remove": (C.c_int, [h, C.c_int32]),
+        "flb_batch_create": (C.c_int, [P, C.c_int32, C.c_void_p, C.POINTER(h)]),
+        "flb_batch_workspace_bytes": (C.c_size_t, [P, C.c_int32]),
+        "flb_batch_destroy": (C.c_int, [h]),
+        "flb_batch_set_sampling": (C.c_int, [h, C.c_int32, C.c_int64, C.c_int64]),
+        "flb_batch_step": (C.c_int, [h, C.c_int64]),
+        "flb_batch_set_graph": (C.c_int, [h, C.c_int32]),
+        "flb_batch_set_tile": (C.c_int, [h, C.c_int32]),
+        "flb_batch_get_tile": (C.c_int, [h, _i32p]),
+        "flb_batch_autotune": (C.c_int, [h, C.c_int32, _i32p, _dp]),
+        "flb_batch_sync": (C.c_int, [h]),
+        "flb_batch_status": (C.c_int, [h, C.c_int32]),
+        "flb_batch_time": (C.c_int, [h, _i64p]),
+        "flb_batch_replica_time": (C.c_int, [h, C.c_int32, _i64p]),
+        "flb_batch_info": (C.c_int, [h, _i32p, _i64p, C.POINTER(C.c_size_t),
+                                     C.POINTER(C.c_size_t)]),
+        "flb_batch_raw_sums": (C.c_int, [h, C.c_int32, _dp, _dp, _i64p]),
+        "flb_batch_get_populations": (C.c_int, [h, C.c_int32, _dp]),
+        "flb_batch_set_populations": (C.c_int, [h, C.c_int32, _dp]),
         "flb_error_string": (C.c_char_p, [C.c_int]),
         "flb_version": (C.c_int, []),
     }
@@ -108,7 +132,13 @@ def exported_symbols():
             "flb_reset_error", "flb_correlations", "flb_raw_sums", "flb_conservation",
             "flb_get_populations", "flb_set_populations", "flb_run_host", "flb_noise_draws",
             "flb_collide_nodes", "flb_set_option", "flb_step_noalloc", "flb_error_string",
-            "flb_version"]
+            "flb_version", "flb_batch_open", "flb_batch_replica_bytes", "flb_batch_add",
+            "flb_batch_remove", "flb_batch_create", "flb_batch_workspace_bytes",
+            "flb_batch_destroy", "flb_batch_set_sampling", "flb_batch_step",
+            "flb_batch_set_graph", "flb_batch_set_tile", "flb_batch_get_tile",
+            "flb_batch_autotune", "flb_batch_sync", "flb_batch_status", "flb_batch_time",
+            "flb_batch_replica_time", "flb_batch_info", "flb_batch_raw_sums",
+            "flb_batch_get_populations", "flb_batch_set_populations"]
 
 
 def _check(rc: int, what: str):
@@ -296,6 +326,141 @@ def flb_step_noalloc(p, dev_f, dev_work, t0, nsteps, stream=None):
     return S1, S2
 
 
+def _param_array(ps):
+    arr = (flb_params * len(ps))()
+    for k, p in enumerate(ps):
+        arr[k] = make_params(p)
+    return arr
+
+
+def flb_batch_open(basis, max_replicas: int, pool_bytes: int, stream=None):
+    b = C.c_void_p()
+    bs = BASIS[basis] if isinstance(basis, str) else int(basis)
+    _check(load().flb_batch_open(bs, int(max_replicas), int(pool_bytes), _stream_handle(stream),
+                                 C.byref(b)), "flb_batch_open")
+    return b
+
+
+def flb_batch_replica_bytes(p) -> int:
+    s = make_params(p)
+    return int(load().flb_batch_replica_bytes(C.byref(s)))
+
+
+def flb_batch_add(b, p, nsteps: int = 0) -> int:
+    s = make_params(p)
+    slot = C.c_int32()
+    _check(load().flb_batch_add(b, C.byref(s), int(nsteps), C.byref(slot)), "flb_batch_add")
+    return slot.value
+
+
+def flb_batch_remove(b, slot: int) -> None:
+    _check(load().flb_batch_remove(b, int(slot)), "flb_batch_remove")
+
+
+def flb_batch_create(ps, stream=None):
+    arr = _param_array(ps)
+    b = C.c_void_p()
+    _check(load().flb_batch_create(arr, len(ps), _stream_handle(stream), C.byref(b)),
+           "flb_batch_create")
+    return b
+
+
+def flb_batch_workspace_bytes(ps) -> int:
+    arr = _param_array(ps)
+    return int(load().flb_batch_workspace_bytes(arr, len(ps)))
+
+
+def flb_batch_destroy(b) -> None:
+    _check(load().flb_batch_destroy(b), "flb_batch_destroy")
+
+
+def flb_batch_set_sampling(b, slot: int, warmup: int, every: int) -> None:
+    _check(load().flb_batch_set_sampling(b, int(slot), int(warmup), int(every)),
+           "flb_batch_set_sampling")
+
+
+def flb_batch_step(b, n: int) -> None:
+    _check(load().flb_batch_step(b, int(n)), "flb_batch_step")
+
+
+def flb_batch_set_graph(b, steps: int) -> None:
+    _check(load().flb_batch_set_graph(b, int(steps)), "flb_batch_set_graph")
+
+
+def flb_batch_set_tile(b, tile) -> None:
+    v = TILE[tile] if isinstance(tile, str) else int(tile)
+    _check(load().flb_batch_set_tile(b, v), "flb_batch_set_tile")
+
+
+def flb_batch_get_tile(b) -> int:
+    v = C.c_int32()
+    _check(load().flb_batch_get_tile(b, C.byref(v)), "flb_batch_get_tile")
+    return v.value
+
+
+def flb_batch_autotune(b, trial_steps: int):
+    """Returns (chosen tile index, ms per step of every tile shape)."""
+    tile = C.c_int32()
+    ms = np.zeros(TILE_COUNT)
+    _check(load().flb_batch_autotune(b, int(trial_steps), C.byref(tile), _ptr(ms)),
+           "flb_batch_autotune")
+    return tile.value, ms
+
+
+def flb_batch_sync(b) -> None:
+    _check(load().flb_batch_sync(b), "flb_batch_sync")
+
+
+def flb_batch_status(b, slot: int) -> int:
+    """FLB status code of one replica (0 = OK); raises only for a bad slot."""
+    rc = load().flb_batch_status(b, int(slot))
+    if rc == ERR_ARG:
+        raise FlbError(rc, "flb_batch_status")
+    return rc
+
+
+def flb_batch_time(b) -> int:
+    t = C.c_int64()
+    _check(load().flb_batch_time(b, C.byref(t)), "flb_batch_time")
+    return t.value
+
+
+def flb_batch_replica_time(b, slot: int) -> int:
+    t = C.c_int64()
+    _check(load().flb_batch_replica_time(b, int(slot), C.byref(t)), "flb_batch_replica_time")
+    return t.value
+
+
+def flb_batch_info(b):
+    """(live replicas, tiles in the current shape, pool bytes used, pool size)."""
+    n, t = C.c_int32(), C.c_int64()
+    used, size = C.c_size_t(), C.c_size_t()
+    _check(load().flb_batch_info(b, C.byref(n), C.byref(t), C.byref(used), C.byref(size)),
+           "flb_batch_info")
+    return n.value, t.value, used.value, size.value
+
+
+def flb_batch_raw_sums(b, slot: int):
+    S1, S2 = np.zeros(9), np.zeros((9, 9))
+    n = C.c_int64()
+    _check(load().flb_batch_raw_sums(b, int(slot), _ptr(S1), _ptr(S2), C.byref(n)),
+           "flb_batch_raw_sums")
+    return S1, S2, n.value
+
+
+def flb_batch_get_populations(b, slot: int, Lx: int, Ly: int, out=None):
+    if out is None:
+        out = np.empty((9, Ly, Lx))
+    assert out.dtype == np.float64 and out.flags.c_contiguous and out.size == 9 * Lx * Ly
+    _check(load().flb_batch_get_populations(b, int(slot), _ptr(out)), "flb_batch_get_populations")
+    return out
+
+
+def flb_batch_set_populations(b, slot: int, f) -> None:
+    a = np.ascontiguousarray(f, dtype=np.float64)
+    _check(load().flb_batch_set_populations(b, int(slot), _ptr(a)), "flb_batch_set_populations")
+
+
 # ---------------------------------------------------------------------------
 # Convenience object
 # ---------------------------------------------------------------------------
@@ -359,3 +524,100 @@ class Lattice:
 
     def conservation(self):
         return flb_conservation(self.h)
+
+
+class Batch:
+    """Many FP32 lattices stepped by one launch per step (owns an flb_batch).
+
+    ``Batch(params_list)`` adds the given lattices as slots 0..n-1 with no step
+    limit; ``Batch.open(basis, max_replicas, pool_bytes)`` starts empty, for
+    replicas that join and leave (``add`` / ``remove``)."""
+
+    def __init__(self, ps=None, stream=None, graph_steps=0, tile=None, _handle=None):
+        self.params = {}
+        if _handle is not None:
+            self.h = _handle
+        else:
+            self.h = flb_batch_create(list(ps), stream)
+            self.params = {k: p for k, p in enumerate(ps)}
+        if graph_steps:
+            flb_batch_set_graph(self.h, graph_steps)
+        if tile is not None:
+            flb_batch_set_tile(self.h, tile)
+
+    @classmethod
+    def open(cls, basis, max_replicas, pool_bytes, stream=None, graph_steps=0):
+        return cls(stream=stream, graph_steps=graph_steps,
+                   _handle=flb_batch_open(basis, max_replicas, pool_bytes, stream))
+
+    def add(self, p, nsteps=0):
+        slot = flb_batch_add(self.h, p, nsteps)
+        self.params[slot] = p
+        return slot
+
+    def remove(self, slot):
+        flb_batch_remove(self.h, slot)
+        self.params.pop(slot, None)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            flb_batch_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_sampling(self, warmup, every, slot=-1):
+        flb_batch_set_sampling(self.h, slot, warmup, every)
+
+    def step(self, n):
+        flb_batch_step(self.h, n)
+        return self
+
+    def sync(self):
+        flb_batch_sync(self.h)
+
+    def status(self, slot):
+        return flb_batch_status(self.h, slot)
+
+    def set_tile(self, tile):
+        flb_batch_set_tile(self.h, tile)
+
+    @property
+    def tile(self):
+        return flb_batch_get_tile(self.h)
+
+    def autotune(self, trial_steps=20):
+        return flb_batch_autotune(self.h, trial_steps)
+
+    def set_graph(self, steps):
+        flb_batch_set_graph(self.h, steps)
+
+    @property
+    def t(self):
+        return flb_batch_time(self.h)
+
+    def replica_time(self, slot):
+        return flb_batch_replica_time(self.h, slot)
+
+    def info(self):
+        return flb_batch_info(self.h)
+
+    def raw_sums(self, slot):
+        return flb_batch_raw_sums(self.h, slot)
+
+    def populations(self, slot):
+        p = self.params[slot]
+        return flb_batch_get_populations(self.h, slot, p.Lx, p.Ly)
+
+    def set_populations(self, slot, f):
+        flb_batch_set_populations(self.h, slot, f)
