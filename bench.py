@@ -28,6 +28,11 @@ sys.path.insert(0, ROOT)
 METRIC = "MLUPS & % of HBM roofline (FP32 vs FP64); batched replica-steps/s, p50/p99"
 UNIT = "MLUPS"
 BYTES_PER_NODE = {"fp32": 72, "fp64": 144}
+# DRAM bytes (read + write) per launch of the FP32 step kernel at 4096^2,
+# f-norm basis, sampling on: ncu dram__bytes_read.sum + dram__bytes_write.sum
+# of one 2048^2 launch (156.0 + 101.6 MB) scaled by the node count (x4).
+# Valid only for the kernel version it was taken on; None elsewhere.
+DRAM_TRAFFIC = {("fp32", "local", 4096): 4 * (156.027136e6 + 101.609984e6)}
 
 
 def parse():
@@ -51,6 +56,12 @@ def parse():
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched-ensemble comparison added to the JSON line")
     ap.add_argument("--batched-steps", type=int, default=200)
+    ap.add_argument("--workload", default="single", choices=["single", "ensemble"],
+                    help="single: the 4096^2 lattice (with the ensemble comparison added); "
+                         "ensemble: only the batched replica ensemble, as the main line")
+    ap.add_argument("--replicas", type=int, default=256, help="replicas of the ensemble")
+    ap.add_argument("--no-per-lattice", action="store_true",
+                    help="skip the one-launch-per-lattice arm of the ensemble comparison")
     ap.add_argument("--graph-steps", type=int, default=25)
     return ap.parse_args()
 
@@ -165,7 +176,7 @@ def bench_batched(args, stream):
     import torch
 
     from paper_1204_6734_gb300 import flb, inputs
-    ps = inputs.replica_ensemble()
+    ps = inputs.replica_ensemble(n=args.replicas)
     nodes = sum(p.Lx * p.Ly for p in ps)
     out = {"workload": f"{len(ps)} periodic replicas, sides log-uniform in [64, 1024], u_x0 ~ U[0, 0.3], "
                        "kT in {1e-5, 1e-4, 1e-3}, shear rate ~ U[0.6, 1.8], FP32, local basis, "
@@ -175,9 +186,10 @@ def bench_batched(args, stream):
     def timed(fn, k):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
-        e0.record(stream)
-        fn(k)
-        e1.record(stream)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            fn(k)
+            e1.record(stream)
         e1.synchronize()
         return e0.elapsed_time(e1) * 1e-3
 
@@ -201,6 +213,12 @@ def bench_batched(args, stream):
                        "frac": achieved / peak, "peak_kind": kind,
                        "kernel": "batch_step_kernel<local,sample>"}
 
+    if args.no_per_lattice:
+        return out
+    # the same replicas as lattice handles, one launch per lattice and step:
+    # driven from Python (what a caller of the one-lattice API does), and
+    # captured into one CUDA graph (no host overhead left: the GPU cost of
+    # one launch per lattice)
     lats = [flb.Lattice(p, stream=stream, kernel="pipelined") for p in ps]
     try:
         for lat in lats:
@@ -213,16 +231,51 @@ def bench_batched(args, stream):
         per_lattice(2)
         k1 = max(5, args.batched_steps // 10)
         dt1 = timed(per_lattice, k1)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            per_lattice(k1)
+        with torch.cuda.stream(stream):
+            g.replay()
+        dt2 = timed(lambda k: g.replay(), k1)
         for lat in lats:
             lat.sync()
+        del g
     finally:
         for lat in lats:
             lat.close()
     out["one_lattice_per_launch"] = {"replica_steps_per_s": len(ps) * k1 / dt1,
                                      "mlups": nodes * k1 / dt1 / 1e6, "steps": k1,
-                                     "ms_per_step": dt1 / k1 * 1e3, "gpu_launches_per_step": len(ps)}
+                                     "ms_per_step": dt1 / k1 * 1e3, "gpu_launches_per_step": len(ps),
+                                     "driver": "python loop of flb_step"}
+    out["one_lattice_per_launch_graph"] = {"replica_steps_per_s": len(ps) * k1 / dt2,
+                                           "mlups": nodes * k1 / dt2 / 1e6, "steps": k1,
+                                           "ms_per_step": dt2 / k1 * 1e3,
+                                           "gpu_launches_per_step": len(ps),
+                                           "driver": "the same launches captured in one CUDA graph"}
     out["speedup"] = out["replica_steps_per_s"] / out["one_lattice_per_launch"]["replica_steps_per_s"]
+    out["speedup_vs_graph"] = out["replica_steps_per_s"] / \
+        out["one_lattice_per_launch_graph"]["replica_steps_per_s"]
     return out
+
+
+def run_ensemble(args, rank, world, dist, dev):
+    """--workload ensemble: the batched replica ensemble as the main line
+    (replica-steps/s; --steps batch steps timed after --warmup)."""
+    import torch
+    stream = torch.cuda.Stream(device=dev)
+    args.batched_steps = args.steps
+    with ClockSampler(smi_id(dev)) as clk:
+        b = bench_batched(args, stream)
+    if rank == 0:
+        out = {"metric": METRIC, "value": b["replica_steps_per_s"], "unit": "replica-steps/s",
+               "n_gpus": world, "steps": b["steps"], "warmup": args.warmup,
+               "ms_per_step": b["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": b["workload"], "replicas": b["replicas"], "nodes": b["nodes"],
+                          "l2": "inputs larger than L2"},
+               "roofline": b["roofline"], "batched": b, "clocks": clk.summary(),
+               "gpu_launches": b["steps"]}
+        print(json.dumps(out))
 
 
 def run_reference(args):
@@ -275,6 +328,9 @@ def main():
     dev = torch.cuda.current_device()
     flb.load()
 
+    if args.workload == "ensemble":
+        return run_ensemble(args, rank, world, dist, dev)
+
     p = inputs.single_lattice(args.ux0, args.basis, side=args.side, precision=args.precision)
     p.replica = rank                      # independent replica per rank
     p.seed = p.seed + 7919 * rank
@@ -323,9 +379,13 @@ def main():
     pipelined = args.precision == "fp32"
     kname = ("step_tma_kernel<%s,sample>" % args.basis) if pipelined else \
         ("step_kernel<f64,%s,sample>" % args.basis)
+    traffic = DRAM_TRAFFIC.get((args.precision, args.basis, args.side))
+    if args.pipeline_warps or args.pipeline_sampling or args.sample_every != 1:
+        traffic = None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
-                "kernel": kname}
+                "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                "kernel": kname, "algorithmic_bytes": algo_bytes,
+                "traffic_source": "ncu capture at 2048^2 scaled x4" if traffic else None}
 
     Cff, CMM, mean, ns = lat.correlations(args.basis)
     lat.close()
