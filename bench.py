@@ -56,10 +56,17 @@ def parse():
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched-ensemble comparison added to the JSON line")
     ap.add_argument("--batched-steps", type=int, default=200)
-    ap.add_argument("--workload", default="single", choices=["single", "ensemble"],
+    ap.add_argument("--workload", default="single", choices=["single", "ensemble", "serving"],
                     help="single: the 4096^2 lattice (with the ensemble comparison added); "
                          "ensemble: only the batched replica ensemble, as the main line")
     ap.add_argument("--replicas", type=int, default=256, help="replicas of the ensemble")
+    ap.add_argument("--serve-requests", type=int, default=128,
+                    help="requests of the serving trace (its first N) served in each mode")
+    ap.add_argument("--serve-pool-gb", type=float, default=16.0,
+                    help="device pool of the server: the HBM budget admission works against")
+    ap.add_argument("--serve-slots", type=int, default=256)
+    ap.add_argument("--serve-chunk", type=int, default=16)
+    ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-per-lattice", action="store_true",
                     help="skip the one-launch-per-lattice arm of the ensemble comparison")
     ap.add_argument("--graph-steps", type=int, default=25)
@@ -258,6 +265,58 @@ def bench_batched(args, stream):
     return out
 
 
+def serve_trace(args, stream, mode, reqs):
+    """Serve a trace of requests (Poisson arrivals replayed in real time: each
+    is submitted once its arrival time has passed on the server clock) until
+    all have finished. Latency = completion seen by the host - arrival."""
+    from paper_1204_6734_gb300 import flb
+    pool = int(args.serve_pool_gb * (1 << 30))
+    with flb.Server("local", pool, args.serve_slots, args.serve_chunk, mode=mode,
+                    stream=stream) as s:
+        t_start = s.stats()["clock_s"]
+        t_first = reqs[0].arrival_s
+        arrival, results, i, n = {}, [], 0, len(reqs)
+        while len(results) < n:
+            now = s.stats()["clock_s"] - t_start
+            while i < n and reqs[i].arrival_s - t_first <= now:
+                q = reqs[i]
+                rid = s.submit(q.params, q.steps, q.warmup, q.every)
+                arrival[rid] = t_start + q.arrival_s - t_first
+                i += 1
+            got = s.poll(wait=(i == n))
+            results += got
+            if not got and i < n:
+                time.sleep(0.0005)
+        st = s.stats()
+    lat = sorted(r["t_done"] - arrival[r["id"]] for r in results)
+    wall = max(r["t_done"] for r in results) - t_start
+
+    def pct(q):
+        return lat[min(len(lat) - 1, int(math.ceil(q * len(lat))) - 1)]
+    return {"mode": mode, "requests": n, "wall_s": wall,
+            "replica_steps_per_s": st["replica_steps"] / wall,
+            "mlups": st["node_steps"] / wall / 1e6,
+            "latency_p50_s": pct(0.50), "latency_p99_s": pct(0.99), "latency_mean_s": sum(lat) / n,
+            "gpu_busy_s": st["gpu_busy_s"], "chunks": st["chunks"],
+            "failed": sum(1 for r in results if r["status"] != 0)}
+
+
+def bench_serving(args, stream, modes=("batched", "per_lattice")):
+    from paper_1204_6734_gb300 import inputs
+    reqs = inputs.serving_requests()[:args.serve_requests]
+    out = {"workload": f"first {len(reqs)} requests of the serving trace: Poisson arrivals at 200/s, "
+                       "sides log-uniform in [32, 2048], u_x0 ~ U[0, 0.3], kT log-uniform in "
+                       "[1e-5, 1e-3], shear rate ~ U[0.6, 1.8], steps in [500, 20000], FP32, "
+                       "local basis, sampled every step after a tenth of the steps",
+           "pool_gb": args.serve_pool_gb, "slots": args.serve_slots, "chunk_steps": args.serve_chunk,
+           "node_steps": sum(r.steps * r.params.Lx * r.params.Ly for r in reqs)}
+    for m in modes:
+        out[m] = serve_trace(args, stream, m, reqs)
+    if "batched" in out and "per_lattice" in out:
+        out["speedup"] = out["batched"]["replica_steps_per_s"] / out["per_lattice"]["replica_steps_per_s"]
+    return out
+
+
 def run_ensemble(args, rank, world, dist, dev):
     """--workload ensemble: the batched replica ensemble as the main line
     (replica-steps/s; --steps batch steps timed after --warmup)."""
@@ -275,6 +334,25 @@ def run_ensemble(args, rank, world, dist, dev):
                           "l2": "inputs larger than L2"},
                "roofline": b["roofline"], "batched": b, "clocks": clk.summary(),
                "gpu_launches": b["steps"]}
+        print(json.dumps(out))
+
+
+def run_serving(args, rank, world, dist, dev):
+    """--workload serving: the request trace through the server as the main
+    line (replica-steps/s with p50/p99 latency)."""
+    import torch
+    stream = torch.cuda.Stream(device=dev)
+    modes = ("batched",) if args.no_per_lattice else ("batched", "per_lattice")
+    with ClockSampler(smi_id(dev)) as clk:
+        sv = bench_serving(args, stream, modes)
+    if rank == 0:
+        b = sv["batched"]
+        out = {"metric": METRIC, "value": b["replica_steps_per_s"], "unit": "replica-steps/s",
+               "n_gpus": world, "steps": None, "warmup": 0, "ms_per_step": None,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+               "data": "synthetic", "config": {"workload": sv["workload"], "l2": "inputs larger than L2"},
+               "latency_p50_s": b["latency_p50_s"], "latency_p99_s": b["latency_p99_s"],
+               "serving": sv, "clocks": clk.summary()}
         print(json.dumps(out))
 
 
@@ -330,6 +408,8 @@ def main():
 
     if args.workload == "ensemble":
         return run_ensemble(args, rank, world, dist, dev)
+    if args.workload == "serving":
+        return run_serving(args, rank, world, dist, dev)
 
     p = inputs.single_lattice(args.ux0, args.basis, side=args.side, precision=args.precision)
     p.replica = rank                      # independent replica per rank
@@ -410,9 +490,11 @@ def main():
                "d2h_bytes_per_step": (state_bytes + 8 * 90) / args.steps,
                "what": "flb_run_host: pinned host state in, steps with sampling, state + sums out"}
 
-    batched = None
+    batched = serving = None
     if rank == 0 and world == 1 and not args.no_batched and args.precision == "fp32":
         batched = bench_batched(args, stream)
+    if rank == 0 and world == 1 and not args.no_serving and args.precision == "fp32":
+        serving = bench_serving(args, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -439,6 +521,7 @@ def main():
             "mlups_roofline_frac": value / (peak * 1e9 / BYTES_PER_NODE[args.precision] / 1e6) / world,
             "n_samples": ns,
             "batched": batched,
+            "serving": serving,
         }
         print(json.dumps(out))
     if dist is not None:

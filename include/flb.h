@@ -199,11 +199,12 @@ int flb_collide_nodes(const flb_params* p, const double* g, const uint32_t* node
 typedef struct flb_batch_s* flb_batch;
 
 /* Tile shapes of the batched kernel (flb_batch_set_tile, flb_batch_autotune):
- * 128 x 4 nodes, 8 colliding warps, 2 nodes per thread (default);
- * 128 x 6 nodes, 12 colliding warps, 2 nodes per thread;
- * 128 x 2 nodes, 8 colliding warps, 1 node per thread. */
+ * 128 x 4 nodes, 2 nodes per thread (default);
+ * 64 x 8 nodes, 2 nodes per thread (wastes less on narrow lattices);
+ * 128 x 2 nodes, 1 node per thread.
+ * All run 8 colliding warps per CTA and one CTA per SM. */
 #define FLB_TILE_128x4 0
-#define FLB_TILE_128x6 1
+#define FLB_TILE_64x8 1
 #define FLB_TILE_128x2 2
 #define FLB_TILE_COUNT 3
 
@@ -284,6 +285,77 @@ int flb_batch_info(flb_batch b, int32_t* replicas, int64_t* tiles, size_t* pool_
 int flb_batch_raw_sums(flb_batch b, int32_t slot, double* S1, double* S2, int64_t* n_samples);
 int flb_batch_get_populations(flb_batch b, int32_t slot, double* host_out);
 int flb_batch_set_populations(flb_batch b, int32_t slot, const double* host_in);
+
+/* ---------------------------------------------------------------------------
+ * Request server: continuous batching of simulation requests. A request is
+ * one FP32 periodic lattice (flb_params), run for nsteps steps with the given
+ * sampling schedule; its result is its correlation sums. Requests queue in
+ * submission order and are admitted, in that order, as soon as a slot and a
+ * range of the device pool (pool_bytes: the HBM budget) are free; admitted
+ * requests run together and leave when done, while others wait or arrive.
+ * The host enqueues work up to two chunks of `chunk_steps` steps ahead of the
+ * GPU. Like batches, this has no counterpart in the paper.
+ *
+ * Modes: FLB_SERVE_BATCHED runs all admitted requests as one batch (one
+ * launch per step, chunks replayed from a CUDA graph); FLB_SERVE_PER_LATTICE
+ * gives each its own lattice handle (one launch per lattice and step), for
+ * comparison. A request's result does not depend on the mode or on the other
+ * requests, up to the summation order of its sums.
+ * Threading: one thread per server. The stream is the server's.
+ * ------------------------------------------------------------------------- */
+typedef struct flb_server_s* flb_server;
+
+#define FLB_SERVE_BATCHED 0
+#define FLB_SERVE_PER_LATTICE 1
+
+typedef struct {
+    int64_t id;            /* from flb_server_submit */
+    int32_t status;        /* FLB_OK or the request's device error */
+    int32_t reserved;
+    int64_t steps;         /* steps run */
+    int64_t n_samples;     /* sampled node-steps */
+    double S1[9];          /* sums as flb_raw_sums */
+    double S2[81];
+    double t_submit, t_admit, t_done;   /* seconds on the server clock */
+} flb_result;
+
+typedef struct {
+    int64_t submitted, queued;
+    int64_t running;         /* admitted and stepping */
+    int64_t finishing;       /* at their last step, result not yet retired */
+    int64_t completed, pending_results;
+    int64_t chunks;          /* chunks retired */
+    int64_t replica_steps;   /* request-steps in retired chunks */
+    int64_t node_steps;      /* lattice-node updates in retired chunks */
+    int64_t pool_used, pool_size;   /* bytes */
+    double gpu_busy_s;       /* device time of retired chunks (CUDA events) */
+    double clock_s;          /* server clock now: seconds since creation */
+} flb_serve_stats;
+
+/* Errors: FLB_ERR_ARG, FLB_ERR_OOM (pool or page-locked memory), FLB_ERR_CUDA.
+ * max_slots: requests running at once (1 .. 16384). Synchronous. */
+int flb_server_create(int32_t mode, int32_t basis, size_t pool_bytes, int32_t max_slots,
+                      int32_t chunk_steps, void* stream, flb_server* out);
+/* Waits for the stream; results not yet polled are dropped. */
+int flb_server_destroy(flb_server s);
+
+/* Queue a request (p: FP32, the server's basis; nsteps >= 1). *id receives
+ * its id. FLB_ERR_OOM if it could never fit the pool. Returns at once. */
+int flb_server_submit(flb_server s, const flb_params* p, int64_t nsteps, int64_t warmup,
+                      int64_t every, int64_t* id);
+
+/* Make progress: retire completed chunks, admit queued requests, enqueue
+ * chunks; then copy up to max_results finished requests into results and
+ * their count into *n_results. wait != 0: if no result is ready and work is
+ * in flight, block until the oldest chunk completes first. */
+int flb_server_poll(flb_server s, int32_t wait, int32_t max_results, flb_result* results,
+                    int32_t* n_results);
+
+int flb_server_stats(flb_server s, flb_serve_stats* out);
+
+/* Tile shape of a batched server (FLB_TILE_*; default FLB_TILE_64x8).
+ * FLB_ERR_STATE for a per-lattice server. */
+int flb_server_set_tile(flb_server s, int32_t tile);
 
 /* Tuning and testing options of a lattice handle.
  *  FLB_OPT_KERNEL: which step kernel runs -- FLB_KERNEL_AUTO (default: the

@@ -24,11 +24,11 @@
 
 #include "../../include/flb.h"
 #include "flb_arena.h"
-#include "flb_batch_internal.h"
 #include "flb_batch_kernel.cuh"
 #include "flb_host.h"
 #include "flb_internal.h"
 #include "flb_io.cuh"
+#include "flb_runtime.h"
 
 using namespace flb;
 

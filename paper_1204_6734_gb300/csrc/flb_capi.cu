@@ -9,6 +9,7 @@
 
 #include "../../include/flb.h"
 #include "flb_host.h"
+#include "flb_runtime.h"
 #include "flb_internal.h"
 #include "flb_io.cuh"
 #include "flb_kernels.cuh"
@@ -327,31 +328,10 @@ int check_device_error(flb_lattice h) {
 
 }  // namespace
 
-extern "C" {
+namespace flb {
 
-int flb_version(void) { return 100; }
-
-const char* flb_error_string(int code) {
-    switch (code) {
-        case FLB_OK: return "ok";
-        case FLB_ERR_ARG: return "invalid argument";
-        case FLB_ERR_OOM: return "out of device memory or workspace too small";
-        case FLB_ERR_INVALID_VELOCITY: return "a node velocity left the region where all f_i^0(1,u) > 0";
-        case FLB_ERR_NONFINITE: return "non-finite or non-positive density at a node";
-        case FLB_ERR_TIMEOUT: return "a bounded device wait timed out";
-        case FLB_ERR_CUDA: return "CUDA runtime error";
-        case FLB_ERR_STATE: return "call not valid in the current state";
-        default: return "unknown error";
-    }
-}
-
-size_t flb_workspace_bytes(const flb_params* p) {
-    if (!valid_params(p)) return 0;
-    return layout(p, device_sms()).total;
-}
-
-int flb_create(const flb_params* p, void* dev_workspace, size_t workspace_bytes, void* stream,
-               flb_lattice* out) {
+int lattice_create(const flb_params* p, void* dev_workspace, size_t workspace_bytes,
+                   cudaStream_t stream, bool sync, flb_lattice* out) {
     if (!out) return FLB_ERR_ARG;
     *out = nullptr;
     if (!valid_params(p)) return FLB_ERR_ARG;
@@ -362,8 +342,8 @@ int flb_create(const flb_params* p, void* dev_workspace, size_t workspace_bytes,
     if (!h) return FLB_ERR_OOM;
     h->p = *p;
     h->elem = elem_size(p->precision);
-    h->geo = make_geometry(p);
-    h->stream = (cudaStream_t)stream;
+    h->geo = flb::make_geometry(p->Lx, p->Ly);
+    h->stream = stream;
     if (dev_workspace) {
         if (workspace_bytes < L.total || ((uintptr_t)dev_workspace % kAlign) != 0) {
             delete h;
@@ -406,7 +386,7 @@ int flb_create(const flb_params* p, void* dev_workspace, size_t workspace_bytes,
                 (float*)h->buf[0], h->geo, v);
         ce = cudaGetLastError();
     }
-    if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
+    if (ce == cudaSuccess && sync) ce = cudaStreamSynchronize(h->stream);
     h->tma.sample_mode = 0;   // library default
     if (ce == cudaSuccess && p->precision == FLB_FP32)
         ce = tma_plan(&h->tma, h->buf[0], h->buf[1], h->geo, 0);
@@ -418,6 +398,53 @@ int flb_create(const flb_params* p, void* dev_workspace, size_t workspace_bytes,
     }
     *out = h;
     return FLB_OK;
+}
+
+int lattice_enqueue_readout(flb_lattice h, double* acc_out, DevError* err_out) {
+    if (!h) return FLB_ERR_ARG;
+    cudaError_t ce = cudaMemcpyAsync(acc_out, h->acc, sizeof(double) * kSums,
+                                     cudaMemcpyDeviceToHost, h->stream);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(err_out, h->err, sizeof(DevError), cudaMemcpyDeviceToHost, h->stream);
+    return cuda_rc(ce);
+}
+
+int64_t lattice_samples(flb_lattice h) { return h ? h->nsamp : 0; }
+
+int64_t lattice_time(flb_lattice h) { return h ? h->t : -1; }
+
+void lattice_forget(flb_lattice h) {
+    if (h && !h->own_ws) delete h;
+}
+
+}  // namespace flb
+
+extern "C" {
+
+int flb_version(void) { return 100; }
+
+const char* flb_error_string(int code) {
+    switch (code) {
+        case FLB_OK: return "ok";
+        case FLB_ERR_ARG: return "invalid argument";
+        case FLB_ERR_OOM: return "out of device memory or workspace too small";
+        case FLB_ERR_INVALID_VELOCITY: return "a node velocity left the region where all f_i^0(1,u) > 0";
+        case FLB_ERR_NONFINITE: return "non-finite or non-positive density at a node";
+        case FLB_ERR_TIMEOUT: return "a bounded device wait timed out";
+        case FLB_ERR_CUDA: return "CUDA runtime error";
+        case FLB_ERR_STATE: return "call not valid in the current state";
+        default: return "unknown error";
+    }
+}
+
+size_t flb_workspace_bytes(const flb_params* p) {
+    if (!valid_params(p)) return 0;
+    return layout(p, device_sms()).total;
+}
+
+int flb_create(const flb_params* p, void* dev_workspace, size_t workspace_bytes, void* stream,
+               flb_lattice* out) {
+    return lattice_create(p, dev_workspace, workspace_bytes, (cudaStream_t)stream, true, out);
 }
 
 int flb_destroy(flb_lattice h) {

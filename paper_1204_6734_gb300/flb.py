@@ -44,6 +44,22 @@ class flb_params(C.Structure):
                 ("seed", C.c_uint64), ("replica", C.c_uint32), ("reserved", C.c_uint32)]
 
 
+class flb_result(C.Structure):
+    _fields_ = [("id", C.c_int64), ("status", C.c_int32), ("reserved", C.c_int32),
+                ("steps", C.c_int64), ("n_samples", C.c_int64), ("S1", C.c_double * 9),
+                ("S2", C.c_double * 81), ("t_submit", C.c_double), ("t_admit", C.c_double),
+                ("t_done", C.c_double)]
+
+
+class flb_serve_stats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("queued", C.c_int64), ("running", C.c_int64),
+                ("finishing", C.c_int64), ("completed", C.c_int64), ("pending_results", C.c_int64), ("chunks", C.c_int64),
+                ("replica_steps", C.c_int64), ("node_steps", C.c_int64), ("pool_used", C.c_int64),
+                ("pool_size", C.c_int64), ("gpu_busy_s", C.c_double), ("clock_s", C.c_double)]
+
+
+SERVE = {"batched": 0, "per_lattice": 1}
+
 _lib = None
 _dp = C.POINTER(C.c_double)
 _i64p = C.POINTER(C.c_int64)
@@ -114,6 +130,13 @@ def load(build_if_missing: bool = True):
         "flb_batch_raw_sums": (C.c_int, [h, C.c_int32, _dp, _dp, _i64p]),
         "flb_batch_get_populations": (C.c_int, [h, C.c_int32, _dp]),
         "flb_batch_set_populations": (C.c_int, [h, C.c_int32, _dp]),
+        "flb_server_create": (C.c_int, [C.c_int32, C.c_int32, C.c_size_t, C.c_int32, C.c_int32,
+                                        C.c_void_p, C.POINTER(h)]),
+        "flb_server_destroy": (C.c_int, [h]),
+        "flb_server_submit": (C.c_int, [h, P, C.c_int64, C.c_int64, C.c_int64, _i64p]),
+        "flb_server_poll": (C.c_int, [h, C.c_int32, C.c_int32, C.POINTER(flb_result), _i32p]),
+        "flb_server_stats": (C.c_int, [h, C.POINTER(flb_serve_stats)]),
+        "flb_server_set_tile": (C.c_int, [h, C.c_int32]),
         "flb_error_string": (C.c_char_p, [C.c_int]),
         "flb_version": (C.c_int, []),
     }
@@ -138,7 +161,9 @@ def exported_symbols():
             "flb_batch_set_graph", "flb_batch_set_tile", "flb_batch_get_tile",
             "flb_batch_autotune", "flb_batch_sync", "flb_batch_status", "flb_batch_time",
             "flb_batch_replica_time", "flb_batch_info", "flb_batch_raw_sums",
-            "flb_batch_get_populations", "flb_batch_set_populations"]
+            "flb_batch_get_populations", "flb_batch_set_populations", "flb_server_create",
+            "flb_server_destroy", "flb_server_submit", "flb_server_poll", "flb_server_stats",
+            "flb_server_set_tile"]
 
 
 def _check(rc: int, what: str):
@@ -461,6 +486,54 @@ def flb_batch_set_populations(b, slot: int, f) -> None:
     _check(load().flb_batch_set_populations(b, int(slot), _ptr(a)), "flb_batch_set_populations")
 
 
+def flb_server_create(mode, basis, pool_bytes: int, max_slots: int, chunk_steps: int, stream=None):
+    s = C.c_void_p()
+    m = SERVE[mode] if isinstance(mode, str) else int(mode)
+    bs = BASIS[basis] if isinstance(basis, str) else int(basis)
+    _check(load().flb_server_create(m, bs, int(pool_bytes), int(max_slots), int(chunk_steps),
+                                    _stream_handle(stream), C.byref(s)), "flb_server_create")
+    return s
+
+
+def flb_server_destroy(s) -> None:
+    _check(load().flb_server_destroy(s), "flb_server_destroy")
+
+
+def flb_server_submit(s, p, nsteps: int, warmup: int = 0, every: int = 0) -> int:
+    q = make_params(p)
+    rid = C.c_int64()
+    _check(load().flb_server_submit(s, C.byref(q), int(nsteps), int(warmup), int(every),
+                                    C.byref(rid)), "flb_server_submit")
+    return rid.value
+
+
+def flb_server_poll(s, wait: bool = False, max_results: int = 64):
+    """List of finished requests as dicts (id, status, steps, n_samples, S1,
+    S2, t_submit, t_admit, t_done)."""
+    buf = (flb_result * max_results)()
+    n = C.c_int32()
+    _check(load().flb_server_poll(s, 1 if wait else 0, max_results, buf, C.byref(n)),
+           "flb_server_poll")
+    out = []
+    for k in range(n.value):
+        r = buf[k]
+        out.append({"id": r.id, "status": r.status, "steps": r.steps, "n_samples": r.n_samples,
+                    "S1": np.array(r.S1[:]), "S2": np.array(r.S2[:]).reshape(9, 9),
+                    "t_submit": r.t_submit, "t_admit": r.t_admit, "t_done": r.t_done})
+    return out
+
+
+def flb_server_set_tile(s, tile) -> None:
+    v = TILE[tile] if isinstance(tile, str) else int(tile)
+    _check(load().flb_server_set_tile(s, v), "flb_server_set_tile")
+
+
+def flb_server_stats(s) -> dict:
+    st = flb_serve_stats()
+    _check(load().flb_server_stats(s, C.byref(st)), "flb_server_stats")
+    return {name: getattr(st, name) for name, _ in flb_serve_stats._fields_}
+
+
 # ---------------------------------------------------------------------------
 # Convenience object
 # ---------------------------------------------------------------------------
@@ -621,3 +694,49 @@ class Batch:
 
     def set_populations(self, slot, f):
         flb_batch_set_populations(self.h, slot, f)
+
+
+class Server:
+    """Continuous-batching request server (owns an flb_server)."""
+
+    def __init__(self, basis="local", pool_bytes=1 << 30, max_slots=256, chunk_steps=16,
+                 mode="batched", stream=None):
+        self.h = flb_server_create(mode, basis, pool_bytes, max_slots, chunk_steps, stream)
+
+    def submit(self, p, nsteps, warmup=0, every=0):
+        return flb_server_submit(self.h, p, nsteps, warmup, every)
+
+    def poll(self, wait=False, max_results=64):
+        return flb_server_poll(self.h, wait, max_results)
+
+    def stats(self):
+        return flb_server_stats(self.h)
+
+    def set_tile(self, tile):
+        flb_server_set_tile(self.h, tile)
+
+    def drain(self):
+        """Poll (blocking) until every submitted request has a result."""
+        out = []
+        while True:
+            st = self.stats()
+            if st["completed"] == st["submitted"] and st["pending_results"] == 0:
+                return out
+            out += self.poll(wait=True)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            flb_server_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -111,13 +111,16 @@ class Request:
     arrival_s: float
     params: LatticeParams
     steps: int
+    warmup: int = 0     # correlations sampled every `every` steps from `warmup` on
+    every: int = 1
 
 
 def serving_requests(n: int = 10_000, rate_hz: float = 200.0, seed: int = 5,
                      lo: int = 32, hi: int = 2048, basis: str = LOCAL) -> List[Request]:
     """Poisson arrivals; sides log-uniform in [lo, hi]; u_x0 ~ U[0, 0.3];
     kT log-uniform in [1e-5, 1e-3]; shear rate ~ U[0.6, 1.8]; steps uniform
-    integers in [500, 20000]; seed = request id."""
+    integers in [500, 20000]; seed = request id. Each request samples its
+    correlations on every step after a warm-up of a tenth of its steps."""
     g = np.random.Generator(np.random.PCG64(seed))
     t = 0.0
     out = []
@@ -131,7 +134,7 @@ def serving_requests(n: int = 10_000, rate_hz: float = 200.0, seed: int = 5,
         steps = int(g.integers(500, 20001))
         p = LatticeParams(Lx, Ly, 1.0, ux0, 0.0, kT, omega_groups(ws, 1.0, 1.0), basis,
                           "fp32", seed=rid, replica=rid)
-        out.append(Request(rid, t, p, steps))
+        out.append(Request(rid, t, p, steps, warmup=steps // 10, every=1))
     return out
 
 
