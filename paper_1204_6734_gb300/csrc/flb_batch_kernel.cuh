@@ -177,7 +177,7 @@ batch_step_kernel(const BatchArgs a) {
             if (producer) {
                 for (; k < ntile && issued < ntile; ++k) {
                     const int s = k % S;
-                    if (!mbar_wait(&empty[s], (k / S) & 1)) {
+                    if (!mbar_wait_sleep(&empty[s], (k / S) & 1)) {
                         ok = false;
                         break;
                     }
@@ -216,7 +216,7 @@ batch_step_kernel(const BatchArgs a) {
         };
         for (; k < ntile && ok; ++k) {
             const int s = k % S, n = k / S;
-            if (!mbar_wait(&full[s], n & 1)) {
+            if (!mbar_wait_sleep(&full[s], n & 1)) {
                 ok = false;
                 break;
             }
@@ -272,7 +272,7 @@ batch_step_kernel(const BatchArgs a) {
                 if (lane_id == 0) mbar_arrive(&empty[s]);
             }
             if (producer && issued < ntile) {
-                if (!mbar_wait(&empty[s], n & 1)) {
+                if (!mbar_wait_sleep(&empty[s], n & 1)) {
                     ok = false;
                     break;
                 }

@@ -208,7 +208,6 @@ struct flb_lattice_s {
     double* acc;         // kSums running sums
     double* small;       // basis (81) + finalize output (171) + conservation (3)
     DevError* err;
-    unsigned int* ticket;  // CTA completion counter of the pipelined kernel
     cudaStream_t stream;
     int64_t t, warmup, every, nsamp;
     int sticky;
@@ -242,7 +241,7 @@ int step_grid(const Geometry& g, int sms) {
 }
 
 struct Layout {
-    size_t buf_bytes, partial_off, acc_off, small_off, err_off, ticket_off, total;
+    size_t buf_bytes, partial_off, acc_off, small_off, err_off, total;
     int nblocks, npartials;
 };
 
@@ -252,7 +251,7 @@ Layout layout(const flb_params* p, int sms) {
     L.nblocks = step_grid(g, sms);
     L.buf_bytes = align_up((size_t)(9 * g.plane) * elem_size(p->precision));
     size_t off = 2 * L.buf_bytes;
-    L.npartials = L.nblocks > tma_max_grid(sms) ? L.nblocks : tma_max_grid(sms);
+    L.npartials = L.nblocks;
     L.partial_off = off;
     off += align_up(sizeof(double) * (size_t)L.npartials * kSums);
     L.acc_off = off;
@@ -261,8 +260,6 @@ Layout layout(const flb_params* p, int sms) {
     off += align_up(sizeof(double) * (81 + 171 + 3 + 3 * (size_t)L.nblocks));
     L.err_off = off;
     off += align_up(sizeof(DevError));
-    L.ticket_off = off;
-    off += align_up(sizeof(unsigned int));
     L.total = off;
     return L;
 }
@@ -299,9 +296,7 @@ cudaError_t launch_step_tma(flb_lattice h, bool sample) {
     a.geo = h->geo;
     a.step = (uint32_t)h->t;
     a.tiles_x = a.ntiles = 0;
-    a.partials = h->partials;
     a.acc = h->acc;
-    a.ticket = h->ticket;
     a.err = h->err;
     for (int i = 0; i < 9; ++i) a.ref[i] = (float)h->ref[i];
     return tma_step(h->tma, h->cur, a, collide_const<float>(&h->p), h->p.basis, sample, h->stream);
@@ -368,7 +363,6 @@ int lattice_create(const flb_params* p, void* dev_workspace, size_t workspace_by
     h->acc = (double*)(h->ws + L.acc_off);
     h->small = (double*)(h->ws + L.small_off);
     h->err = (DevError*)(h->ws + L.err_off);
-    h->ticket = (unsigned int*)(h->ws + L.ticket_off);
     h->nblocks = L.nblocks;
     h->variant = FLB_KERNEL_AUTO;
     h->cur = 0;

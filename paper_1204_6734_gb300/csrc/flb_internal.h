@@ -14,9 +14,7 @@ struct TmaArgs {
     Geometry geo;
     uint32_t step;
     int tiles_x, ntiles;    // 128 x TH tiles of the lattice
-    double* partials;       // [grid][kSums] per-CTA FP64 sums (sampling)
     double* acc;            // running FP64 sums (sampling)
-    unsigned int* ticket;   // CTA completion counter, zero between launches
     DevError* err;
     float ref[9];           // f^0(rho0, u0) subtracted before sampling
 };
@@ -39,10 +37,6 @@ cudaError_t tma_plan(TmaPlan* plan, void* buf0, void* buf1, const Geometry& g, i
 // Tensor map of the nine planes of one FP32 buffer (ghost-frame layout), seen
 // as one 2D array of pitch x 9 (Ly + 2) elements, for boxes of box_w x th.
 cudaError_t tma_encode_planes(CUtensorMap* map, void* buf, const Geometry& g, int box_w, int th);
-
-// Grid (CTAs) the plan launches with the given consumer-warp count, for sizing
-// the per-CTA partial sums before the buffers exist.
-int tma_max_grid(int sms);
 
 // One fused step from buffer `src` into a.dst. basis: 0 Hermite, 1 f-norm.
 cudaError_t tma_step(const TmaPlan& plan, int src, const TmaArgs& a,

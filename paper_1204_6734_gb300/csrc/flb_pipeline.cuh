@@ -32,7 +32,7 @@ struct TileShape {
     static constexpr int RED = NW > kSamplers ? NW : kSamplers;        // warps reducing
     static constexpr size_t smem_bytes() {
         return sizeof(float) * (size_t)STAGES * STAGE + 2 * STAGES * sizeof(uint64_t) +
-               sizeof(double) * RED * kSums + 16;
+               sizeof(double) * RED * kSums;
     }
 };
 
@@ -44,12 +44,14 @@ __device__ __forceinline__ void store_lane(float* dst, const Geometry& geo, int 
     store_node(dst, geo, x, y, v);
 }
 
-// CTA and grid reduction of per-thread correlation sums held by `group`
-// threads (warps [w0, w0 + group/32)): warp shuffles, FP64 across warps into
-// this CTA's partials, then the last CTA to finish adds all CTA partials in a
-// fixed order to the running sums.
+// CTA reduction of per-thread correlation sums held by `group` threads (warps
+// [w0, w0 + group/32)): warp shuffles, FP64 across warps in warp order, then
+// one FP64 atomic add per sum and CTA into the running sums. The order in which
+// CTAs add is not fixed, so the last bits of the FP64 sums may differ between
+// runs; a deterministic last-CTA reduction was measured to hold one SM for
+// 15-25 us at the end of every sampled step.
 __device__ __forceinline__ void publish_sums(const float (&v)[kSums], int w0, int group,
-                                             double* red, int* flag, const TmaArgs& a) {
+                                             double* red, const TmaArgs& a) {
     const int warp = threadIdx.x >> 5, lane_id = threadIdx.x & 31;
     const int nw = group / 32, c = threadIdx.x - 32 * w0;
 #pragma unroll
@@ -63,19 +65,7 @@ __device__ __forceinline__ void publish_sums(const float (&v)[kSums], int w0, in
     if (c < kSums) {
         double tot = 0.0;
         for (int w = 0; w < nw; ++w) tot += red[w * kSums + c];
-        a.partials[(size_t)blockIdx.x * kSums + c] = tot;
-    }
-    __threadfence();
-    named_sync(1, group);
-    if (c == 0) *flag = (atomicAdd(a.ticket, 1u) == gridDim.x - 1) ? 1 : 0;
-    named_sync(1, group);
-    if (*flag) {
-        __threadfence();
-        for (int q = warp - w0; q < kSums; q += nw) {
-            const double s = reduce_partials(a.partials, q, gridDim.x, lane_id);
-            if (lane_id == 0) a.acc[q] += s;
-        }
-        if (c == 0) *a.ticket = 0u;
+        atomicAdd(&a.acc[c], tot);
     }
 }
 

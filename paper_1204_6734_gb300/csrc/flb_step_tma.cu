@@ -14,9 +14,8 @@
 // With sampling on, TH sampler warps (one per tile row) read the same stage and
 // accumulate the 9 + 45 correlation sums in packed FP32x2 registers while the
 // consumers collide; the first sampler lane also issues the TMA loads. At the
-// end the CTA reduces the sums to FP64 partials and the last CTA to finish adds
-// all partials, in CTA order, to the running sums: deterministic, with no
-// separate reduction launch.
+// end the CTA reduces the sums to FP64 and adds them to the running sums with
+// FP64 atomics: no separate reduction launch and no serial tail.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -63,7 +62,7 @@ struct Producer {
         if (!ok) return;
         const int tn = blockIdx.x + issued * gridDim.x;
         if (tn >= a.ntiles) return;
-        if (!mbar_wait(&empty[s], n & 1)) {
+        if (!mbar_wait_sleep(&empty[s], n & 1)) {
             record_error(a.err, kStatusTimeout, -1, a.step);
             ok = false;
             return;
@@ -121,7 +120,6 @@ step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * TS::STAGE);
     uint64_t* empty = full + kStages;
     double* red = reinterpret_cast<double*>(empty + kStages);
-    int* flag = reinterpret_cast<int*>(red + TS::RED * kSums);
 
     const int warp = threadIdx.x >> 5, lane_id = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -162,7 +160,7 @@ step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
         int k = 0;
         for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++k) {
             const int s = k % kStages, n = k / kStages;
-            if (!mbar_wait(&full[s], n & 1)) {
+            if (!mbar_wait_sleep(&full[s], n & 1)) {
                 record_error(a.err, kStatusTimeout, -1, a.step);
                 break;
             }
@@ -214,7 +212,7 @@ step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
             const f2 x = q < 9 ? s1[q] : s2[q - 9];
             v[q] = x.v.x + x.v.y;
         }
-        publish_sums(v, NW, NX * 32, red, flag, a);
+        publish_sums(v, NW, NX * 32, red, a);
         return;
     }
 
@@ -268,19 +266,28 @@ step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
         // the stage is held until g was read the second time
         __syncwarp();
         if (lane_id == 0) mbar_arrive(&empty[s]);
-        if (inA) {
-            if (stt & 0xFF) record_error(a.err, (int)(stt & 0xFF), nodeA, a.step);
-            store_lane(a.dst, a.geo, xA, y, f, 0);
+        if (stt) {
+            if (inA && (stt & 0xFF)) record_error(a.err, (int)(stt & 0xFF), nodeA, a.step);
+            if (inB && (stt >> 8)) record_error(a.err, (int)(stt >> 8), nodeA + 64u, a.step);
         }
-        if (inB) {
-            if (stt >> 8) record_error(a.err, (int)(stt >> 8), nodeA + 64u, a.step);
-            store_lane(a.dst, a.geo, xB, y, f, 1);
+        // tiles away from the lattice edge store without per-node checks
+        const int x0t = xA - r, y0t = y - ty;
+        if (x0t > 0 && y0t > 0 && x0t + kTW < Lx && y0t + TH < Ly) {
+            float* pa = a.dst + at(a.geo, 0, xA, y);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                pa[i * a.geo.plane] = f[i].v.x;
+                pa[i * a.geo.plane + 64] = f[i].v.y;
+            }
+        } else {
+            if (inA) store_lane(a.dst, a.geo, xA, y, f, 0);
+            if (inB) store_lane(a.dst, a.geo, xB, y, f, 1);
         }
         if (producer) prod.refill(smem, &map, a, full, empty, s, n);
     }
     if (kFused) {
         if (producer) prod.drain(a, full, k);
-        publish_sums(reinterpret_cast<float(&)[kSums]>(v), 0, NW * 32, red, flag, a);
+        publish_sums(reinterpret_cast<float(&)[kSums]>(v), 0, NW * 32, red, a);
     }
 }
 
@@ -346,8 +353,6 @@ size_t smem_for(int nw) {
 }
 
 }  // namespace
-
-int tma_max_grid(int sms) { return sms * 2; }
 
 cudaError_t tma_encode_planes(CUtensorMap* map, void* buf, const Geometry& g, int box_w, int th) {
     EncodeFn enc = encode_fn();

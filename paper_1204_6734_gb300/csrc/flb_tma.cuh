@@ -62,6 +62,24 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     return true;
 }
 
+// Wait for warps that run ahead of the colliding warps (sampler warps, the
+// producer) and would otherwise poll for most of a tile: between polls the
+// warp sleeps, with the pause doubling from 32 ns up to kSleepMaxNs, so it
+// takes almost no issue slots from the colliding warps. False on timeout.
+constexpr unsigned kSleepMaxNs = 1024;
+
+__device__ __forceinline__ bool mbar_wait_sleep(uint64_t* bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    unsigned ns = 32;
+    while (!mbar_try_wait(bar, parity)) {
+        __nanosleep(ns);
+        ns = ns < kSleepMaxNs ? 2 * ns : kSleepMaxNs;
+        if (clock64() - t0 > kWaitCycles) return false;
+    }
+    return true;
+}
+
 // 2D tiled TMA load of the box at (x, y) into shared memory, completing on bar.
 // x * element size must be a multiple of 16 bytes.
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
