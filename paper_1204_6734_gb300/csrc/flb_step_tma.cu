@@ -28,13 +28,33 @@
 
 namespace flb {
 
-// Issue the nine TMA box loads of tile t into stage s (one thread).
+// Tile coordinates (tx, ty) of t = blockIdx.x + k gridDim.x, k = 0, 1, ...,
+// advanced without a division per tile.
+struct TileWalk {
+    int tx, ty, dx, dy, nx;
+    __device__ __forceinline__ TileWalk(int t0, int step, int tiles_x) : nx(tiles_x) {
+        ty = t0 / nx;
+        tx = t0 - ty * nx;
+        dy = step / nx;
+        dx = step - dy * nx;
+    }
+    __device__ __forceinline__ void next() {
+        tx += dx;
+        ty += dy;
+        if (tx >= nx) {
+            tx -= nx;
+            ++ty;
+        }
+    }
+};
+
+// Issue the nine TMA box loads of tile (tx, ty) into stage s (one thread).
 template <int NW>
 __device__ __forceinline__ void issue_tile(float* smem, const CUtensorMap* map, const TmaArgs& a,
-                                           int t, int s, uint64_t* full) {
+                                           int tx, int ty, int s, uint64_t* full) {
     using TS = TileShape<NW>;
     mbar_arrive_expect_tx(&full[s], 9u * TS::TH * kBoxW * sizeof(float));
-    const int x0 = (t % a.tiles_x) * kTW, y0 = (t / a.tiles_x) * TS::TH;
+    const int x0 = tx * kTW, y0 = ty * TS::TH;
     float* st = smem + s * TS::STAGE;
 #pragma unroll
     for (int i = 0; i < 9; ++i)
@@ -43,18 +63,34 @@ __device__ __forceinline__ void issue_tile(float* smem, const CUtensorMap* map, 
 }
 
 // Producer state of an elected thread that refills each stage once every warp
-// has released it. Stage s holds tiles s, s + STAGES, ... of this CTA.
-template <int NW>
+// has released it. Stage s holds tiles s, s + STAGES, ... of this CTA. WALK:
+// tile coordinates by TileWalk rather than a division per tile (which of the
+// two schedules faster differs between the two bases' kernels, by measurement).
+template <int NW, bool WALK>
 struct Producer {
     int issued = 0;
     bool ok = true;
+    TileWalk walk;   // the next tile to issue (WALK)
+
+    __device__ __forceinline__ explicit Producer(const TmaArgs& a)
+        : walk(blockIdx.x, gridDim.x, a.tiles_x) {}
+
+    __device__ __forceinline__ void issue(float* smem, const CUtensorMap* map, const TmaArgs& a,
+                                          int t, int s, uint64_t* full) {
+        if (WALK) {
+            issue_tile<NW>(smem, map, a, walk.tx, walk.ty, s, full);
+            walk.next();
+        } else {
+            issue_tile<NW>(smem, map, a, t % a.tiles_x, t / a.tiles_x, s, full);
+        }
+    }
 
     __device__ __forceinline__ void prologue(float* smem, const CUtensorMap* map,
                                              const TmaArgs& a, uint64_t* full) {
         prefetch_tensormap(map);
         for (int t = blockIdx.x; t < a.ntiles && issued < TileShape<NW>::STAGES;
              t += gridDim.x, ++issued)
-            issue_tile<NW>(smem, map, a, t, issued, full);
+            issue(smem, map, a, t, issued, full);
     }
     // after this CTA's k-th tile (stage s, use n) was released by the caller
     __device__ __forceinline__ void refill(float* smem, const CUtensorMap* map, const TmaArgs& a,
@@ -67,7 +103,7 @@ struct Producer {
             ok = false;
             return;
         }
-        issue_tile<NW>(smem, map, a, tn, s, full);
+        issue(smem, map, a, tn, s, full);
         ++issued;
     }
     // no copy may be in flight when the CTA exits: wait for tiles issued but not
@@ -116,6 +152,7 @@ step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
     constexpr int TH = TS::TH;
     constexpr int kStages = TS::STAGES;
     constexpr int NX = WarpCount<MODE>::template extra<NW>();
+    constexpr bool kWalk = BASIS == 0;   // see Producer
     extern __shared__ __align__(128) float smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * TS::STAGE);
     uint64_t* empty = full + kStages;
@@ -136,7 +173,7 @@ step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
     if (MODE == kNoSampling && warp == NW) {
         // ---------------- producer warp
         if (lane_id == 0) {
-            Producer<NW> prod;
+            Producer<NW, kWalk> prod(a);
             prod.prologue(smem, &map, a, full);
             int k = 0;
             for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++k)
@@ -150,7 +187,7 @@ step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
         // ---------------- sampler warps
         const int sw = warp - NW;
         const bool producer = sw == 0 && lane_id == 0;
-        Producer<NW> prod;
+        Producer<NW, kWalk> prod(a);
         if (producer) prod.prologue(smem, &map, a, full);
         f2 s1[9], s2[45];
 #pragma unroll
@@ -158,15 +195,16 @@ step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
 #pragma unroll
         for (int q = 0; q < 45; ++q) s2[q] = f2(0.f);
         int k = 0;
-        for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++k) {
+        TileWalk w(blockIdx.x, gridDim.x, a.tiles_x);
+        for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++k, w.next()) {
             const int s = k % kStages, n = k / kStages;
             if (!mbar_wait_sleep(&full[s], n & 1)) {
                 record_error(a.err, kStatusTimeout, -1, a.step);
                 break;
             }
-            const int x0 = (t % a.tiles_x) * kTW;
+            const int x0 = (kWalk ? w.tx : t % a.tiles_x) * kTW;
             for (int row = sw; row < TH; row += NX) {
-                const int y = (t / a.tiles_x) * TH + row;
+                const int y = (kWalk ? w.ty : t / a.tiles_x) * TH + row;
                 const float* st = smem + s * TS::STAGE + row * kBoxW + 4 + lane_id;
                 f2 d[2][9];
 #pragma unroll
@@ -221,7 +259,7 @@ step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
     const int ty = c >> 6, r = c & 63;
     constexpr bool kFused = MODE == kFusedSampling;
     const bool producer = kFused && c == 0;
-    Producer<NW> prod;
+    Producer<NW, kWalk> prod(a);
     if (producer) prod.prologue(smem, &map, a, full);
     float v[kFused ? kSums : 1];
     if (kFused) {
@@ -229,7 +267,8 @@ step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
         for (int q = 0; q < kSums; ++q) v[q] = 0.f;
     }
     int k = 0;
-    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++k) {
+    TileWalk w(blockIdx.x, gridDim.x, a.tiles_x);
+    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++k, w.next()) {
         const int s = k % kStages, n = k / kStages;
         if (!mbar_wait(&full[s], n & 1)) {
             record_error(a.err, kStatusTimeout, -1, a.step);
@@ -246,7 +285,8 @@ step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
         f2 g[9];
         load(g);
 
-        const int x0 = (t % a.tiles_x) * kTW, y = (t / a.tiles_x) * TH + ty;
+        const int x0 = (kWalk ? w.tx : t % a.tiles_x) * kTW;
+        const int y = (kWalk ? w.ty : t / a.tiles_x) * TH + ty;
         const int xA = x0 + r, xB = xA + 64;
         const bool inA = xA < Lx && y < Ly, inB = xB < Lx && y < Ly;
         if (kFused) {
