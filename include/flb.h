@@ -70,8 +70,10 @@ typedef struct {
     double omega[9];     /* relaxation rate 1/tau^a of moment a; entries 0..2
                             (conserved) are ignored, 3..8 must lie in (0, 2) */
     int32_t basis;       /* flb_basis */
-    int32_t precision;   /* flb_precision: FP64 and FP32 compute in that type;
-                            FP16_DEV is reserved */
+    int32_t precision;   /* flb_precision: FP64 and FP32 store and compute in
+                            that type; FP16_DEV stores h_i = (f_i - f_i^0(rho0,
+                            u0)) / sqrt(kT) in FP16 (kT > 0 required) and
+                            computes in FP32 */
     uint64_t seed;       /* Philox key */
     uint32_t replica;    /* third Philox counter word */
     uint32_t reserved;   /* must be 0 */
@@ -154,6 +156,13 @@ int flb_get_populations(flb_lattice h, double* host_out);
  * doubles, layout above; converted to the handle's precision). Clears a
  * recorded device error. Synchronises. */
 int flb_set_populations(flb_lattice h, const double* host_in);
+
+/* Difference of the current pre-collision states of two lattices of the same
+ * size, in any precisions, computed on the device: out[0] = max |f_a - f_b|,
+ * out[1] = root mean square of f_a - f_b over all 9 Lx Ly values, out[2] =
+ * max |f_b|. No counterpart in the paper: it serves the precision study.
+ * Synchronises both handles' streams. Errors: FLB_ERR_ARG (sizes differ). */
+int flb_state_difference(flb_lattice a, flb_lattice b, double out[3]);
 
 /* Whole-job entry point with host buffers: create a lattice, upload the
  * initial state (or start from equilibrium when f_in is NULL), run nsteps

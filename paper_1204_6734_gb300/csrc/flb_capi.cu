@@ -2,10 +2,12 @@
 // memory, kernel launches, correlation/conservation reductions, state I/O.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "../../include/flb.h"
 #include "flb_host.h"
@@ -108,16 +110,27 @@ __global__ void finalize_kernel(const double* acc, long long nsamp, const double
 }
 
 // Total mass and momentum of the pre-collision state, FP64 per block.
+__device__ __forceinline__ double pop_value(const double* src, long long k, int, const DevCodec&) {
+    return src[k];
+}
+__device__ __forceinline__ double pop_value(const float* src, long long k, int, const DevCodec&) {
+    return (double)src[k];
+}
+__device__ __forceinline__ double pop_value(const __half* src, long long k, int i,
+                                            const DevCodec& c) {
+    return dev_decode(c, i, src[k]);
+}
+
 template <class T>
 __global__ void __launch_bounds__(kStepThreads)
-conservation_kernel(const T* src, Geometry geo, double* partials) {
+conservation_kernel(const T* src, Geometry geo, double* partials, DevCodec codec) {
     const long long N = (long long)geo.Lx * geo.Ly;
     double r = 0.0, jx = 0.0, jy = 0.0;
     // the interior of the buffer is a permutation of the pre-collision state
     for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < (int)N; n += gridDim.x * blockDim.x) {
         const int y = n / geo.Lx, x = n - y * geo.Lx;
         for (int i = 0; i < 9; ++i) {
-            const double v = (double)src[at(geo, i, x, y)];
+            const double v = pop_value(src, at(geo, i, x, y), i, codec);
             r += v;
             jx += v * cvx(i);
             jy += v * cvy(i);
@@ -149,6 +162,61 @@ __global__ void sum3_kernel(const double* partials, int nblocks, double* out) {
     double t = 0.0;
     for (int b = 0; b < nblocks; ++b) t += partials[b * 3 + k];
     out[k] = t;
+}
+
+// Max |f_a - f_b|, sum of (f_a - f_b)^2 and max |f_b| over the pre-collision
+// states of two lattices of the same size (any storage precisions), per block.
+struct StateView {
+    const void* buf;
+    int prec;   // FLB_FP64, FLB_FP32 or FLB_FP16_DEV
+    Geometry geo;
+    DevCodec codec;
+    __device__ __forceinline__ double get(int i, int x, int y) const {
+        const long long k = at(geo, i, wrap(x - cvx(i), geo.Lx), wrap(y - cvy(i), geo.Ly));
+        if (prec == FLB_FP64) return ((const double*)buf)[k];
+        if (prec == FLB_FP32) return (double)((const float*)buf)[k];
+        return dev_decode(codec, i, ((const __half*)buf)[k]);
+    }
+};
+
+__global__ void __launch_bounds__(kStepThreads)
+state_difference_kernel(StateView a, StateView b, double* partials) {
+    const int Lx = a.geo.Lx;
+    const long long N = (long long)Lx * a.geo.Ly;
+    double mx = 0.0, ss = 0.0, mb = 0.0;
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < (int)N; n += gridDim.x * blockDim.x) {
+        const int y = n / Lx, x = n - y * Lx;
+        for (int i = 0; i < 9; ++i) {
+            const double fa = a.get(i, x, y), fb = b.get(i, x, y);
+            const double d = fa - fb;
+            mx = fmax(mx, fabs(d));
+            ss += d * d;
+            mb = fmax(mb, fabs(fb));
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        mb = fmax(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+    }
+    __shared__ double red[3][kStepThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[0][warp] = mx;
+        red[1][warp] = ss;
+        red[2][warp] = mb;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kStepThreads / 32; ++w) {
+            red[0][0] = fmax(red[0][0], red[0][w]);
+            red[1][0] += red[1][w];
+            red[2][0] = fmax(red[2][0], red[2][w]);
+        }
+        partials[blockIdx.x * 3 + 0] = red[0][0];
+        partials[blockIdx.x * 3 + 1] = red[1][0];
+        partials[blockIdx.x * 3 + 2] = red[2][0];
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -221,7 +289,7 @@ namespace {
 constexpr size_t kAlign = 256;
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
-int elem_size(int prec) { return prec == FLB_FP64 ? 8 : 4; }
+int elem_size(int prec) { return prec == FLB_FP64 ? 8 : (prec == FLB_FP16_DEV ? 2 : 4); }
 
 Geometry make_geometry(const flb_params* p) { return flb::make_geometry(p->Lx, p->Ly); }
 
@@ -306,8 +374,38 @@ bool uses_tma(flb_lattice h) {
     return h->p.precision == FLB_FP32 && h->variant != FLB_KERNEL_GENERIC;
 }
 
+// The pipelined kernels (FP32, FP16 store) add their sums to h->acc themselves.
+bool reduces_in_kernel(flb_lattice h) { return uses_tma(h) || h->p.precision == FLB_FP16_DEV; }
+
+DevCodec dev_codec(flb_lattice h) {
+    DevCodec c;
+    for (int i = 0; i < 9; ++i) c.ref[i] = (float)h->ref[i];
+    c.scale = (float)std::sqrt(h->p.kT);
+    return c;
+}
+
+// FP16 deviation store: h = (f - ref) / sqrt(kT), collision in FP32.
+cudaError_t launch_step_fp16(flb_lattice h, bool sample) {
+    HArgs a;
+    a.dst = (__half*)h->buf[h->cur ^ 1];
+    a.geo = h->geo;
+    a.step = (uint32_t)h->t;
+    a.tiles_x = a.ntiles = 0;
+    a.acc = h->acc;
+    a.err = h->err;
+    const DevCodec c = dev_codec(h);
+    a.scale = c.scale;
+    a.inv_scale = 1.0f / c.scale;
+    for (int i = 0; i < 9; ++i) {
+        a.ref[i] = c.ref[i];
+        a.nref[i] = -c.ref[i] * a.inv_scale;
+    }
+    return fp16_step(h->tma, h->cur, a, collide_const<float>(&h->p), h->p.basis, sample, h->stream);
+}
+
 cudaError_t launch_step(flb_lattice h, bool sample) {
     if (h->p.precision == FLB_FP64) return launch_step_p<double>(h, sample);
+    if (h->p.precision == FLB_FP16_DEV) return launch_step_fp16(h, sample);
     if (uses_tma(h)) return launch_step_tma(h, sample);
     return launch_step_p<float>(h, sample);
 }
@@ -375,15 +473,19 @@ int lattice_create(const flb_params* p, void* dev_workspace, size_t workspace_by
         if (p->precision == FLB_FP64)
             fill_kernel<double><<<grid_for(9 * h->geo.plane), 256, 0, h->stream>>>(
                 (double*)h->buf[0], h->geo, v);
-        else
+        else if (p->precision == FLB_FP32)
             fill_kernel<float><<<grid_for(9 * h->geo.plane), 256, 0, h->stream>>>(
                 (float*)h->buf[0], h->geo, v);
+        else   // FP16 deviation store: f = ref everywhere is h = 0
+            cudaMemsetAsync(h->buf[0], 0, L.buf_bytes, h->stream);
         ce = cudaGetLastError();
     }
     if (ce == cudaSuccess && sync) ce = cudaStreamSynchronize(h->stream);
     h->tma.sample_mode = 0;   // library default
     if (ce == cudaSuccess && p->precision == FLB_FP32)
         ce = tma_plan(&h->tma, h->buf[0], h->buf[1], h->geo, 0);
+    if (ce == cudaSuccess && p->precision == FLB_FP16_DEV)
+        ce = fp16_plan(&h->tma, h->buf[0], h->buf[1], h->geo);
     if (ce != cudaSuccess) {
         cudaGetLastError();
         if (h->own_ws) cudaFree(h->ws);
@@ -473,7 +575,7 @@ int flb_step(flb_lattice h, int64_t n) {
         const bool sample =
             h->every > 0 && h->t >= h->warmup && ((h->t - h->warmup) % h->every) == 0;
         cudaError_t ce = launch_step(h, sample);
-        if (ce == cudaSuccess && sample && !uses_tma(h)) {
+        if (ce == cudaSuccess && sample && !reduces_in_kernel(h)) {
             accumulate_partials_kernel<<<kSums, 32, 0, h->stream>>>(h->partials, h->nblocks,
                                                                      h->acc);
             ce = cudaGetLastError();
@@ -492,6 +594,7 @@ int flb_set_option(flb_lattice h, int32_t option, int32_t value) {
         if (value != FLB_KERNEL_AUTO && value != FLB_KERNEL_GENERIC && value != FLB_KERNEL_PIPELINED)
             return FLB_ERR_ARG;
         if (value == FLB_KERNEL_PIPELINED && h->p.precision != FLB_FP32) return FLB_ERR_ARG;
+        if (value == FLB_KERNEL_GENERIC && h->p.precision == FLB_FP16_DEV) return FLB_ERR_ARG;
         h->variant = value;
         return FLB_OK;
     }
@@ -595,10 +698,13 @@ int flb_conservation(flb_lattice h, double sums[3]) {
     double* res = h->small + 81 + 171;
     if (h->p.precision == FLB_FP64)
         conservation_kernel<double><<<h->nblocks, kStepThreads, 0, h->stream>>>(
-            (const double*)h->buf[h->cur], h->geo, part);
-    else
+            (const double*)h->buf[h->cur], h->geo, part, DevCodec());
+    else if (h->p.precision == FLB_FP32)
         conservation_kernel<float><<<h->nblocks, kStepThreads, 0, h->stream>>>(
-            (const float*)h->buf[h->cur], h->geo, part);
+            (const float*)h->buf[h->cur], h->geo, part, DevCodec());
+    else
+        conservation_kernel<__half><<<h->nblocks, kStepThreads, 0, h->stream>>>(
+            (const __half*)h->buf[h->cur], h->geo, part, dev_codec(h));
     sum3_kernel<<<1, 32, 0, h->stream>>>(part, h->nblocks, res);
     cudaError_t ce = cudaGetLastError();
     if (ce == cudaSuccess)
@@ -606,6 +712,44 @@ int flb_conservation(flb_lattice h, double sums[3]) {
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
     if (ce != cudaSuccess) return FLB_ERR_CUDA;
     return check_device_error(h);
+}
+
+int flb_state_difference(flb_lattice a, flb_lattice b, double out[3]) {
+    if (!a || !b || !out || a->p.Lx != b->p.Lx || a->p.Ly != b->p.Ly) return FLB_ERR_ARG;
+    StateView va{a->buf[a->cur], a->p.precision, a->geo, dev_codec(a)};
+    StateView vb{b->buf[b->cur], b->p.precision, b->geo, dev_codec(b)};
+    const int grid = grid_for((long long)a->p.Lx * a->p.Ly);
+    double* part = nullptr;
+    if (cudaMalloc(&part, sizeof(double) * 3 * grid) != cudaSuccess) {
+        cudaGetLastError();
+        return FLB_ERR_OOM;
+    }
+    // both lattices' pending steps first
+    cudaError_t ce = cudaStreamSynchronize(b->stream);
+    if (ce == cudaSuccess) {
+        state_difference_kernel<<<grid, kStepThreads, 0, a->stream>>>(va, vb, part);
+        ce = cudaGetLastError();
+    }
+    std::vector<double> host(3 * (size_t)grid);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(host.data(), part, sizeof(double) * host.size(),
+                             cudaMemcpyDeviceToHost, a->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(a->stream);
+    cudaFree(part);
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        return FLB_ERR_CUDA;
+    }
+    double mx = 0.0, ss = 0.0, mb = 0.0;
+    for (int k = 0; k < grid; ++k) {
+        mx = std::max(mx, host[3 * k]);
+        ss += host[3 * k + 1];
+        mb = std::max(mb, host[3 * k + 2]);
+    }
+    out[0] = mx;
+    out[1] = std::sqrt(ss / (9.0 * (double)a->p.Lx * (double)a->p.Ly));
+    out[2] = mb;
+    return FLB_OK;
 }
 
 int flb_get_populations(flb_lattice h, double* host_out) {
@@ -620,9 +764,12 @@ int flb_get_populations(flb_lattice h, double* host_out) {
     if (h->p.precision == FLB_FP64)
         gather_state_kernel<double><<<grid, 256, 0, h->stream>>>((const double*)h->buf[h->cur],
                                                                  h->geo, tmp);
-    else
+    else if (h->p.precision == FLB_FP32)
         gather_state_kernel<float><<<grid, 256, 0, h->stream>>>((const float*)h->buf[h->cur],
                                                                 h->geo, tmp);
+    else
+        gather_dev_kernel<<<grid, 256, 0, h->stream>>>((const __half*)h->buf[h->cur], h->geo,
+                                                       dev_codec(h), tmp);
     cudaError_t ce = cudaGetLastError();
     if (ce == cudaSuccess)
         ce = cudaMemcpyAsync(host_out, tmp, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
@@ -647,9 +794,12 @@ int flb_set_populations(flb_lattice h, const double* host_in) {
         if (h->p.precision == FLB_FP64)
             scatter_state_kernel<double><<<grid, 256, 0, h->stream>>>(tmp, h->geo,
                                                                       (double*)h->buf[h->cur]);
-        else
+        else if (h->p.precision == FLB_FP32)
             scatter_state_kernel<float><<<grid, 256, 0, h->stream>>>(tmp, h->geo,
                                                                      (float*)h->buf[h->cur]);
+        else
+            scatter_dev_kernel<<<grid, 256, 0, h->stream>>>(tmp, h->geo, dev_codec(h),
+                                                            (__half*)h->buf[h->cur]);
         ce = cudaGetLastError();
     }
     if (ce == cudaSuccess) ce = cudaMemsetAsync(h->err, 0, sizeof(DevError), h->stream);

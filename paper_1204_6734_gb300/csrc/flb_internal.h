@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "flb_kernels.cuh"
@@ -34,9 +35,30 @@ struct TmaPlan {
 // cudaSuccess or the error that prevents the pipelined kernel.
 cudaError_t tma_plan(TmaPlan* plan, void* buf0, void* buf1, const Geometry& g, int nw);
 
-// Tensor map of the nine planes of one FP32 buffer (ghost-frame layout), seen
-// as one 2D array of pitch x 9 (Ly + 2) elements, for boxes of box_w x th.
-cudaError_t tma_encode_planes(CUtensorMap* map, void* buf, const Geometry& g, int box_w, int th);
+// Tensor map of the nine planes of one buffer (ghost-frame layout), seen as
+// one 2D array of pitch x 9 (Ly + 2) elements of elem_bytes (4: FP32, 2: FP16),
+// for boxes of box_w x th.
+cudaError_t tma_encode_planes(CUtensorMap* map, void* buf, const Geometry& g, int box_w, int th,
+                              int elem_bytes = 4);
+
+// Arguments of the FP16-deviation-store step (flb_step_fp16.cu): the buffer
+// holds h = (f - ref) / scale in FP16, scale = sqrt(kT).
+struct HArgs {
+    __half* dst;            // buffer receiving h*(t)
+    Geometry geo;
+    uint32_t step;
+    int tiles_x, ntiles;
+    double* acc;            // running FP64 sums of f - ref (sampling)
+    DevError* err;
+    float ref[9];           // f^0(rho0, u0)
+    float nref[9];          // -ref / scale
+    float scale, inv_scale;
+};
+
+// Tensor maps and launch shape of the FP16-store kernel; one step of it.
+cudaError_t fp16_plan(TmaPlan* plan, void* buf0, void* buf1, const Geometry& g);
+cudaError_t fp16_step(const TmaPlan& plan, int src, const HArgs& a, const CollideConst<float>& cc,
+                      int basis, bool sample, cudaStream_t s);
 
 // One fused step from buffer `src` into a.dst. basis: 0 Hermite, 1 f-norm.
 cudaError_t tma_step(const TmaPlan& plan, int src, const TmaArgs& a,

@@ -3,6 +3,7 @@
 // which holds f*_i(z) = f_i(z + v_i) for the next pull; and a uniform fill.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "flb_kernels.cuh"
@@ -42,6 +43,39 @@ __global__ void fill_kernel(T* buf, Geometry geo, Vec9 v) {
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < total;
          k += (long long)gridDim.x * blockDim.x)
         buf[k] = (T)v.v[k / geo.plane];
+}
+
+// FP16 deviation store: a buffer holds h_i = (f_i - ref_i) / scale.
+struct DevCodec {
+    float ref[9];
+    float scale;
+};
+
+__device__ __forceinline__ double dev_decode(const DevCodec& c, int i, __half h) {
+    return (double)c.ref[i] + (double)c.scale * (double)__half2float(h);
+}
+
+static __global__ void scatter_dev_kernel(const double* in, Geometry geo, DevCodec c, __half* buf) {
+    const long long N = (long long)geo.Lx * geo.Ly;
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < (int)N; n += gridDim.x * blockDim.x) {
+        const int y = n / geo.Lx, x = n - y * geo.Lx;
+        for (int i = 0; i < 9; ++i) {
+            const int zx = wrap(x - cvx(i), geo.Lx), zy = wrap(y - cvy(i), geo.Ly);
+            const double h = (in[i * N + n] - (double)c.ref[i]) / (double)c.scale;
+            store_pop(buf, geo, i, zx, zy, __double2half(h));
+        }
+    }
+}
+
+static __global__ void gather_dev_kernel(const __half* buf, Geometry geo, DevCodec c, double* out) {
+    const long long N = (long long)geo.Lx * geo.Ly;
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < (int)N; n += gridDim.x * blockDim.x) {
+        const int y = n / geo.Lx, x = n - y * geo.Lx;
+        for (int i = 0; i < 9; ++i) {
+            const int xs = wrap(x - cvx(i), geo.Lx), ys = wrap(y - cvy(i), geo.Ly);
+            out[i * N + n] = dev_decode(c, i, buf[at(geo, i, xs, ys)]);
+        }
+    }
 }
 
 }  // namespace flb

@@ -394,14 +394,18 @@ size_t smem_for(int nw) {
 
 }  // namespace
 
-cudaError_t tma_encode_planes(CUtensorMap* map, void* buf, const Geometry& g, int box_w, int th) {
+cudaError_t tma_encode_planes(CUtensorMap* map, void* buf, const Geometry& g, int box_w, int th,
+                              int elem_bytes) {
     EncodeFn enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
     const cuuint64_t dims[2] = {(cuuint64_t)g.pitch, (cuuint64_t)(9 * (long long)(g.Ly + 2))};
-    const cuuint64_t strides[1] = {(cuuint64_t)g.pitch * sizeof(float)};
+    if (elem_bytes != 4 && elem_bytes != 2) return cudaErrorInvalidValue;
+    const cuuint64_t strides[1] = {(cuuint64_t)g.pitch * (cuuint64_t)elem_bytes};
     const cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)th};
     const cuuint32_t estr[2] = {1, 1};
-    const CUresult rc = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, buf, dims, strides, box, estr,
+    const CUtensorMapDataType dt =
+        elem_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    const CUresult rc = enc(map, dt, 2, buf, dims, strides, box, estr,
                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return rc == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;

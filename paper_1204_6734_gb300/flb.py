@@ -100,6 +100,7 @@ def load(build_if_missing: bool = True):
         "flb_raw_sums": (C.c_int, [h, _dp, _dp, _i64p]),
         "flb_conservation": (C.c_int, [h, _dp]),
         "flb_get_populations": (C.c_int, [h, _dp]),
+        "flb_state_difference": (C.c_int, [h, h, _dp]),
         "flb_set_populations": (C.c_int, [h, _dp]),
         "flb_run_host": (C.c_int, [P, _dp, C.c_int64, C.c_int64, C.c_int64, _dp, _dp, _dp, _i64p]),
         "flb_noise_draws": (C.c_int, [C.c_uint64, C.c_uint32, C.c_uint32, _u32p, C.c_int32,
@@ -155,7 +156,7 @@ def exported_symbols():
             "flb_reset_error", "flb_correlations", "flb_raw_sums", "flb_conservation",
             "flb_get_populations", "flb_set_populations", "flb_run_host", "flb_noise_draws",
             "flb_collide_nodes", "flb_set_option", "flb_step_noalloc", "flb_error_string",
-            "flb_version", "flb_batch_open", "flb_batch_replica_bytes", "flb_batch_add",
+            "flb_version", "flb_state_difference", "flb_batch_open", "flb_batch_replica_bytes", "flb_batch_add",
             "flb_batch_remove", "flb_batch_create", "flb_batch_workspace_bytes",
             "flb_batch_destroy", "flb_batch_set_sampling", "flb_batch_step",
             "flb_batch_set_graph", "flb_batch_set_tile", "flb_batch_get_tile",
@@ -289,6 +290,13 @@ def flb_conservation(h):
     out = np.zeros(3)
     _check(load().flb_conservation(h, _ptr(out)), "flb_conservation")
     return out
+
+
+def flb_state_difference(a, b):
+    """(max |f_a - f_b|, RMS of f_a - f_b, max |f_b|) of two lattices' states."""
+    out = np.zeros(3)
+    _check(load().flb_state_difference(a, b, _ptr(out)), "flb_state_difference")
+    return tuple(out)
 
 
 def flb_get_populations(h, Lx: int, Ly: int, out=None):
