@@ -107,31 +107,48 @@ __device__ __forceinline__ bool sampled_at(const ReplicaHot& h, int t) {
 // Fill stage s with global tile t (one thread). The tile record {x0, y0, t_r,
 // live} is written with a plain shared store before the arrival on the full
 // barrier, whose release makes it visible to the waiting warps.
+struct TileFetch {
+    const ReplicaDesc* d;
+    int x0, y0, tr, Ly;
+    bool live;
+};
+
+// The global reads behind one tile (its code, then its replica's time and
+// geometry): done one tile ahead of the issue, so their latency overlaps the
+// producer's wait for the stage.
 template <int TW, int NPT>
-__device__ __forceinline__ void batch_issue(float* smem, const BatchArgs& a, unsigned step, int t,
-                                            int s, uint64_t* full) {
+__device__ __forceinline__ TileFetch batch_fetch(const BatchArgs& a, unsigned step, int t) {
     using BS = BatchShape<TW, NPT>;
+    TileFetch f;
     const uint32_t code = __ldg(&a.tiles[t]);
-    const ReplicaDesc* d = a.desc + (code >> kLocalBits);
+    f.d = a.desc + (code >> kLocalBits);
     const int local = (int)(code & kLocalMask);
-    const int tr = __ldg(&d->hot.t0) + (int)(step - (unsigned)__ldg(&d->hot.join));
-    const int tiles_x = __ldg(&d->hot.tiles_x), Ly = __ldg(&d->hot.Ly);
-    const bool live = tr < __ldg(&d->hot.tend);
+    f.tr = __ldg(&f.d->hot.t0) + (int)(step - (unsigned)__ldg(&f.d->hot.join));
+    const int tiles_x = __ldg(&f.d->hot.tiles_x);
+    f.Ly = __ldg(&f.d->hot.Ly);
+    f.live = f.tr < __ldg(&f.d->hot.tend);
     const int ty = local / tiles_x;
-    const int x0 = (local - ty * tiles_x) * TW, y0 = ty * BS::TH;
+    f.x0 = (local - ty * tiles_x) * TW;
+    f.y0 = ty * BS::TH;
+    return f;
+}
+
+template <int TW, int NPT>
+__device__ __forceinline__ void batch_issue(float* smem, const TileFetch& f, int s, uint64_t* full) {
+    using BS = BatchShape<TW, NPT>;
     float* st = smem + s * BS::STAGE;
-    *reinterpret_cast<int4*>(st + 9 * BS::SPLANE + BS::HOT) = make_int4(x0, y0, tr, live ? 1 : 0);
-    if (!live) {
+    *reinterpret_cast<int4*>(st + 9 * BS::SPLANE + BS::HOT) = make_int4(f.x0, f.y0, f.tr, f.live ? 1 : 0);
+    if (!f.live) {
         mbar_arrive(&full[s]);
         return;
     }
     mbar_arrive_expect_tx(&full[s], 9u * BS::TH * BS::BW * sizeof(float) + sizeof(ReplicaHot));
-    const CUtensorMap* map = &d->map[tr & 1];
+    const CUtensorMap* map = &f.d->map[f.tr & 1];
 #pragma unroll
     for (int i = 0; i < 9; ++i)
-        tma_load_2d(st + i * BS::SPLANE, map, x0 + kXO - 4, i * (Ly + 2) + y0 + 1 - cvy(i),
+        tma_load_2d(st + i * BS::SPLANE, map, f.x0 + kXO - 4, i * (f.Ly + 2) + f.y0 + 1 - cvy(i),
                     &full[s]);
-    bulk_load(st + 9 * BS::SPLANE, &d->hot, sizeof(ReplicaHot), &full[s]);
+    bulk_load(st + 9 * BS::SPLANE, &f.d->hot, sizeof(ReplicaHot), &full[s]);
 }
 
 // Warp roles: NW consumer warps, then one producer warp (SAMPLE = false) or
@@ -170,9 +187,12 @@ batch_step_kernel(const BatchArgs a) {
         const bool producer = warp == NW && lane_id == 0;
         int issued = 0, k = 0;
         bool ok = true;
-        if (producer)
+        TileFetch nxt{};
+        if (producer) {
             for (; issued < S && issued < ntile; ++issued)
-                batch_issue<TW, NPT>(smem, a, step, tbeg + issued, issued, full);
+                batch_issue<TW, NPT>(smem, batch_fetch<TW, NPT>(a, step, tbeg + issued), issued, full);
+            if (issued < ntile) nxt = batch_fetch<TW, NPT>(a, step, tbeg + issued);
+        }
         if (!SAMPLE) {
             if (producer) {
                 for (; k < ntile && issued < ntile; ++k) {
@@ -181,8 +201,8 @@ batch_step_kernel(const BatchArgs a) {
                         ok = false;
                         break;
                     }
-                    batch_issue<TW, NPT>(smem, a, step, tbeg + issued, s, full);
-                    ++issued;
+                    batch_issue<TW, NPT>(smem, nxt, s, full);
+                    if (++issued < ntile) nxt = batch_fetch<TW, NPT>(a, step, tbeg + issued);
                 }
                 if (!ok) {
                     record_error(first_err(), kStatusTimeout, -1, step);
@@ -276,8 +296,8 @@ batch_step_kernel(const BatchArgs a) {
                     ok = false;
                     break;
                 }
-                batch_issue<TW, NPT>(smem, a, step, tbeg + issued, s, full);
-                ++issued;
+                batch_issue<TW, NPT>(smem, nxt, s, full);
+                if (++issued < ntile) nxt = batch_fetch<TW, NPT>(a, step, tbeg + issued);
             }
         }
         flush();
@@ -336,13 +356,21 @@ batch_step_kernel(const BatchArgs a) {
                 hs.cc, f);
             __syncwarp();
             if (lane_id == 0) mbar_arrive(&empty[s]);
-            if (inA) {
-                if (stt & 0xFF) record_error(err, (int)(stt & 0xFF), nodeA, tr);
-                store_lane(dst, geo, xA, y, f, 0);
+            if (stt) {
+                if (inA && (stt & 0xFF)) record_error(err, (int)(stt & 0xFF), nodeA, tr);
+                if (inB && (stt >> 8)) record_error(err, (int)(stt >> 8), nodeA + TW / 2, tr);
             }
-            if (inB) {
-                if (stt >> 8) record_error(err, (int)(stt >> 8), nodeA + TW / 2, tr);
-                store_lane(dst, geo, xB, y, f, 1);
+            // tiles away from the lattice edge store without per-node checks
+            if (info.x > 0 && info.y > 0 && info.x + TW < geo.Lx && info.y + TH < geo.Ly) {
+                float* pa = dst + at(geo, 0, xA, y);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    pa[i * geo.plane] = f[i].v.x;
+                    pa[i * geo.plane + TW / 2] = f[i].v.y;
+                }
+            } else {
+                if (inA) store_lane(dst, geo, xA, y, f, 0);
+                if (inB) store_lane(dst, geo, xB, y, f, 1);
             }
         } else {
             auto load = [&](float* g) {
