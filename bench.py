@@ -29,10 +29,10 @@ METRIC = "MLUPS & % of HBM roofline (FP32 vs FP64); batched replica-steps/s, p50
 UNIT = "MLUPS"
 BYTES_PER_NODE = {"fp32": 72, "fp64": 144}
 # DRAM bytes (read + write) per launch of the FP32 step kernel at 4096^2,
-# f-norm basis, sampling on: ncu dram__bytes_read.sum + dram__bytes_write.sum
-# of one 2048^2 launch (156.0 + 101.6 MB) scaled by the node count (x4).
-# Valid only for the kernel version it was taken on; None elsewhere.
-DRAM_TRAFFIC = {("fp32", "local", 4096): 4 * (156.027136e6 + 101.609984e6)}
+# f-norm basis, sampling every step: ncu dram__bytes_read.sum +
+# dram__bytes_write.sum of the full-size launch (614.3 + 559.4 MB, averaged
+# over 23 launches). Valid only for the kernel version it was taken on.
+DRAM_TRAFFIC = {("fp32", "local", 4096): 614.3e6 + 559.4e6}
 
 
 def parse():
@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched-ensemble comparison added to the JSON line")
     ap.add_argument("--batched-steps", type=int, default=200)
-    ap.add_argument("--workload", default="single", choices=["single", "ensemble", "serving"],
+    ap.add_argument("--workload", default="single", choices=["single", "ensemble", "serving", "precision"],
                     help="single: the 4096^2 lattice (with the ensemble comparison added); "
                          "ensemble: only the batched replica ensemble, as the main line")
     ap.add_argument("--replicas", type=int, default=256, help="replicas of the ensemble")
@@ -301,10 +301,10 @@ def serve_trace(args, stream, mode, reqs):
             "failed": sum(1 for r in results if r["status"] != 0)}
 
 
-def bench_serving(args, stream, modes=("batched", "per_lattice")):
+def bench_serving(args, stream, modes=("batched", "per_lattice"), rate_hz=200.0):
     from paper_1204_6734_gb300 import inputs
-    reqs = inputs.serving_requests()[:args.serve_requests]
-    out = {"workload": f"first {len(reqs)} requests of the serving trace: Poisson arrivals at 200/s, "
+    reqs = inputs.serving_requests(n=args.serve_requests, rate_hz=rate_hz)
+    out = {"workload": f"first {len(reqs)} requests of the serving trace: Poisson arrivals at {rate_hz:.3g}/s, "
                        "sides log-uniform in [32, 2048], u_x0 ~ U[0, 0.3], kT log-uniform in "
                        "[1e-5, 1e-3], shear rate ~ U[0.6, 1.8], steps in [500, 20000], FP32, "
                        "local basis, sampled every step after a tenth of the steps",
@@ -345,6 +345,11 @@ def run_serving(args, rank, world, dist, dev):
     modes = ("batched",) if args.no_per_lattice else ("batched", "per_lattice")
     with ClockSampler(smi_id(dev)) as clk:
         sv = bench_serving(args, stream, modes)
+        # the same requests arriving at 70 % of the batched server's measured
+        # node-update capacity (the overload run above)
+        work = sv["node_steps"] / args.serve_requests
+        rate70 = 0.7 * sv["batched"]["mlups"] * 1e6 / work
+        sv["at_70pct_capacity"] = bench_serving(args, stream, modes, rate_hz=rate70)
     if rank == 0:
         b = sv["batched"]
         out = {"metric": METRIC, "value": b["replica_steps_per_s"], "unit": "replica-steps/s",
@@ -354,6 +359,65 @@ def run_serving(args, rank, world, dist, dev):
                "latency_p50_s": b["latency_p50_s"], "latency_p99_s": b["latency_p99_s"],
                "serving": sv, "clocks": clk.summary()}
         print(json.dumps(out))
+
+
+def run_precision(args, rank, world, dist, dev):
+    """--workload precision: the same lattice (8192^2 by default, u_x0 = 0.2,
+    kT = 1e-4, all rates 1, f-norm, seed 4) run --steps steps in FP64, FP32 and
+    the FP16 deviation store with the same draws, sampled every step after a
+    tenth of the steps; errors of the FP32 and FP16 states and of <df_i df_j>
+    against the FP64 run, and the throughput of each."""
+    import numpy as np
+    import torch
+
+    from paper_1204_6734_gb300 import flb, inputs
+    stream = torch.cuda.Stream(device=dev)
+    side = args.side if args.side != 4096 else 8192
+    warm = args.steps // 10
+    lats, res = {}, {}
+    with ClockSampler(smi_id(dev)) as clk:
+        for prec in ("fp64", "fp32", "fp16dev"):
+            p = inputs.precision_lattice(prec, side=side)
+            lat = flb.Lattice(p, stream=stream)
+            lat.set_sampling(warm, 1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            lat.step(args.steps)
+            e1.record(stream)
+            lat.sync()
+            ms = e0.elapsed_time(e1) / args.steps
+            Cff, CMM, mean, n = lat.correlations("local")
+            lats[prec] = lat
+            res[prec] = {"ms_per_step": ms, "mlups": p.Lx * p.Ly / ms / 1e3,
+                         "bytes_per_node": {"fp64": 144, "fp32": 72, "fp16dev": 36}[prec],
+                         "Cff": Cff, "CMM": CMM, "n_samples": n}
+    kT, wmax = 1e-4, 4.0 / 9.0
+    out = {}
+    for prec in ("fp64", "fp32", "fp16dev"):
+        r = res[prec]
+        o = {"mlups": r["mlups"], "ms_per_step": r["ms_per_step"], "bytes_per_node": r["bytes_per_node"]}
+        if prec != "fp64":
+            mx, rms, fmax = flb.flb_state_difference(lats[prec].h, lats["fp64"].h)
+            o["population_error_max"] = mx
+            o["population_error_rms"] = rms
+            o["corr_error_max_over_kT_wmax"] = float(np.abs(r["Cff"] - res["fp64"]["Cff"]).max() / (kT * wmax))
+            o["moment_corr_error_max_over_kT"] = float(np.abs(r["CMM"] - res["fp64"]["CMM"]).max() / kT)
+        out[prec] = o
+    for lat in lats.values():
+        lat.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": out["fp32"]["mlups"], "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": 0, "ms_per_step": out["fp32"]["ms_per_step"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": f"precision study: {side}x{side} periodic, u_x0=0.2, kT=1e-4, "
+                                       "all rates 1, f-norm basis, seed 4, FP64 / FP32 / FP16 "
+                                       f"deviation store, sampled every step after {warm}",
+                           "l2": "inputs larger than L2"},
+                "precision": out, "clocks": clk.summary(),
+                "n_samples": int(res["fp32"]["n_samples"])}
+        print(json.dumps(line))
 
 
 def run_reference(args):
@@ -410,6 +474,8 @@ def main():
         return run_ensemble(args, rank, world, dist, dev)
     if args.workload == "serving":
         return run_serving(args, rank, world, dist, dev)
+    if args.workload == "precision":
+        return run_precision(args, rank, world, dist, dev)
 
     p = inputs.single_lattice(args.ux0, args.basis, side=args.side, precision=args.precision)
     p.replica = rank                      # independent replica per rank
@@ -465,7 +531,7 @@ def main():
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                 "kernel": kname, "algorithmic_bytes": algo_bytes,
-                "traffic_source": "ncu capture at 2048^2 scaled x4" if traffic else None}
+                "traffic_source": "ncu dram bytes of the full-size launch" if traffic else None}
 
     Cff, CMM, mean, ns = lat.correlations(args.basis)
     lat.close()
