@@ -457,7 +457,7 @@ def main():
     import numpy as np
     import torch
 
-    from paper_1204_6734_gb300 import flb, inputs
+    from paper_1204_6734_gb300 import flb, inputs, replicas
 
     rank, world, local = dist_env()
     if world > 1:
@@ -470,16 +470,22 @@ def main():
     dev = torch.cuda.current_device()
     flb.load()
 
-    if args.workload == "ensemble":
-        return run_ensemble(args, rank, world, dist, dev)
-    if args.workload == "serving":
-        return run_serving(args, rank, world, dist, dev)
-    if args.workload == "precision":
-        return run_precision(args, rank, world, dist, dev)
+    if args.workload != "single" and rank != 0:
+        # the ensemble, serving and precision workloads run on one GPU (rank 0)
+        dist.barrier()
+        dist.destroy_process_group()
+        return
+    if args.workload != "single":
+        if dist is not None:
+            dist.barrier()
+        run = {"ensemble": run_ensemble, "serving": run_serving, "precision": run_precision}
+        run[args.workload](args, rank, world, dist, dev)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
 
-    p = inputs.single_lattice(args.ux0, args.basis, side=args.side, precision=args.precision)
-    p.replica = rank                      # independent replica per rank
-    p.seed = p.seed + 7919 * rank
+    p = replicas.rank_params(
+        inputs.single_lattice(args.ux0, args.basis, side=args.side, precision=args.precision), rank)
     nodes = p.Lx * p.Ly
     stream = torch.cuda.Stream(device=dev)
     lat = flb.Lattice(p, stream=stream,
@@ -512,11 +518,8 @@ def main():
     lat.sync()
     total_ms = t_all0.elapsed_time(t_all1)
     per_step = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = nodes * world * args.steps / (total_ms * 1e-3) / 1e6
+    total_ms = replicas.max_over_ranks(total_ms, dist, device="cuda")
+    value = replicas.whole_job_rate(nodes * args.steps, world, total_ms * 1e-3) / 1e6
     step_ms = statistics.mean(per_step)
 
     peak, peak_kind = measured_peaks()
