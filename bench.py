@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched-ensemble comparison added to the JSON line")
     ap.add_argument("--batched-steps", type=int, default=200)
-    ap.add_argument("--workload", default="single", choices=["single", "ensemble", "serving", "precision"],
+    ap.add_argument("--workload", default="single", choices=["single", "ensemble", "serving", "precision", "sweep"],
                     help="single: the 4096^2 lattice (with the ensemble comparison added); "
                          "ensemble: only the batched replica ensemble, as the main line")
     ap.add_argument("--replicas", type=int, default=256, help="replicas of the ensemble")
@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--serve-slots", type=int, default=256)
     ap.add_argument("--serve-chunk", type=int, default=16)
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-other-basis", action="store_true",
+                    help="skip timing the same lattice in the other basis")
     ap.add_argument("--no-per-lattice", action="store_true",
                     help="skip the one-launch-per-lattice arm of the ensemble comparison")
     ap.add_argument("--graph-steps", type=int, default=25)
@@ -420,6 +422,75 @@ def run_precision(args, rank, world, dist, dev):
         print(json.dumps(line))
 
 
+MOMENT_NAMES = ("rho", "j_x", "j_y", "Pi_xx-yy", "Pi_xy", "Pi_xx+yy", "q_x", "q_y", "eps")
+# Quadratic coefficients q the paper prints for 21x21 lattices (Section 4,
+# after Figs. 19-21): Hermite norm measured in the Hermite norm, f-norm (its
+# look-up-table variant) measured in the f-norm at u0.
+PAPER_Q = {"standard": {"rho": 1.9, "Pi_xx-yy": 1.6, "j_y": 1.14},
+           "local": {"rho": 0.47, "Pi_xx-yy": 0.54, "j_y": 0.75}}
+
+
+def run_sweep(args, rank, world, dist, dev):
+    """--workload sweep: the u_x0 sweep of the 4096^2 lattice in both bases
+    (--steps steps each, sampled every step after a tenth); the normalised
+    moment variances <dM^a dM^a> / (kT rho0) - 1, measured in the run's own
+    basis at u0, fitted with l u_x0 + q u_x0^2 over |u_x0| <= 0.25 (the
+    paper's fit range) for every moment."""
+    import numpy as np
+    import torch
+
+    from paper_1204_6734_gb300 import flb, inputs
+    stream = torch.cuda.Stream(device=dev)
+    warm = max(1, args.steps // 10)
+    res = {}
+    with ClockSampler(smi_id(dev)) as clk:
+        for basis in ("standard", "local"):
+            rows = []
+            for u in inputs.SWEEP_UX0:
+                p = inputs.single_lattice(u, basis, side=args.side)
+                with flb.Lattice(p, stream=stream) as lat:
+                    lat.set_sampling(warm, 1)
+                    lat.step(args.steps)
+                    lat.sync()
+                    Cff, CMM, mean, n = lat.correlations(basis)
+                dev_ = np.diag(CMM) / (p.kT * p.rho0) - 1.0
+                rows.append((u, dev_, np.diag(Cff) / (p.kT * feq_of(p))))
+            us = np.array([r[0] for r in rows])
+            D = np.array([r[1] for r in rows])
+            fit = us <= 0.25
+            A = np.stack([us[fit], us[fit] ** 2], axis=1)
+            coef, *_ = np.linalg.lstsq(A, D[fit], rcond=None)
+            res[basis] = {
+                "u_x0": [float(u) for u in us],
+                "moment_variance_minus_1": {MOMENT_NAMES[a]: [float(x) for x in D[:, a]] for a in range(9)},
+                "population_variance_over_kT_f0": [[float(x) for x in r[2]] for r in rows],
+                "fit_l": {MOMENT_NAMES[a]: float(coef[0, a]) for a in range(9)},
+                "fit_q": {MOMENT_NAMES[a]: float(coef[1, a]) for a in range(9)},
+                "paper_q_21x21": PAPER_Q[basis],
+            }
+    if rank == 0:
+        line = {"metric": METRIC, "value": None, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": warm, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"u_x0 sweep {list(inputs.SWEEP_UX0)} of the {args.side}^2 "
+                                       "lattice (kT=1e-4, shear 1.0, bulk 0.8, ghost 1.0), both bases, "
+                                       f"sampled every step after {warm}",
+                           "l2": "inputs larger than L2"},
+                "sweep": res, "clocks": clk.summary()}
+        print(json.dumps(line))
+
+
+def feq_of(p):
+    """f_i^0(rho0, u0) of Eq. d2q9f0, to normalise the measured variances."""
+    import numpy as np
+    usq = p.ux0 ** 2 + p.uy0 ** 2
+    cx = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
+    cy = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    uv = p.ux0 * cx + p.uy0 * cy
+    return p.rho0 * w * (1 + 3 * uv + 4.5 * uv ** 2 - 1.5 * usq)
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -478,7 +549,8 @@ def main():
     if args.workload != "single":
         if dist is not None:
             dist.barrier()
-        run = {"ensemble": run_ensemble, "serving": run_serving, "precision": run_precision}
+        run = {"ensemble": run_ensemble, "serving": run_serving, "precision": run_precision,
+               "sweep": run_sweep}
         run[args.workload](args, rank, world, dist, dev)
         if dist is not None:
             dist.destroy_process_group()
@@ -559,6 +631,29 @@ def main():
                "d2h_bytes_per_step": (state_bytes + 8 * 90) / args.steps,
                "what": "flb_run_host: pinned host state in, steps with sampling, state + sums out"}
 
+    # the same lattice in the other basis (same size, precision and sampling)
+    other = None
+    if rank == 0 and world == 1 and not args.no_other_basis:
+        ob = "standard" if args.basis == "local" else "local"
+        q = replicas.rank_params(inputs.single_lattice(args.ux0, ob, side=args.side,
+                                                       precision=args.precision), rank)
+        with flb.Lattice(q, stream=stream) as lo:
+            lo.set_sampling(0, args.sample_every)
+            lo.step(args.warmup)
+            lo.sync()
+            n_other = min(args.steps, 500)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lo.step(n_other)
+            e1.record(stream)
+            lo.sync()
+            ms_o = e0.elapsed_time(e1) / n_other
+        mlups_o = q.Lx * q.Ly / ms_o / 1e3
+        ach = BYTES_PER_NODE[args.precision] * q.Lx * q.Ly / (ms_o * 1e-3) / 1e9
+        other = {"basis": ob, "mlups": mlups_o, "ms_per_step": ms_o, "steps": n_other,
+                 "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                              "frac": ach / peak, "peak_kind": peak_kind}}
+
     batched = serving = None
     if rank == 0 and world == 1 and not args.no_batched and args.precision == "fp32":
         batched = bench_batched(args, stream)
@@ -589,6 +684,7 @@ def main():
             "clocks": clk.summary(),
             "mlups_roofline_frac": value / (peak * 1e9 / BYTES_PER_NODE[args.precision] / 1e6) / world,
             "n_samples": ns,
+            "other_basis": other,
             "batched": batched,
             "serving": serving,
         }
