@@ -21,7 +21,7 @@ import numpy as np
 
 from . import build as _build
 
-BASIS = {"standard": 0, "local": 1}
+BASIS = {"standard": 0, "local": 1, "lut": 2}
 ERRORS = {0: "ok", -1: "invalid argument", -3: "invalid velocity (some f_i^0(1,u) <= 0)",
           -4: "non-finite value"}
 
@@ -54,6 +54,8 @@ def lib():
         L.orc_hermite_meq.argtypes = [C.c_double, C.c_double, C.c_double, dp]
         L.orc_local_basis.argtypes = [C.c_double, C.c_double, dp]
         L.orc_local_basis.restype = C.c_int
+        L.orc_lut_velocity.argtypes = [C.c_double, C.c_double, dp, dp]
+        L.orc_lut_velocity.restype = C.c_int
         L.orc_philox4x32_10.argtypes = [u32p, u32p, u32p]
         L.orc_draw_fields.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, u32p]
         L.orc_normals.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, dp]
@@ -128,6 +130,15 @@ def local_basis(ux, uy):
     if rc:
         raise OracleError(rc, f"at u=({ux},{uy})")
     return out
+
+
+def lut_velocity(ux, uy):
+    """Table velocity u_g of the look-up-table f-norm (Section 4) nearest to u."""
+    gx, gy = C.c_double(), C.c_double()
+    rc = lib().orc_lut_velocity(float(ux), float(uy), C.byref(gx), C.byref(gy))
+    if rc != 0:
+        raise OracleError(rc, "lut_velocity")
+    return gx.value, gy.value
 
 
 def philox(ctr, key):

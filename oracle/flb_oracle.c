@@ -307,6 +307,68 @@ static int collide_local(const orc_params* p, const double g[9], const double N[
     return ORC_OK;
 }
 
+/* Look-up-table f-norm (the practical variant of Section 4): the basis is not
+ * formed at the node's own velocity u but at the nearest velocity u_g of a
+ * 51 x 51 table, u_g = ((k_x - 25)/50, (k_y - 25)/50), k = 0..50 (spacing
+ * 0.02, |u_g| <= 0.5 per component), k = floor(50 u + 25.5). A velocity off the
+ * table, or a table velocity where some f_i^0(1, u_g) <= 0 (the corners, Fig.
+ * 11), has no basis: the paper's run fails there. */
+int orc_lut_velocity(double ux, double uy, double* ugx, double* ugy) {
+    const double kx = floor(50.0 * ux + 25.5), ky = floor(50.0 * uy + 25.5);
+    if (!(kx >= 0.0 && kx <= 50.0 && ky >= 0.0 && ky <= 50.0)) return ORC_ERR_INVALID_VELOCITY;
+    *ugx = (kx - 25.0) / 50.0;
+    *ugy = (ky - 25.0) / 50.0;
+    return ORC_OK;
+}
+
+/* The collision with the table basis mt(u_g): moments Mt^a = sum_i mt^a_i g_i;
+ * the equilibrium moments in that basis are no longer rho delta^{a0} (Eq.
+ * fnormmeq holds only at u_g = u) but the projection Mt^{a,eq} = sum_i mt^a_i
+ * f_i^0(rho, u) of the node's equilibrium (the paper keeps that projection to
+ * O(u_g^3); here it is taken exactly); relaxation towards it with
+ * Lambda = -omega_a and noise xi^a N^a for a = 3..8, and the back transform
+ * with n^a_i = mt^a_i f_i^0(1, u_g). The conserved moments pass through. */
+static int collide_lut(const orc_params* p, const double g[9], const double N[6],
+                       double fstar[9]) {
+    double rho = 0.0, jx = 0.0, jy = 0.0;
+    for (int i = 0; i < 9; ++i) {
+        rho += g[i];
+        jx += g[i] * VX[i];
+        jy += g[i] * VY[i];
+    }
+    if (!(rho > 0.0) || !isfinite(jx) || !isfinite(jy)) return ORC_ERR_NONFINITE;
+    const double ux = jx / rho, uy = jy / rho;
+    double ugx, ugy;
+    int rc = orc_lut_velocity(ux, uy, &ugx, &ugy);
+    if (rc != ORC_OK) return rc;
+    double mt[81];
+    rc = orc_local_basis(ugx, ugy, mt);
+    if (rc != ORC_OK) return rc;
+    double Wg[9], f0[9];
+    orc_feq(1.0, ugx, ugy, Wg);
+    orc_feq(rho, ux, uy, f0);
+
+    double Mt[9], Mteq[9];
+    for (int a = 0; a < 9; ++a) {
+        Mt[a] = 0.0;
+        Mteq[a] = 0.0;
+        for (int i = 0; i < 9; ++i) {
+            Mt[a] += mt[a * 9 + i] * g[i];
+            Mteq[a] += mt[a * 9 + i] * f0[i];
+        }
+    }
+    double dM[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int a = 3; a < 9; ++a)
+        dM[a] = -p->omega[a] * (Mt[a] - Mteq[a]) +
+                noise_amplitude(p->kT, rho, p->omega[a]) * N[a - 3];
+    for (int i = 0; i < 9; ++i) {
+        double df = 0.0;
+        for (int a = 0; a < 9; ++a) df += mt[a * 9 + i] * Wg[i] * dM[a];
+        fstar[i] = g[i] + df;
+    }
+    return ORC_OK;
+}
+
 int orc_collide_node(const orc_params* p, const double g[9], uint32_t node,
                      uint32_t step, double fstar[9]) {
     double N[6];
@@ -316,6 +378,8 @@ int orc_collide_node(const orc_params* p, const double g[9], uint32_t node,
         rc = collide_standard(p, g, N, fstar);
     else if (p->basis == ORC_BASIS_LOCAL)
         rc = collide_local(p, g, N, fstar);
+    else if (p->basis == ORC_BASIS_LOCAL_LUT)
+        rc = collide_lut(p, g, N, fstar);
     else
         return ORC_ERR_ARG;
     if (rc != ORC_OK) return rc;

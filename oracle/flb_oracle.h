@@ -31,7 +31,7 @@
 extern "C" {
 #endif
 
-enum { ORC_BASIS_STANDARD = 0, ORC_BASIS_LOCAL = 1 };
+enum { ORC_BASIS_STANDARD = 0, ORC_BASIS_LOCAL = 1, ORC_BASIS_LOCAL_LUT = 2 };
 
 enum {
     ORC_OK = 0,
@@ -44,7 +44,8 @@ typedef struct {
     int32_t Lx, Ly;
     double rho0, ux0, uy0, kT;
     double omega[9];   /* relaxation rate 1/tau^a per moment; 0..2 are ignored */
-    int32_t basis;     /* ORC_BASIS_STANDARD (Hermite norm) or ORC_BASIS_LOCAL (f-norm) */
+    int32_t basis;     /* ORC_BASIS_STANDARD (Hermite norm), ORC_BASIS_LOCAL (f-norm) or
+                          ORC_BASIS_LOCAL_LUT (f-norm from the velocity table) */
     uint32_t replica;  /* third Philox counter word */
     uint64_t seed;     /* Philox key */
 } orc_params;
@@ -63,6 +64,11 @@ void orc_hermite_meq(double rho, double ux, double uy, double meq[9]);
  * normalised by the square root) under the scalar product sum_i a_i W_i b_i,
  * W_i = f_i^0(1, u). Returns ORC_ERR_INVALID_VELOCITY if some W_i <= 0. */
 int orc_local_basis(double ux, double uy, double mt[81]);
+
+/* Section 4, look-up-table variant: the table velocity u_g = ((k_x - 25)/50,
+ * (k_y - 25)/50) nearest to u, k = floor(50 u + 25.5) in 0..50; returns
+ * ORC_ERR_INVALID_VELOCITY off the table. */
+int orc_lut_velocity(double ux, double uy, double* ugx, double* ugy);
 
 /* Salmon et al. (SC'11) Philox4x32 with 10 rounds. */
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
