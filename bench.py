@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--basis", default="local", choices=["local", "standard"])
+    ap.add_argument("--basis", default="local", choices=["local", "standard", "lut"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--ux0", type=float, default=0.1)
     ap.add_argument("--side", type=int, default=4096)
@@ -427,7 +427,8 @@ MOMENT_NAMES = ("rho", "j_x", "j_y", "Pi_xx-yy", "Pi_xy", "Pi_xx+yy", "q_x", "q_
 # after Figs. 19-21): Hermite norm measured in the Hermite norm, f-norm (its
 # look-up-table variant) measured in the f-norm at u0.
 PAPER_Q = {"standard": {"rho": 1.9, "Pi_xx-yy": 1.6, "j_y": 1.14},
-           "local": {"rho": 0.47, "Pi_xx-yy": 0.54, "j_y": 0.75}}
+           "local": {"rho": 0.47, "Pi_xx-yy": 0.54, "j_y": 0.75},
+           "lut": {"rho": 0.47, "Pi_xx-yy": 0.54, "j_y": 0.75}}
 
 
 def run_sweep(args, rank, world, dist, dev):
@@ -444,15 +445,16 @@ def run_sweep(args, rank, world, dist, dev):
     warm = max(1, args.steps // 10)
     res = {}
     with ClockSampler(smi_id(dev)) as clk:
-        for basis in ("standard", "local"):
+        for basis in ("standard", "local", "lut"):
             rows = []
+            mb = "standard" if basis == "standard" else "local"
             for u in inputs.SWEEP_UX0:
                 p = inputs.single_lattice(u, basis, side=args.side)
                 with flb.Lattice(p, stream=stream) as lat:
                     lat.set_sampling(warm, 1)
                     lat.step(args.steps)
                     lat.sync()
-                    Cff, CMM, mean, n = lat.correlations(basis)
+                    Cff, CMM, mean, n = lat.correlations(mb)
                 dev_ = np.diag(CMM) / (p.kT * p.rho0) - 1.0
                 rows.append((u, dev_, np.diag(Cff) / (p.kT * feq_of(p))))
             us = np.array([r[0] for r in rows])
@@ -634,7 +636,7 @@ def main():
     # the same lattice in the other basis (same size, precision and sampling)
     other = None
     if rank == 0 and world == 1 and not args.no_other_basis:
-        ob = "standard" if args.basis == "local" else "local"
+        ob = "standard" if args.basis != "standard" else "local"
         q = replicas.rank_params(inputs.single_lattice(args.ux0, ob, side=args.side,
                                                        precision=args.precision), rank)
         with flb.Lattice(q, stream=stream) as lo:

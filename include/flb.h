@@ -58,7 +58,15 @@ extern "C" {
 #define FLB_ERR_CUDA (-6)             /* a CUDA runtime call failed */
 #define FLB_ERR_STATE (-7)            /* call not valid in the handle's state (e.g. no samples) */
 
-typedef enum { FLB_BASIS_STANDARD = 0, FLB_BASIS_LOCAL = 1 } flb_basis;
+/* Bases of the collision: the Hermite norm of the appendix (fixed weights
+ * w_i), the f-norm of Section 4 (weights f_i^0(1, u) at the node's own u,
+ * orthogonalised per node), and the f-norm from the paper's 51 x 51 velocity
+ * table (Section 4: the basis at the nearest table velocity u_g, spacing
+ * 0.02, |u_g| <= 0.5; equilibrium moments projected onto it exactly; velocity
+ * off the table or at a table point where some f_i^0(1, u_g) <= 0 is
+ * FLB_ERR_INVALID_VELOCITY). FP64 and FP32 only for the table variant; batches
+ * and the server take the first two. */
+typedef enum { FLB_BASIS_STANDARD = 0, FLB_BASIS_LOCAL = 1, FLB_BASIS_LOCAL_LUT = 2 } flb_basis;
 typedef enum { FLB_FP64 = 0, FLB_FP32 = 1, FLB_FP16_DEV = 2 } flb_precision;
 
 /* Parameters of one periodic lattice. */

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/flb.h"
+#include "flb_basis.cuh"
 #include "flb_host.h"
 #include "flb_runtime.h"
 #include "flb_internal.h"
@@ -32,54 +33,14 @@ __global__ void accumulate_partials_kernel(const double* partials, int nblocks, 
 // Gram matrix sum_i p^a_i p^b_i f_i^0(1,u0), m~ = L^{-1} P. One thread.
 __global__ void measure_basis_kernel(int basis, double ux0, double uy0, double* out) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double P[9][9];
-    {
-        // row a of P = P^T applied to the unit vector e_a (D_1 = -K1, D_2 = -K2)
-        for (int a = 0; a < 9; ++a) {
-            double Dn[6];
-            for (int b = 0; b < 6; ++b) Dn[b] = (a == 3 + b) ? 1.0 : 0.0;
-            double h[9];
-            hermite_back<double, true>(a == 0 ? 1.0 : 0.0, a == 1 ? -1.0 : 0.0,
-                                       a == 2 ? -1.0 : 0.0, Dn, h);
-            for (int i = 0; i < 9; ++i) P[a][i] = h[i];
-        }
-    }
     if (basis == FLB_BASIS_STANDARD) {
+        double P[9][9];
+        hermite_rows_fp64(P);
         for (int a = 0; a < 9; ++a)
             for (int i = 0; i < 9; ++i) out[a * 9 + i] = P[a][i];
         return;
     }
-    double W[9];
-    const double usq = ux0 * ux0 + uy0 * uy0;
-    for (int i = 0; i < 9; ++i) {
-        const double uv = ux0 * cvx(i) + uy0 * cvy(i);
-        const double wi = i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
-        W[i] = wi * (1.0 + 3.0 * uv + 4.5 * uv * uv - 1.5 * usq);
-    }
-    double L[9][9];
-    for (int a = 0; a < 9; ++a)
-        for (int b = 0; b < 9; ++b) {
-            double s = 0.0;
-            for (int i = 0; i < 9; ++i) s += P[a][i] * W[i] * P[b][i];
-            L[a][b] = s;
-        }
-    for (int j = 0; j < 9; ++j) {
-        double d = L[j][j];
-        for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
-        d = sqrt(d);
-        L[j][j] = d;
-        for (int i = j + 1; i < 9; ++i) {
-            double s = L[i][j];
-            for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
-            L[i][j] = s / d;
-        }
-    }
-    for (int i = 0; i < 9; ++i)          // forward substitution per column of P
-        for (int a = 0; a < 9; ++a) {
-            double s = P[a][i];
-            for (int k = 0; k < a; ++k) s -= L[a][k] * out[k * 9 + i];
-            out[a * 9 + i] = s / L[a][a];
-        }
+    fnorm_basis_fp64(ux0, uy0, out);
 }
 
 __global__ void finalize_kernel(const double* acc, long long nsamp, const double* B,
@@ -242,14 +203,20 @@ __global__ void noise_draws_kernel(uint64_t seed, uint32_t replica, uint32_t ste
 
 template <class T, int BASIS>
 __global__ void collide_nodes_kernel(const double* g, const uint32_t* ids, uint32_t step,
-                                     int n, CollideConst<T> cc, double* fs, int* status) {
+                                     int n, CollideConst<T> cc, const T* lut, double* fs,
+                                     int* status) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     T gg[9], ff[9];
     for (int i = 0; i < 9; ++i) gg[i] = (T)g[k * 9 + i];
     const uint32_t id = ids[k];
-    const int st = (int)(collide<T, BASIS>(
-        gg, [&](T* N) { node_normals(cc.key, id, step, N); }, cc, ff) & 0xFF);
+    const int st = (int)(collide_basis<T, BASIS>(
+                             gg, [&](T* N) { node_normals(cc.key, id, step, N); },
+                             [&](T* g2) {
+                                 for (int i = 0; i < 9; ++i) g2[i] = gg[i];
+                             },
+                             lut, cc, ff) &
+                         0xFF);
     for (int i = 0; i < 9; ++i) fs[k * 9 + i] = (double)ff[i];
     status[k] = st;
 }
@@ -281,6 +248,8 @@ struct flb_lattice_s {
     int sticky;
     int variant;           // FLB_KERNEL_*
     TmaPlan tma;           // pipelined FP32 kernel (tensor maps, launch shape)
+    const float* lut32 = nullptr;    // velocity tables (look-up-table f-norm)
+    const double* lut64 = nullptr;
     double ref[9];
 };
 
@@ -344,6 +313,7 @@ cudaError_t launch_step_t(flb_lattice h) {
     a.step = (uint32_t)h->t;
     a.partials = h->partials;
     a.err = h->err;
+    a.lut = (const T*)(sizeof(T) == 8 ? (const void*)h->lut64 : (const void*)h->lut32);
     for (int i = 0; i < 9; ++i) a.ref[i] = (T)h->ref[i];
     step_kernel<T, BASIS, SAMPLE><<<h->nblocks, kStepThreads, 0, h->stream>>>(
         a, collide_const<T>(&h->p));
@@ -354,7 +324,9 @@ template <class T>
 cudaError_t launch_step_p(flb_lattice h, bool sample) {
     if (h->p.basis == FLB_BASIS_STANDARD)
         return sample ? launch_step_t<T, 0, true>(h) : launch_step_t<T, 0, false>(h);
-    return sample ? launch_step_t<T, 1, true>(h) : launch_step_t<T, 1, false>(h);
+    if (h->p.basis == FLB_BASIS_LOCAL)
+        return sample ? launch_step_t<T, 1, true>(h) : launch_step_t<T, 1, false>(h);
+    return sample ? launch_step_t<T, 2, true>(h) : launch_step_t<T, 2, false>(h);
 }
 
 // Pipelined FP32 kernel: also reduces the sampled sums into h->acc itself.
@@ -366,6 +338,7 @@ cudaError_t launch_step_tma(flb_lattice h, bool sample) {
     a.tiles_x = a.ntiles = 0;
     a.acc = h->acc;
     a.err = h->err;
+    a.lut = h->lut32;
     for (int i = 0; i < 9; ++i) a.ref[i] = (float)h->ref[i];
     return tma_step(h->tma, h->cur, a, collide_const<float>(&h->p), h->p.basis, sample, h->stream);
 }
@@ -482,6 +455,9 @@ int lattice_create(const flb_params* p, void* dev_workspace, size_t workspace_by
     }
     if (ce == cudaSuccess && sync) ce = cudaStreamSynchronize(h->stream);
     h->tma.sample_mode = 0;   // library default
+    if (ce == cudaSuccess && p->basis == FLB_BASIS_LOCAL_LUT &&
+        lut_tables(&h->lut32, &h->lut64) != FLB_OK)
+        ce = cudaErrorUnknown;
     if (ce == cudaSuccess && p->precision == FLB_FP32)
         ce = tma_plan(&h->tma, h->buf[0], h->buf[1], h->geo, 0);
     if (ce == cudaSuccess && p->precision == FLB_FP16_DEV)
@@ -875,22 +851,28 @@ int flb_collide_nodes(const flb_params* p, const double* g, const uint32_t* node
         ce = cudaMemcpy(d_g, g, 9 * (size_t)n * sizeof(double), cudaMemcpyHostToDevice);
     if (ce == cudaSuccess)
         ce = cudaMemcpy(d_ids, node_ids, (size_t)n * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    const float* l32 = nullptr;
+    const double* l64 = nullptr;
+    if (ce == cudaSuccess && p->basis == FLB_BASIS_LOCAL_LUT && lut_tables(&l32, &l64) != FLB_OK)
+        ce = cudaErrorUnknown;
     if (ce == cudaSuccess) {
         const int grid = (n + 127) / 128;
         if (p->precision == FLB_FP64) {
+            const CollideConst<double> cc = collide_const<double>(p);
             if (p->basis == FLB_BASIS_STANDARD)
-                collide_nodes_kernel<double, 0><<<grid, 128>>>(d_g, d_ids, step, n,
-                                                               collide_const<double>(p), d_f, d_st);
+                collide_nodes_kernel<double, 0><<<grid, 128>>>(d_g, d_ids, step, n, cc, l64, d_f, d_st);
+            else if (p->basis == FLB_BASIS_LOCAL)
+                collide_nodes_kernel<double, 1><<<grid, 128>>>(d_g, d_ids, step, n, cc, l64, d_f, d_st);
             else
-                collide_nodes_kernel<double, 1><<<grid, 128>>>(d_g, d_ids, step, n,
-                                                               collide_const<double>(p), d_f, d_st);
+                collide_nodes_kernel<double, 2><<<grid, 128>>>(d_g, d_ids, step, n, cc, l64, d_f, d_st);
         } else {
+            const CollideConst<float> cc = collide_const<float>(p);
             if (p->basis == FLB_BASIS_STANDARD)
-                collide_nodes_kernel<float, 0><<<grid, 128>>>(d_g, d_ids, step, n,
-                                                              collide_const<float>(p), d_f, d_st);
+                collide_nodes_kernel<float, 0><<<grid, 128>>>(d_g, d_ids, step, n, cc, l32, d_f, d_st);
+            else if (p->basis == FLB_BASIS_LOCAL)
+                collide_nodes_kernel<float, 1><<<grid, 128>>>(d_g, d_ids, step, n, cc, l32, d_f, d_st);
             else
-                collide_nodes_kernel<float, 1><<<grid, 128>>>(d_g, d_ids, step, n,
-                                                              collide_const<float>(p), d_f, d_st);
+                collide_nodes_kernel<float, 2><<<grid, 128>>>(d_g, d_ids, step, n, cc, l32, d_f, d_st);
         }
         ce = cudaGetLastError();
     }

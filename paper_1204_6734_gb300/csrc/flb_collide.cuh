@@ -347,4 +347,163 @@ __device__ __forceinline__ uint32_t collide(const V g[9], Noise noise, Refetch r
     return st;
 }
 
+// ---------------------------------------------------------------------------
+// Look-up-table f-norm (Section 4, the paper's practical variant): the basis at
+// the nearest velocity u_g of a 51 x 51 table, u_g = ((k_x - 25)/50,
+// (k_y - 25)/50), k = floor(50 u + 25.5) in 0..50. A table entry holds, each
+// padded to kLutRow values, the rows a = 3..8 of the f-norm basis at u_g, the
+// weights W(u_g) = f^0(1, u_g), and a validity flag (0 where some W_i <= 0).
+// The collision: Y^a = m~^a(u_g) . (g - f^0(rho, u)) is the non-equilibrium
+// moment in the table basis (the equilibrium moments are the projection of the
+// node's own f^0, taken exactly), D^a = -omega_a Y^a + xi^a N^a, and
+// f* = g + W(u_g) (.) sum_a m~^a D^a.
+// ---------------------------------------------------------------------------
+constexpr int kLutN = 51;
+constexpr int kLutRow = 12;
+constexpr int kLutStride = 8 * kLutRow;   // 6 rows, W, flag (+ padding)
+constexpr int kLutW = 6 * kLutRow;
+constexpr int kLutFlag = 7 * kLutRow;
+
+__device__ __forceinline__ double lut_coord(double u) {
+    return floor(__dadd_rn(__dmul_rn(50.0, u), 25.5));
+}
+__device__ __forceinline__ float lut_coord(float u) {
+    return floorf(__fadd_rn(__fmul_rn(50.0f, u), 25.5f));
+}
+
+// Table cell of velocity u, or -1 off the table (NaN included).
+template <class S>
+__device__ __forceinline__ int lut_cell(S ux, S uy) {
+    const S kx = lut_coord(ux), ky = lut_coord(uy);
+    if (!(kx >= S(0) && kx <= S(kLutN - 1) && ky >= S(0) && ky <= S(kLutN - 1))) return -1;
+    return (int)ky * kLutN + (int)kx;
+}
+
+// Row of kLutRow table values (16-byte aligned) through the read-only path.
+__device__ __forceinline__ void lut_load_row(const float* p, float (&r)[kLutRow]) {
+    const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+    for (int k = 0; k < kLutRow / 4; ++k) {
+        const float4 v = __ldg(q + k);
+        r[4 * k] = v.x;
+        r[4 * k + 1] = v.y;
+        r[4 * k + 2] = v.z;
+        r[4 * k + 3] = v.w;
+    }
+}
+__device__ __forceinline__ void lut_load_row(const double* p, double (&r)[kLutRow]) {
+    const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+    for (int k = 0; k < kLutRow / 2; ++k) {
+        const double2 v = __ldg(q + k);
+        r[2 * k] = v.x;
+        r[2 * k + 1] = v.y;
+    }
+}
+
+template <class V, class Noise>
+__device__ __forceinline__ uint32_t collide_lut(const V g[9], Noise noise,
+                                                const typename Elem<V>::type* lut,
+                                                const CollideConst<typename Elem<V>::type>& cc,
+                                                V f[9]) {
+    using S = typename Elem<V>::type;
+    constexpr int NL = Lanes<V>::n;
+    const V s13 = g[1] + g[3], s24 = g[2] + g[4];
+    const V d13 = g[1] - g[3], d24 = g[2] - g[4];
+    const V c58 = g[5] + g[8], c67 = g[6] + g[7];
+    const V c56 = g[5] + g[6], c78 = g[7] + g[8];
+    const V rho = (g[0] + (s13 + s24)) + (c58 + c67);
+    const V jx = d13 + (c58 - c67), jy = d24 + (c56 - c78);
+    const V ir = rcp(rho);
+    const V ux = jx * ir, uy = jy * ir;
+    // table entry per lane
+    const S* e[NL];
+    uint32_t st = 0;
+#pragma unroll
+    for (int k = 0; k < NL; ++k) {
+        const S r = lane(rho, k);
+        const int cell = lut_cell(lane(ux, k), lane(uy, k));
+        e[k] = lut + (size_t)(cell < 0 ? 0 : cell) * kLutStride;
+        uint32_t s = kStatusOk;
+        if (!(r > S(0)) || !isfinite(r))
+            s = kStatusNonfinite;
+        else if (cell < 0 || __ldg(e[k] + kLutFlag) == S(0))
+            s = kStatusInvalidVelocity;
+        st |= s << (8 * k);
+    }
+    // one table row (9 values of each lane's entry) with vector loads
+    auto row_of = [&](int off, V r[9]) {
+        S a[NL][kLutRow];
+#pragma unroll
+        for (int k = 0; k < NL; ++k) lut_load_row(e[k] + off, a[k]);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            if constexpr (NL == 1)
+                r[i] = V(a[0][i]);
+            else
+                r[i] = V(a[0][i], a[NL - 1][i]);
+        }
+    };
+    // g - f^0(rho, u) (Eq. d2q9f0)
+    V d[9];
+    {
+        const V uxx = ux * ux, uyy = uy * uy, uxy = ux * uy;
+        const V usq = uxx + uyy;
+        const V base = mad(usq, V(S(-1.5)), V(S(1)));
+        const V b45 = mad(usq, V(S(4.5)), base);
+        const V ax = mad(uxx, V(S(4.5)), base), ay = mad(uyy, V(S(4.5)), base);
+        const V dp = mad(uxy, V(S(9)), b45), dm = mad(uxy, V(S(-9)), b45);
+        const V spy = ux + uy, smy = ux - uy;
+        const V r9 = rho * V(S(1.0 / 9.0)), r36 = rho * V(S(1.0 / 36.0));
+        const V tx = ax * r9, ty = ay * r9, tp = dp * r36, tm = dm * r36;
+        const V rx = rho * ux * V(S(1.0 / 3.0)), ry = rho * uy * V(S(1.0 / 3.0));
+        const V rp = rho * spy * V(S(1.0 / 12.0)), rm = rho * smy * V(S(1.0 / 12.0));
+        d[0] = g[0] - (base * rho) * V(S(4.0 / 9.0));
+        d[1] = g[1] - (tx + rx);
+        d[3] = g[3] - (tx - rx);
+        d[2] = g[2] - (ty + ry);
+        d[4] = g[4] - (ty - ry);
+        d[5] = g[5] - (tp + rp);
+        d[7] = g[7] - (tp - rp);
+        d[8] = g[8] - (tm + rm);
+        d[6] = g[6] - (tm - rm);
+    }
+    V N[6];
+    noise(N);
+    const V sr = sqr(rho);
+    V h[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) h[i] = V(S(0));
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+        V row[9];
+        row_of(a * kLutRow, row);
+        V y = row[0] * d[0];
+#pragma unroll
+        for (int i = 1; i < 9; ++i) y = mad(row[i], d[i], y);
+        const V D = mad(V(cc.nomega[a]), y, (sr * N[a]) * V(cc.amp[a]));
+#pragma unroll
+        for (int i = 0; i < 9; ++i) h[i] = mad(row[i], D, h[i]);
+    }
+    V W[9];
+    row_of(kLutW, W);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i] = mad(W[i], h[i], g[i]);
+    keep_invalid(st, g, f);
+    return st;
+}
+
+// The collision of basis BASIS: 0 Hermite norm, 1 f-norm, 2 look-up-table
+// f-norm (lut: the velocity table, unused otherwise).
+template <class V, int BASIS, class Noise, class Refetch>
+__device__ __forceinline__ uint32_t collide_basis(const V g[9], Noise noise, Refetch refetch,
+                                                  const typename Elem<V>::type* lut,
+                                                  const CollideConst<typename Elem<V>::type>& cc,
+                                                  V f[9]) {
+    if constexpr (BASIS == 2)
+        return collide_lut<V>(g, noise, lut, cc, f);
+    else
+        return collide<V, BASIS>(g, noise, refetch, cc, f);
+}
+
 }  // namespace flb

@@ -33,10 +33,13 @@ inline int valid_params(const flb_params* p) {
     if (!std::isfinite(p->ux0) || !std::isfinite(p->uy0)) return 0;
     for (int a = 3; a < 9; ++a)
         if (!(p->omega[a] > 0 && p->omega[a] < 2)) return 0;
-    if (p->basis != FLB_BASIS_STANDARD && p->basis != FLB_BASIS_LOCAL) return 0;
+    if (p->basis != FLB_BASIS_STANDARD && p->basis != FLB_BASIS_LOCAL &&
+        p->basis != FLB_BASIS_LOCAL_LUT)
+        return 0;
     if (p->precision != FLB_FP64 && p->precision != FLB_FP32 && p->precision != FLB_FP16_DEV)
         return 0;
     if (p->precision == FLB_FP16_DEV && !(p->kT > 0)) return 0;   // the store scale is sqrt(kT)
+    if (p->precision == FLB_FP16_DEV && p->basis == FLB_BASIS_LOCAL_LUT) return 0;
     if (p->reserved != 0) return 0;
     // the mean velocity must leave every f_i^0(1,u0) > 0 (Fig. 11)
     const double usq = p->ux0 * p->ux0 + p->uy0 * p->uy0;

@@ -17,6 +17,7 @@ struct TmaArgs {
     int tiles_x, ntiles;    // 128 x TH tiles of the lattice
     double* acc;            // running FP64 sums (sampling)
     DevError* err;
+    const float* lut;       // velocity table (look-up-table f-norm only)
     float ref[9];           // f^0(rho0, u0) subtracted before sampling
 };
 
@@ -60,7 +61,8 @@ cudaError_t fp16_plan(TmaPlan* plan, void* buf0, void* buf1, const Geometry& g);
 cudaError_t fp16_step(const TmaPlan& plan, int src, const HArgs& a, const CollideConst<float>& cc,
                       int basis, bool sample, cudaStream_t s);
 
-// One fused step from buffer `src` into a.dst. basis: 0 Hermite, 1 f-norm.
+// One fused step from buffer `src` into a.dst. basis: 0 Hermite, 1 f-norm,
+// 2 look-up-table f-norm.
 cudaError_t tma_step(const TmaPlan& plan, int src, const TmaArgs& a,
                      const CollideConst<float>& cc, int basis, bool sample, cudaStream_t s);
 

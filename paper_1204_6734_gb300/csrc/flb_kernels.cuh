@@ -39,6 +39,7 @@ struct StepArgs {
     uint32_t step;
     double* partials;   // [gridDim.x][kSums] when sampling
     DevError* err;
+    const T* lut;       // velocity table (look-up-table f-norm only)
     T ref[9];           // c = f^0(rho0, u0), subtracted before sampling
 };
 
@@ -107,8 +108,13 @@ step_kernel(StepArgs<T> a, CollideConst<T> cc) {
             }
         }
         T f[9];
-        const uint32_t st = collide<T, BASIS>(
-            g, [&](T* N) { node_normals(cc.key, (uint32_t)n, a.step, N); }, cc, f);
+        const uint32_t st = collide_basis<T, BASIS>(
+            g, [&](T* N) { node_normals(cc.key, (uint32_t)n, a.step, N); },
+            [&](T* gg) {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) gg[i] = g[i];
+            },
+            a.lut, cc, f);
         if (st != kStatusOk) record_error(a.err, (int)(st & 0xFF), n, a.step);
         store_node(a.dst, a.geo, x, y, f);
     }

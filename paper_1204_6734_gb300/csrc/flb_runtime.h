@@ -36,6 +36,11 @@ int lattice_enqueue_readout(flb_lattice h, double* acc_out, DevError* err_out);
 int64_t lattice_samples(flb_lattice h);
 int64_t lattice_time(flb_lattice h);
 
+// Device addresses of the look-up-table f-norm's velocity tables (FP32 and
+// FP64) on the current device, built on first use (synchronously, on a stream
+// of its own). Either pointer may be NULL.
+int lut_tables(const float** t32, const double** t64);
+
 // Free the host side of a handle whose workspace the caller owns, without
 // waiting for its stream: the caller orders any reuse of the workspace after
 // the handle's last enqueued work.

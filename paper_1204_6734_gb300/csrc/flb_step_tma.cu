@@ -301,8 +301,9 @@ step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
         }
         const uint32_t nodeA = (uint32_t)xA + (uint32_t)Lx * (uint32_t)y;
         f2 f[9];
-        const uint32_t stt = collide<f2, BASIS>(
-            g, [&](f2* N) { node_normals(cc.key, nodeA, nodeA + 64u, a.step, N); }, load, cc, f);
+        const uint32_t stt = collide_basis<f2, BASIS>(
+            g, [&](f2* N) { node_normals(cc.key, nodeA, nodeA + 64u, a.step, N); }, load, a.lut,
+            cc, f);
         // the stage is held until g was read the second time
         __syncwarp();
         if (lane_id == 0) mbar_arrive(&empty[s]);
@@ -361,8 +362,9 @@ EncodeFn encode_fn() {
 
 template <int NW, int MODE>
 const void* kernel_ptr_m(int basis) {
-    return basis == 0 ? (const void*)step_tma_kernel<0, MODE, NW>
-                      : (const void*)step_tma_kernel<1, MODE, NW>;
+    if (basis == 0) return (const void*)step_tma_kernel<0, MODE, NW>;
+    if (basis == 1) return (const void*)step_tma_kernel<1, MODE, NW>;
+    return (const void*)step_tma_kernel<2, MODE, NW>;
 }
 
 template <int NW>
@@ -426,7 +428,7 @@ cudaError_t tma_plan(TmaPlan* plan, void* buf0, void* buf1, const Geometry& g, i
     cudaError_t ce = cudaGetDevice(&dev);
     if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int per_sm = 2;
-    for (int basis = 0; basis < 2 && ce == cudaSuccess; ++basis)
+    for (int basis = 0; basis < 3 && ce == cudaSuccess; ++basis)
         for (int mode = 0; mode < 3 && ce == cudaSuccess; ++mode) {
             const void* fn = kernel_for(nw, basis, mode);
             ce = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -22,7 +22,7 @@ from . import build as _build
 OK = 0
 ERR_ARG, ERR_OOM, ERR_INVALID_VELOCITY, ERR_NONFINITE, ERR_TIMEOUT, ERR_CUDA, ERR_STATE = (
     -1, -2, -3, -4, -5, -6, -7)
-BASIS = {"standard": 0, "local": 1}
+BASIS = {"standard": 0, "local": 1, "lut": 2}
 OPT_KERNEL, OPT_PIPELINE_WARPS, OPT_PIPELINE_SAMPLING = 0, 1, 2
 KERNEL = {"auto": 0, "generic": 1, "pipelined": 2}
 PRECISION = {"fp64": 0, "fp32": 1, "fp16dev": 2}

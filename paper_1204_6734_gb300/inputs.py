@@ -21,6 +21,7 @@ import numpy as np
 
 STANDARD = "standard"
 LOCAL = "local"
+LUT = "lut"         # the f-norm from the paper's velocity table (Section 4)
 
 
 def omega_groups(shear: float, bulk: float, ghost: float) -> tuple:
@@ -68,9 +69,9 @@ SWEEP_UX0 = (0.0, 0.05, 0.1, 0.2, 0.3)
 def single_lattice(ux0: float = 0.1, basis: str = LOCAL, side: int = 4096,
                    precision: str = "fp32") -> LatticeParams:
     """The 4096^2 FP32 lattice: kT = 1e-4, shear 1.0, bulk 0.8, ghost 1.0,
-    seed 1000 + 10 i_u + (0 standard | 1 local)."""
+    seed 1000 + 10 i_u + (0 standard | 1 local | 2 look-up-table f-norm)."""
     iu = SWEEP_UX0.index(ux0) if ux0 in SWEEP_UX0 else 0
-    seed = 1000 + 10 * iu + (1 if basis == LOCAL else 0)
+    seed = 1000 + 10 * iu + {STANDARD: 0, LOCAL: 1, LUT: 2}[basis]
     return LatticeParams(side, side, 1.0, ux0, 0.0, 1e-4, omega_groups(1.0, 0.8, 1.0),
                          basis, precision, seed=seed)
 
