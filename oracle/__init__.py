@@ -241,3 +241,62 @@ def moment_covariance(Cff, measure_basis, ux0, uy0):
     """<dM^a dM^b> = sum_ij m^a_i m^b_j <df_i df_j> (Eq. dfidfj2dmadmb)."""
     m = measure_matrix(measure_basis, ux0, uy0)
     return m @ np.asarray(Cff) @ m.T
+
+
+# --------------------------------------------------------------------------
+# Static structure factors (Eqs. sfactorr, sfactoru, rcorrelator)
+# --------------------------------------------------------------------------
+
+def hydro_fields(f, p):
+    """delta rho(x) = rho(x) - rho0 and delta j(x) = j(x) - rho0 u0 of a state
+    f[i, y, x] (the fields the structure factors transform)."""
+    vx, vy, *_ = tables()
+    rho = f.sum(axis=0)
+    jx = np.tensordot(vx, f, axes=1)
+    jy = np.tensordot(vy, f, axes=1)
+    return rho - p.rho0, jx - p.rho0 * p.ux0, jy - p.rho0 * p.uy0
+
+
+def dft2(a):
+    """a(k) = sum_x a(x) exp(-i k.x), k = 2 pi (m_x / Lx, m_y / Ly); array
+    index [m_y, m_x] (numpy's forward FFT has this sign and no normalisation)."""
+    return np.fft.fft2(a)
+
+
+def structure_sample(f, p):
+    """One sample's |drho(k)|^2, |dj_x(k)|^2 and dj_x(k) dj_y(-k) (complex),
+    each of shape (Ly, Lx)."""
+    dr, djx, djy = hydro_fields(f, p)
+    R, X, Y = dft2(dr), dft2(djx), dft2(djy)
+    return np.abs(R) ** 2, np.abs(X) ** 2, X * np.conj(Y)
+
+
+class StructureRun:
+    """An oracle run that also accumulates the structure factors of the
+    pre-collision state at t = warmup, warmup + every, ...:
+    S_k(rho) = <drho(k) drho(-k)> / rho0, S_k(j_x) = <dj_x(k) dj_x(-k)> / rho0,
+    R_k(j_x, j_y) = <dj_x(k) dj_y(-k)> / rho0 (complex)."""
+
+    def __init__(self, p, f=None, warmup=0, every=1):
+        self.run = Run(p, f=f)
+        self.p, self.warmup, self.every = p, int(warmup), int(every)
+        shape = (p.Ly, p.Lx)
+        self.srr, self.sxx = np.zeros(shape), np.zeros(shape)
+        self.rxy = np.zeros(shape, dtype=complex)
+        self.nsamp = 0
+
+    def step(self, n):
+        for _ in range(int(n)):
+            t = self.run.t
+            if self.every > 0 and t >= self.warmup and (t - self.warmup) % self.every == 0:
+                a, b, c = structure_sample(self.run.f, self.p)
+                self.srr += a
+                self.sxx += b
+                self.rxy += c
+                self.nsamp += 1
+            self.run.step(1)
+        return self
+
+    def factors(self):
+        k = 1.0 / (self.nsamp * self.p.rho0)
+        return self.srr * k, self.sxx * k, self.rxy * k
