@@ -172,6 +172,33 @@ int flb_set_populations(flb_lattice h, const double* host_in);
  * Synchronises both handles' streams. Errors: FLB_ERR_ARG (sizes differ). */
 int flb_state_difference(flb_lattice a, flb_lattice b, double out[3]);
 
+/* Static structure factors (Eqs. sfactorr, sfactoru, rcorrelator).
+ * flb_set_structure_sampling samples the pre-collision state of every step t
+ * with t >= warmup and (t - warmup) % every == 0 (every = 0: off) and clears
+ * the sums. On a sampling step, before the step's collision, the device forms
+ * delta rho(x) = rho(x) - rho0, delta j(x) = j(x) - rho0 u0, transforms them,
+ * a(k) = sum_x a(x) exp(-i k.x) with k = 2 pi (m_x / Lx, m_y / Ly), and adds
+ * |drho(k)|^2, |dj_x(k)|^2 and dj_x(k) conj(dj_y(k)) to FP64 sums. The
+ * transform runs in FP64 for FP64 lattices, in FP32 otherwise: radix-2 FFTs
+ * for power-of-two sides, a direct O(L^2) transform per row or column for
+ * other sides. The first call with every > 0 allocates the library's own
+ * device buffers (4 complex plus 4 double arrays of Lx*Ly values), freed by
+ * flb_destroy. Errors: FLB_ERR_ARG (negative arguments; a side above 20480 in
+ * FP32 or 10240 in FP64), FLB_ERR_OOM, a recorded device error (sticky). */
+int flb_set_structure_sampling(flb_lattice h, int64_t warmup, int64_t every);
+
+/* The sampled factors, each an Ly x Lx array indexed [m_y][m_x] (host memory,
+ * caller-owned): S_rho = <|drho(k)|^2> / rho0, S_jx = <|dj_x(k)|^2> / rho0 and
+ * R = <dj_x(k) conj(dj_y(k))> / rho0 = R_re + i R_im, averages over the
+ * samples. At rest (u0 = 0) every k != 0 mode of S_rho approaches Lx Ly kT
+ * and of S_jx Lx Ly kT / 3, the per-site variances kT rho0 and kT rho0 / 3 of
+ * the fluctuating equilibrium; R approaches 0. Any array pointer may be NULL;
+ * *n_samples (may be NULL) receives the number of samples. Synchronises.
+ * Errors: FLB_ERR_STATE when an array is asked for and nothing was sampled,
+ * FLB_ERR_OOM, FLB_ERR_CUDA. */
+int flb_structure_factors(flb_lattice h, double* S_rho, double* S_jx, double* R_re, double* R_im,
+                          int64_t* n_samples);
+
 /* Whole-job entry point with host buffers: create a lattice, upload the
  * initial state (or start from equilibrium when f_in is NULL), run nsteps
  * with sampling (warmup, every), and copy back the final state (f_out may be

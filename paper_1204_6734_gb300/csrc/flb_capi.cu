@@ -15,6 +15,7 @@
 #include "flb_runtime.h"
 #include "flb_internal.h"
 #include "flb_io.cuh"
+#include "flb_structure.h"
 #include "flb_kernels.cuh"
 
 namespace flb {
@@ -251,6 +252,8 @@ struct flb_lattice_s {
     const float* lut32 = nullptr;    // velocity tables (look-up-table f-norm)
     const double* lut64 = nullptr;
     double ref[9];
+    StructSampler* sk = nullptr;      // structure factors (allocated on demand)
+    int64_t sk_warmup = 0, sk_every = 0;
 };
 
 namespace {
@@ -522,6 +525,7 @@ int flb_create(const flb_params* p, void* dev_workspace, size_t workspace_bytes,
 int flb_destroy(flb_lattice h) {
     if (!h) return FLB_OK;
     cudaError_t ce = cudaStreamSynchronize(h->stream);
+    structure_destroy(h->sk);
     if (h->own_ws) {
         cudaError_t fe = cudaFree(h->ws);
         if (ce == cudaSuccess) ce = fe;
@@ -543,6 +547,43 @@ int flb_set_sampling(flb_lattice h, int64_t warmup, int64_t every) {
     return flb_reset_statistics(h);
 }
 
+int flb_set_structure_sampling(flb_lattice h, int64_t warmup, int64_t every) {
+    if (!h || warmup < 0 || every < 0) return FLB_ERR_ARG;
+    if (h->sticky) return h->sticky;
+    if (every > 0 && !h->sk) {
+        const int rc = structure_create(&h->sk, h->p.Lx, h->p.Ly,
+                                        h->p.precision == FLB_FP64 ? 8 : 4);
+        if (rc) return rc;
+    }
+    h->sk_warmup = warmup;
+    h->sk_every = every;
+    return h->sk ? cuda_rc(structure_reset(h->sk, h->stream)) : FLB_OK;
+}
+
+int flb_structure_factors(flb_lattice h, double* S_rho, double* S_jx, double* R_re, double* R_im,
+                          int64_t* n_samples) {
+    if (!h) return FLB_ERR_ARG;
+    const int64_t ns = structure_samples(h->sk);
+    if (n_samples) *n_samples = ns;
+    if (!S_rho && !S_jx && !R_re && !R_im) return FLB_OK;
+    if (!h->sk || ns == 0) return FLB_ERR_STATE;
+    const size_t N = (size_t)h->p.Lx * h->p.Ly;
+    std::vector<double> sums;
+    try {
+        sums.resize(4 * N);
+    } catch (const std::bad_alloc&) {
+        return FLB_ERR_OOM;
+    }
+    const int rc = structure_read(h->sk, sums.data(), h->stream);
+    if (rc) return rc;
+    const double k = 1.0 / ((double)ns * h->p.rho0);
+    double* out[4] = {S_rho, S_jx, R_re, R_im};
+    for (int q = 0; q < 4; ++q)
+        if (out[q])
+            for (size_t n = 0; n < N; ++n) out[q][n] = sums[q * N + n] * k;
+    return FLB_OK;
+}
+
 int flb_step(flb_lattice h, int64_t n) {
     if (!h || n < 0) return FLB_ERR_ARG;
     if (h->sticky) return h->sticky;
@@ -550,7 +591,11 @@ int flb_step(flb_lattice h, int64_t n) {
     for (int64_t s = 0; s < n; ++s) {
         const bool sample =
             h->every > 0 && h->t >= h->warmup && ((h->t - h->warmup) % h->every) == 0;
-        cudaError_t ce = launch_step(h, sample);
+        cudaError_t ce = cudaSuccess;
+        if (h->sk_every > 0 && h->t >= h->sk_warmup && ((h->t - h->sk_warmup) % h->sk_every) == 0)
+            ce = structure_sample(h->sk, h->buf[h->cur], h->p.precision, h->geo, dev_codec(h), h->ref,
+                                  h->stream);
+        if (ce == cudaSuccess) ce = launch_step(h, sample);
         if (ce == cudaSuccess && sample && !reduces_in_kernel(h)) {
             accumulate_partials_kernel<<<kSums, 32, 0, h->stream>>>(h->partials, h->nblocks,
                                                                      h->acc);

@@ -1,0 +1,35 @@
+// flb_structure.h -- static structure factors of a lattice's hydrodynamic
+// fields (Eqs. sfactorr, sfactoru, rcorrelator), sampled on the device.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "flb_io.cuh"
+#include "flb_layout.cuh"
+
+namespace flb {
+
+struct StructSampler;
+
+// Device buffers for an Lx x Ly lattice at transform precision rbytes (4:
+// FP32, 8: FP64); FLB_ERR_ARG when a row or column of complex values does not
+// fit one CTA's shared memory (sides above 20480 in FP32, 10240 in FP64);
+// FLB_ERR_OOM when an allocation fails.
+int structure_create(StructSampler** out, int Lx, int Ly, int rbytes);
+void structure_destroy(StructSampler* s);
+cudaError_t structure_reset(StructSampler* s, cudaStream_t st);
+// One sample of the pre-collision state the pull from `buf` gives:
+// accumulates |drho(k)|^2, |dj_x(k)|^2 and dj_x(k) conj(dj_y(k)); ref[9] is
+// f^0(rho0, u0), the fields being sums of f_i - ref_i.
+cudaError_t structure_sample(StructSampler* s, const void* buf, int precision, const Geometry& geo,
+                             const DevCodec& codec, const double* ref, cudaStream_t st);
+// The four FP64 sums [S_rho | S_jx | Re R | Im R], each Ly x Lx ([m_y][m_x]),
+// unnormalised, into host memory; synchronises the stream. FLB_OK,
+// FLB_ERR_OOM or FLB_ERR_CUDA.
+int structure_read(StructSampler* s, double* host4N, cudaStream_t st);
+int64_t structure_samples(const StructSampler* s);
+
+}  // namespace flb

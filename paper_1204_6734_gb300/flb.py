@@ -101,6 +101,8 @@ def load(build_if_missing: bool = True):
         "flb_conservation": (C.c_int, [h, _dp]),
         "flb_get_populations": (C.c_int, [h, _dp]),
         "flb_state_difference": (C.c_int, [h, h, _dp]),
+        "flb_set_structure_sampling": (C.c_int, [h, C.c_int64, C.c_int64]),
+        "flb_structure_factors": (C.c_int, [h, _dp, _dp, _dp, _dp, _i64p]),
         "flb_set_populations": (C.c_int, [h, _dp]),
         "flb_run_host": (C.c_int, [P, _dp, C.c_int64, C.c_int64, C.c_int64, _dp, _dp, _dp, _i64p]),
         "flb_noise_draws": (C.c_int, [C.c_uint64, C.c_uint32, C.c_uint32, _u32p, C.c_int32,
@@ -164,7 +166,7 @@ def exported_symbols():
             "flb_batch_replica_time", "flb_batch_info", "flb_batch_raw_sums",
             "flb_batch_get_populations", "flb_batch_set_populations", "flb_server_create",
             "flb_server_destroy", "flb_server_submit", "flb_server_poll", "flb_server_stats",
-            "flb_server_set_tile"]
+            "flb_server_set_tile", "flb_set_structure_sampling", "flb_structure_factors"]
 
 
 def _check(rc: int, what: str):
@@ -297,6 +299,22 @@ def flb_state_difference(a, b):
     out = np.zeros(3)
     _check(load().flb_state_difference(a, b, _ptr(out)), "flb_state_difference")
     return tuple(out)
+
+
+def flb_set_structure_sampling(h, warmup: int, every: int) -> None:
+    _check(load().flb_set_structure_sampling(h, int(warmup), int(every)),
+           "flb_set_structure_sampling")
+
+
+def flb_structure_factors(h, Lx: int, Ly: int):
+    """(S_rho, S_jx, R, n_samples): S_k(rho), S_k(j_x) and the complex
+    R_k(j_x, j_y), each (Ly, Lx) indexed [m_y, m_x]."""
+    Sr, Sx = np.empty((Ly, Lx)), np.empty((Ly, Lx))
+    Rr, Ri = np.empty((Ly, Lx)), np.empty((Ly, Lx))
+    n = C.c_int64()
+    _check(load().flb_structure_factors(h, _ptr(Sr), _ptr(Sx), _ptr(Rr), _ptr(Ri), C.byref(n)),
+           "flb_structure_factors")
+    return Sr, Sx, Rr + 1j * Ri, n.value
 
 
 def flb_get_populations(h, Lx: int, Ly: int, out=None):
@@ -602,6 +620,12 @@ class Lattice:
 
     def raw_sums(self):
         return flb_raw_sums(self.h)
+
+    def set_structure_sampling(self, warmup, every):
+        flb_set_structure_sampling(self.h, warmup, every)
+
+    def structure_factors(self):
+        return flb_structure_factors(self.h, self.p.Lx, self.p.Ly)
 
     def conservation(self):
         return flb_conservation(self.h)

@@ -1,0 +1,153 @@
+"""Static structure factors S_k(rho), S_k(j_x), R_k(j_x, j_y) (Eqs. sfactorr,
+sfactoru, rcorrelator) sampled on the GPU, against the FP64 oracle.
+
+* FP64 lattices (FP64 transform): whole runs against oracle.StructureRun, on
+  sides that take the fused power-of-two path, the direct transform, and the
+  general path with one side of each kind;
+  relative 1e-9 of the largest mode (the trajectories agree to 1e-12 of the
+  populations, the transforms to rounding).
+* FP32 and FP16-store lattices (FP32 transform): every step's sample against
+  the oracle's transform of the lattice's own state (read back in FP64), so
+  both sides see the same fields; 2e-5 of the largest mode (FP32 butterflies,
+  log2 L rounding steps on each axis).
+* the full 4096 x 4096 FP32 lattice: one sample at 24 wavevectors against the
+  oracle's transform of those k one by one, plus Parseval over all k.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1204_6734_gb300 import flb, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    flb.load()
+
+
+def lattice_params(Lx, Ly, basis, precision, ux0=0.1, uy0=-0.05, kT=1e-3, seed=7):
+    return inputs.LatticeParams(Lx, Ly, 1.0, ux0, uy0, kT, inputs.omega_groups(1.2, 0.8, 1.5), basis,
+                                precision, seed=seed)
+
+
+def perturbed(p, seed):
+    f0 = oracle.init_equilibrium(p)
+    return f0 * (1 + 0.02 * inputs.perturbation(f0.shape, seed=seed))
+
+
+@pytest.mark.parametrize("shape,basis", [((32, 16), "local"), ((2, 64), "standard"), ((21, 21), "local"),
+                                         ((24, 9), "standard"), ((16, 3), "local"), ((7, 32), "lut"),
+                                         ((1, 8), "local")])
+def test_fp64_run_against_oracle(shape, basis):
+    Lx, Ly = shape
+    p = lattice_params(Lx, Ly, basis, "fp64", seed=11 + Lx)
+    f_init = perturbed(p, seed=Lx * 7 + Ly)
+    ref = oracle.StructureRun(p, f=f_init, warmup=3, every=4).step(50)
+    Sr0, Sx0, R0 = ref.factors()
+    with flb.Lattice(p) as lat:
+        lat.set_populations(f_init)
+        lat.set_structure_sampling(3, 4)
+        lat.step(50)
+        Sr, Sx, R, n = lat.structure_factors()
+    assert n == ref.nsamp == 12
+    for got, want in ((Sr, Sr0), (Sx, Sx0), (R, R0)):
+        assert np.abs(got - want).max() < 1e-9 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("precision,shape", [("fp32", (64, 32)), ("fp32", (512, 256)), ("fp32", (40, 24)),
+                                             ("fp16dev", (32, 48)), ("fp16dev", (128, 64))])
+def test_reduced_precision_samples_of_its_own_state(precision, shape):
+    Lx, Ly = shape
+    p = lattice_params(Lx, Ly, "local", precision, kT=1e-4, seed=3)
+    acc = [np.zeros((Ly, Lx)), np.zeros((Ly, Lx)), np.zeros((Ly, Lx), dtype=complex)]
+    with flb.Lattice(p) as lat:
+        lat.step(20)
+        lat.set_structure_sampling(20, 1)
+        for _ in range(6):
+            f = lat.populations()
+            for a, s in zip(acc, oracle.structure_sample(f, p)):
+                a += s
+            lat.step(1)
+        Sr, Sx, R, n = lat.structure_factors()
+    assert n == 6
+    for got, want in zip((Sr, Sx, R), acc):
+        want = want / (6 * p.rho0)
+        assert np.abs(got - want).max() < 2e-5 * np.abs(want).max()
+
+
+def test_schedule_reset_and_errors():
+    p = lattice_params(16, 16, "local", "fp64")
+    with flb.Lattice(p) as lat:
+        with pytest.raises(flb.FlbError) as e:
+            lat.structure_factors()
+        assert e.value.code == flb.ERR_STATE
+        lat.set_structure_sampling(5, 3)
+        lat.step(20)                      # t = 5, 8, 11, 14, 17
+        assert lat.structure_factors()[3] == 5
+        lat.set_structure_sampling(0, 0)  # off, sums cleared
+        lat.step(5)
+        with pytest.raises(flb.FlbError):
+            lat.structure_factors()
+        lat.set_structure_sampling(0, 1)  # the schedule counts from t = 0
+        lat.step(2)                       # t = 25, 26
+        assert lat.structure_factors()[3] == 2
+    # an FP64 row of 16384 complex values does not fit one CTA's shared memory
+    with flb.Lattice(lattice_params(16384, 4, "local", "fp64")) as lat:
+        with pytest.raises(flb.FlbError) as e:
+            lat.set_structure_sampling(0, 1)
+        assert e.value.code == flb.ERR_ARG
+
+
+def test_ideal_gas_at_rest_is_flat_in_k():
+    """S_k(rho) -> N kT, S_k(j_x) -> N kT / 3 at every k != 0 (256 x 256,
+    FP32, 400 samples): the mean over k within 1 %. R_k fluctuates about 0
+    with the slow decay of the small-k shear modes; its mean over k, the
+    site average of dj_x dj_y, is zero to 1 %."""
+    kT = 1e-4
+    p = inputs.LatticeParams(256, 256, 1.0, 0.0, 0.0, kT, inputs.omega_groups(1.0, 1.0, 1.0), "local",
+                             "fp32", seed=23)
+    with flb.Lattice(p) as lat:
+        lat.set_structure_sampling(200, 5)
+        lat.step(200 + 5 * 400)
+        Sr, Sx, R, n = lat.structure_factors()
+    N = p.Lx * p.Ly
+    mask = np.ones_like(Sr, dtype=bool)
+    mask[0, 0] = False
+    assert n == 400
+    assert abs(Sr[mask].mean() / (N * kT) - 1) < 0.01
+    assert abs(Sx[mask].mean() / (N * kT / 3) - 1) < 0.01
+    assert np.abs(R[mask]).mean() < 0.1 * N * kT / 3
+    assert abs(R[mask].mean()) < 0.01 * N * kT / 3
+
+
+@pytest.mark.slow
+def test_full_size_sampled_wavevectors():
+    Lx = Ly = 4096
+    p = lattice_params(Lx, Ly, "local", "fp32", ux0=0.1, uy0=0.0, kT=1e-4, seed=5)
+    with flb.Lattice(p) as lat:
+        lat.step(30)
+        lat.set_structure_sampling(30, 1)
+        f = lat.populations()
+        lat.step(1)
+        Sr, Sx, R, n = lat.structure_factors()
+    assert n == 1
+    dr, djx, djy = oracle.hydro_fields(f, p)
+    del f
+    rng = np.random.Generator(np.random.PCG64(2))
+    ks = [(0, 1), (1, 0), (Ly // 2, Lx // 2), (Ly - 1, 3)] + [tuple(k) for k in rng.integers(0, 4096, (20, 2))]
+    scale = np.abs(Sr).mean()
+    for my, mx in ks:
+        wx = np.exp(-2j * np.pi * mx * np.arange(Lx) / Lx)
+        wy = np.exp(-2j * np.pi * my * np.arange(Ly) / Ly)
+        a, b, c = (wy @ (g @ wx) for g in (dr, djx, djy))
+        assert abs(Sr[my, mx] - abs(a) ** 2 / p.rho0) < 1e-4 * scale
+        assert abs(Sx[my, mx] - abs(b) ** 2 / p.rho0) < 1e-4 * np.abs(Sx).mean()
+        assert abs(R[my, mx] - b * np.conj(c) / p.rho0) < 1e-4 * np.abs(Sx).mean()
+    N = Lx * Ly
+    assert Sr.sum() == pytest.approx(N * (dr ** 2).sum() / p.rho0, rel=1e-5)
+    assert Sx.sum() == pytest.approx(N * (djx ** 2).sum() / p.rho0, rel=1e-5)
