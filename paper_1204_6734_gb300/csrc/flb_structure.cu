@@ -7,20 +7,20 @@
 // moments are rho - rho0 and j - rho0 u0 exactly (c has moments rho0, rho0 u0).
 //
 // Two paths compute the transform, FP64 for FP64 lattices, FP32 otherwise:
-//  * both sides powers of two (the fast path, two launches): one CTA per pair
-//    of rows forms the fields from the pulled populations and transforms
-//    them along x as one complex sequence per field (row y in the real part,
-//    row y+1 in the imaginary part), then splits the two rows' spectra by
-//    Hermitian symmetry and keeps m_x = 0..Lx/2; one CTA per column of that
-//    half spectrum transforms along y and adds the three products to the
-//    half-plane sums. The other half follows from S(-k) = S(k),
-//    R(-k) = conj R(k) (real fields), applied when the sums are read.
+//  * both sides powers of two up to 4096 (the fast path, two launches): one
+//    CTA per pair of rows forms the fields from the pulled populations and
+//    transforms them along x as one complex sequence per field (row y in the
+//    real part, row y+1 in the imaginary part), then splits the two rows'
+//    spectra by Hermitian symmetry and keeps m_x = 0..Lx/2, written
+//    column-major; one CTA per column of that half spectrum transforms along
+//    y and adds the three products to the half-plane sums. The other half
+//    follows from S(-k) = S(k), R(-k) = conj R(k) (real fields), applied when
+//    the sums are read.
 //  * other sides: fields, row transforms, column transforms and the sums as
 //    separate launches over the full plane, with a direct O(L^2) transform
 //    for a side that is not a power of two.
-// Each radix-2 transform runs in shared memory, input in bit-reversed order,
-// with one padding element every 2^ps elements so that the bit-reversed
-// scatter does not put a warp's 32 elements on one bank.
+// The power-of-two transforms are in-place Stockham passes in shared memory
+// (radix 8 or 16 in registers, natural order in and out).
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -92,128 +92,282 @@ __host__ __device__ __forceinline__ int log2i(int n) {
     return l;
 }
 
-__device__ __forceinline__ int bitrev(int v, int bits) { return (int)(__brev((unsigned)v) >> (32 - bits)); }
+// Radix-R DFT of v[0..R-1] in registers (R = 2, 4, 8, 16), in place:
+// v[k] <- sum_n v[n] exp(-2 pi i n k / R), as log2 R radix-2 stages on
+// bit-reversed input; the twiddles are roots of unity of order 16, known
+// constants, and the ones equal to 1 and -i cost no multiply.
+__host__ __device__ constexpr double cos16(int e) {
+    // cos(2 pi e / 16) for any integer e
+    e &= 15;
+    return e == 0 ? 1.0 : e == 1 || e == 15 ? 0.92387953251128675613 : e == 2 || e == 14 ? 0.70710678118654752440
+         : e == 3 || e == 13 ? 0.38268343236508977173 : e == 4 || e == 12 ? 0.0
+         : e == 5 || e == 11 ? -0.38268343236508977173 : e == 6 || e == 10 ? -0.70710678118654752440
+         : e == 7 || e == 9 ? -0.92387953251128675613 : -1.0;
+}
 
-__device__ __forceinline__ int pad(int i, int ps) { return i + (i >> ps); }
+template <int R>
+__host__ __device__ constexpr int rev_bits(int i) {
+    int r = 0;
+    for (int b = 1; b < R; b <<= 1) r = (r << 1) | ((i & b) ? 1 : 0);
+    return r;
+}
 
-// In-place radix-2 decimation-in-time transform of `count` sequences of
-// length 2^bits in shared memory, sequence q at s + q * seq, element i at
-// pad(i); input in bit-reversed order, output in natural order.
-// tw[m] = exp(-2 pi i m / L), m < L / 2.
-template <class R>
-__device__ __forceinline__ void fft_pow2(Cx<R>* s, int bits, int count, int seq, int ps,
-                                         const Cx<R>* __restrict__ tw) {
-    const int hb = bits - 1;
-    const int nb = count << hb;
-    for (int lh = 0; lh < bits; ++lh) {
-        const int half = 1 << lh;
-        for (int j = threadIdx.x; j < nb; j += blockDim.x) {
-            const int q = j >> hb, b = j & ((1 << hb) - 1);
-            const int pos = b & (half - 1);
-            const int i1 = ((b >> lh) << (lh + 1)) + pos, i2 = i1 + half;
-            Cx<R>* x = s + q * seq;
-            const Cx<R> w = tw[pos << (hb - lh)];
-            const Cx<R> t = cmul(w, x[pad(i2, ps)]);
-            const Cx<R> u = x[pad(i1, ps)];
-            x[pad(i1, ps)] = {u.re + t.re, u.im + t.im};
-            x[pad(i2, ps)] = {u.re - t.re, u.im - t.im};
+template <int R, class RT>
+__device__ __forceinline__ void dft_reg(Cx<RT>* v) {
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        const int j = rev_bits<R>(i);
+        if (i < j) {
+            const Cx<RT> t = v[i];
+            v[i] = v[j];
+            v[j] = t;
+        }
+    }
+#pragma unroll
+    for (int h = 1; h < R; h <<= 1) {
+#pragma unroll
+        for (int g = 0; g < R; g += 2 * h) {
+#pragma unroll
+            for (int p = 0; p < h; ++p) {
+                const int e = p * (8 / h);   // w = exp(-2 pi i p / (2h)) = exp(-2 pi i e / 16)
+                const Cx<RT> b = v[g + p + h];
+                Cx<RT> t;
+                if (e == 0) {
+                    t = b;
+                } else if (e == 4) {
+                    t = {b.im, -b.re};
+                } else {
+                    const RT c = (RT)cos16(e), sn = (RT)cos16(e - 4);   // sin(2 pi e / 16)
+                    t = {b.re * c + b.im * sn, b.im * c - b.re * sn};
+                }
+                const Cx<RT> a = v[g + p];
+                v[g + p] = {a.re + t.re, a.im + t.im};
+                v[g + p + h] = {a.re - t.re, a.im - t.im};
+            }
+        }
+    }
+}
+
+// Shared-memory position of element i of a sequence transformed with E
+// elements per thread and pass: one padding element every E, so that the
+// stride-R writes of the first pass spread over the banks.
+template <int E>
+__device__ __forceinline__ int spos(int i) {
+    return i + (i >> (E == 16 ? 4 : 3));
+}
+
+template <int E>
+__host__ __device__ constexpr int padded_len(int L) {
+    return L + (L >> (E == 16 ? 4 : 3)) + 1;
+}
+
+// One Stockham pass of radix R (the autosort formulation of Govindaraju et
+// al., SC'08) over `count` sequences of length L = 2^lgL, sequence q at
+// s + q * seq: sub-transforms of size Ns = 2^lgNs become size Ns R. Butterfly
+// j of a sequence reads elements j + r L/R, applies the twiddles
+// exp(-2 pi i r (j mod Ns) / (Ns R)) from the table T[m] = exp(-2 pi i m / L),
+// transforms them in registers and writes them to (j div Ns) Ns R +
+// (j mod Ns) + r Ns. In place: a round of whole sequences is read into
+// registers, the block synchronises, then writes. blockDim.x must be a
+// multiple of the threads per sequence, L / min(E, L).
+template <int E, int R, class RT>
+__device__ __forceinline__ void stockham_pass(Cx<RT>* s, int lgL, int lgNs, int count, int seq,
+                                              const Cx<RT>* __restrict__ T) {
+    constexpr int lgR = R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : 4;
+    const int L = 1 << lgL;
+    const int per = min(E, L) / R;           // butterflies per thread
+    const int nj = L >> lgR;                 // butterflies per sequence
+    const int tps = nj / per;                // threads per sequence
+    const int spr = blockDim.x / tps;        // sequences per round
+    const int Ns = 1 << lgNs;
+    const int tsh = lgL - lgNs - lgR;        // twiddle index scale L / (Ns R)
+    constexpr int PMAX = E / R;
+    for (int q0 = 0; q0 < count; q0 += spr) {
+        const int q = q0 + (int)threadIdx.x / tps;
+        const int t = (int)threadIdx.x % tps;
+        const bool active = q < count;
+        Cx<RT>* x = s + q * seq;
+        Cx<RT> v[PMAX][R];
+        if (active) {
+#pragma unroll
+            for (int b = 0; b < PMAX; ++b) {
+                if (b >= per) break;
+                const int j = t + b * tps, k = j & (Ns - 1);
+#pragma unroll
+                for (int r = 0; r < R; ++r) v[b][r] = x[spos<E>(j + r * nj)];
+                if (lgNs > 0) {
+                    // w_r = exp(-2 pi i r k / (Ns R)): loaded for r a power of
+                    // two, else the product w_hi w_(r - hi), hi the largest
+                    // power of two below r (at most three roundings deep)
+                    Cx<RT> w[R];
+#pragma unroll
+                    for (int r = 1; r < R; ++r) {
+                        const int hi = r >= 8 ? 8 : r >= 4 ? 4 : r >= 2 ? 2 : 1;
+                        w[r] = hi == r ? T[(r * k) << tsh] : cmul(w[hi], w[r - hi]);
+                        v[b][r] = cmul(v[b][r], w[r]);
+                    }
+                }
+                dft_reg<R>(v[b]);
+            }
+        }
+        __syncthreads();
+        if (active) {
+#pragma unroll
+            for (int b = 0; b < PMAX; ++b) {
+                if (b >= per) break;
+                const int j = t + b * tps, k = j & (Ns - 1);
+                const int d = ((j >> lgNs) << (lgNs + lgR)) + k;
+#pragma unroll
+                for (int r = 0; r < R; ++r) x[spos<E>(d + r * Ns)] = v[b][r];
+            }
         }
         __syncthreads();
     }
 }
 
+// Forward transform of `count` sequences of length 2^lgL in shared memory
+// (natural order in and out, element i at spos<E>(i)): passes of radix E
+// (8 or 16), then one of the remainder.
+template <int E, class RT>
+__device__ __forceinline__ void fft_seqs(Cx<RT>* s, int lgL, int count, int seq,
+                                         const Cx<RT>* __restrict__ T) {
+    constexpr int lgE = E == 16 ? 4 : 3;
+    int lgNs = 0;
+    for (; lgNs + lgE <= lgL; lgNs += lgE) stockham_pass<E, E, RT>(s, lgL, lgNs, count, seq, T);
+    switch (lgL - lgNs) {
+        case 1: stockham_pass<E, 2, RT>(s, lgL, lgNs, count, seq, T); break;
+        case 2: stockham_pass<E, 4, RT>(s, lgL, lgNs, count, seq, T); break;
+        case 3: stockham_pass<E, 8, RT>(s, lgL, lgNs, count, seq, T); break;
+        default: break;
+    }
+}
+
+// Elements per thread and pass: 8 in the fused kernels (two 512-thread CTAs
+// per SM at 64 registers, no spills); in the general line transform 16 in
+// FP32 and 8 in FP64 (lines up to 16384 and 8192 in 1024 threads).
+constexpr int kEfast = 8;
+template <class R>
+struct Elines {
+    static constexpr int E = sizeof(R) == 4 ? 16 : 8;
+};
+
 constexpr int kThreads = 512;
 
 // ---- fast path: both sides powers of two ----------------------------------
 
-// One CTA per row pair (y0, y0 + 1): H[f][y][m], m = 0..Lx/2 (row pitch Hx),
-// the x-transform of field f (0: drho, 1: dj_x, 2: dj_y) of row y.
+// Two adjacent complex values as one vector store (16 B in FP32, 2 x 16 B in
+// FP64); p is aligned to twice the element size.
+__device__ __forceinline__ void store_pair(Cx<float>* p, Cx<float> a, Cx<float> b) {
+    *reinterpret_cast<float4*>(p) = make_float4(a.re, a.im, b.re, b.im);
+}
+__device__ __forceinline__ void store_pair(Cx<double>* p, Cx<double> a, Cx<double> b) {
+    reinterpret_cast<double2*>(p)[0] = make_double2(a.re, a.im);
+    reinterpret_cast<double2*>(p)[1] = make_double2(b.re, b.im);
+}
+
+// One CTA per row pair (y0, y0 + 1): H[f][m][y], m = 0..Lx/2 (Hx columns of
+// Ly values), the x-transform of field f (0: drho, 1: dj_x, 2: dj_y) of row y,
+// stored column-major so that the y-transforms read contiguous columns.
 template <class T, class R>
-__global__ void __launch_bounds__(kThreads) rows_pair_kernel(const T* __restrict__ buf, Geometry geo,
-                                                             DevCodec codec, Ref9<R> c, int bits,
-                                                             int ps, const Cx<R>* __restrict__ tw,
+__global__ void __launch_bounds__(kThreads, 2) rows_pair_kernel(const T* __restrict__ buf, Geometry geo,
+                                                             DevCodec codec, Ref9<R> c, int lgLx,
+                                                             const Cx<R>* __restrict__ tw,
                                                              Cx<R>* __restrict__ H, int Hx) {
     extern __shared__ __align__(16) unsigned char raw[];
     Cx<R>* s = reinterpret_cast<Cx<R>*>(raw);
     const int Lx = geo.Lx, Ly = geo.Ly;
-    const int seq = pad(Lx, ps) + 1;
+    const int seq = padded_len<kEfast>(Lx);
     const int y0 = 2 * blockIdx.x, y1 = y0 + 1;
     for (int x = threadIdx.x; x < Lx; x += blockDim.x) {
         R r0, a0, b0, r1, a1, b1;
         node_fields(buf, geo, codec, c, x, y0, r0, a0, b0);
         node_fields(buf, geo, codec, c, x, y1, r1, a1, b1);
-        const int p = pad(bitrev(x, bits), ps);
+        const int p = spos<kEfast>(x);
         s[p] = {r0, r1};
         s[seq + p] = {a0, a1};
         s[2 * seq + p] = {b0, b1};
     }
     __syncthreads();
-    fft_pow2(s, bits, 3, seq, ps, tw);
+    fft_seqs<kEfast>(s, lgLx, 3, seq, tw);
     // z = a + i b with a, b real: A(m) = (Z(m) + conj Z(-m)) / 2,
     // B(m) = (Z(m) - conj Z(-m)) / (2i)
     for (int f = 0; f < 3; ++f) {
         const Cx<R>* z = s + f * seq;
-        Cx<R>* out0 = H + ((size_t)f * Ly + y0) * Hx;
-        Cx<R>* out1 = out0 + Hx;
+        Cx<R>* out = H + (size_t)f * Hx * Ly + y0;
         for (int m = threadIdx.x; m < Hx; m += blockDim.x) {
-            const Cx<R> u = z[pad(m, ps)], w = z[pad((Lx - m) & (Lx - 1), ps)];
-            out0[m] = {R(0.5) * (u.re + w.re), R(0.5) * (u.im - w.im)};
-            out1[m] = {R(0.5) * (u.im + w.im), R(0.5) * (w.re - u.re)};
+            const Cx<R> u = z[spos<kEfast>(m)], w = z[spos<kEfast>((Lx - m) & (Lx - 1))];
+            store_pair(out + (size_t)m * Ly, Cx<R>{R(0.5) * (u.re + w.re), R(0.5) * (u.im - w.im)},
+                       Cx<R>{R(0.5) * (u.im + w.im), R(0.5) * (w.re - u.re)});
         }
     }
 }
 
-// One CTA per block of C columns (C a power of two) of the half spectrum: the
+// One CTA per block of C = 2^lc columns of the half spectrum H[f][m][y]: the
 // y-transform of each, then acc[q][m_x][m_y] += |drho|^2 (q = 0), |dj_x|^2
 // (1), Re and Im of dj_x conj(dj_y) (2, 3); acc[q] is Hx x Ly, m_y fastest.
 template <class R>
-__global__ void __launch_bounds__(kThreads) cols_acc_kernel(const Cx<R>* __restrict__ H, int Ly,
-                                                            int Hx, int bits, int ps, int lc,
+__global__ void __launch_bounds__(kThreads, 2) cols_acc_kernel(const Cx<R>* __restrict__ H, int lgLy,
+                                                            int Hx, int lc,
                                                             const Cx<R>* __restrict__ tw,
                                                             double* __restrict__ acc) {
     extern __shared__ __align__(16) unsigned char raw[];
     Cx<R>* s = reinterpret_cast<Cx<R>*>(raw);
-    const int C = 1 << lc;
-    const int seq = pad(Ly, ps) + 1;
+    const int Ly = 1 << lgLy, C = 1 << lc;
+    const int seq = padded_len<kEfast>(Ly);
     const int c0 = blockIdx.x * C;
-    constexpr int kBatch = 4;
-    for (int f = 0; f < 3; ++f) {
-        const Cx<R>* src = H + (size_t)f * Ly * Hx + c0;
-        Cx<R>* dst = s + f * C * seq;
-        // kBatch independent loads in flight per thread before the stores
-        for (int j0 = threadIdx.x; j0 < (Ly << lc); j0 += kBatch * blockDim.x) {
-            Cx<R> v[kBatch];
+    const int n = Ly << lc;
+    const int lgn = lgLy + lc;
+    const size_t Q = (size_t)Hx * Ly;
+    // kLoad independent loads in flight per thread before the stores
+    constexpr int kLoad = 8;
+    for (int j0 = threadIdx.x; j0 < 3 * n; j0 += kLoad * blockDim.x) {
+        Cx<R> v[kLoad];
 #pragma unroll
-            for (int u = 0; u < kBatch; ++u) {
-                const int j = j0 + u * blockDim.x;
-                const int y = j >> lc, cc = j & (C - 1);
-                v[u] = (j < (Ly << lc) && c0 + cc < Hx) ? src[(size_t)y * Hx + cc] : Cx<R>{R(0), R(0)};
-            }
+        for (int u = 0; u < kLoad; ++u) {
+            const int j = j0 + u * blockDim.x;
+            const int f = j >> lgn, cc = (j >> lgLy) & (C - 1), y = j & (Ly - 1);
+            v[u] = (j < 3 * n && c0 + cc < Hx) ? H[(size_t)f * Q + (size_t)(c0 + cc) * Ly + y]
+                                               : Cx<R>{R(0), R(0)};
+        }
 #pragma unroll
-            for (int u = 0; u < kBatch; ++u) {
-                const int j = j0 + u * blockDim.x;
-                if (j < (Ly << lc)) {
-                    const int y = j >> lc, cc = j & (C - 1);
-                    dst[cc * seq + pad(bitrev(y, bits), ps)] = v[u];
-                }
-            }
+        for (int u = 0; u < kLoad; ++u) {
+            const int j = j0 + u * blockDim.x;
+            const int f = j >> lgn, cc = (j >> lgLy) & (C - 1), y = j & (Ly - 1);
+            if (j < 3 * n) s[(f * C + cc) * seq + spos<kEfast>(y)] = v[u];
         }
     }
     __syncthreads();
-    fft_pow2(s, bits, 3 * C, seq, ps, tw);
-    for (int j = threadIdx.x; j < (Ly << lc); j += blockDim.x) {
-        const int cc = j >> bits, m = j & (Ly - 1);
-        const int col = c0 + cc;
-        if (col >= Hx) continue;
-        const Cx<R> a = s[cc * seq + pad(m, ps)];
-        const Cx<R> b = s[(C + cc) * seq + pad(m, ps)];
-        const Cx<R> d = s[(2 * C + cc) * seq + pad(m, ps)];
-        const size_t k = (size_t)col * Ly + m, Q = (size_t)Hx * Ly;
-        const double ar = a.re, ai = a.im, br = b.re, bi = b.im, dr = d.re, di = d.im;
-        acc[k] += ar * ar + ai * ai;
-        acc[Q + k] += br * br + bi * bi;
-        acc[2 * Q + k] += br * dr + bi * di;
-        acc[3 * Q + k] += bi * dr - br * di;
+    fft_seqs<kEfast>(s, lgLy, 3 * C, seq, tw);
+    // kAcc sites per thread at a time: their 4 kAcc sums are read before any
+    // is written back
+    constexpr int kAcc = 2;
+    for (int j0 = threadIdx.x; j0 < n; j0 += kAcc * blockDim.x) {
+        double old[kAcc][4];
+#pragma unroll
+        for (int u = 0; u < kAcc; ++u) {
+            const int j = j0 + u * blockDim.x;
+            const int col = c0 + (j >> lgLy);
+            const size_t k = (size_t)col * Ly + (j & (Ly - 1));
+            const bool ok = j < n && col < Hx;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) old[u][q] = ok ? acc[q * Q + k] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kAcc; ++u) {
+            const int j = j0 + u * blockDim.x;
+            const int cc = j >> lgLy, m = j & (Ly - 1);
+            const int col = c0 + cc;
+            if (j >= n || col >= Hx) continue;
+            const Cx<R> a = s[cc * seq + spos<kEfast>(m)];
+            const Cx<R> b = s[(C + cc) * seq + spos<kEfast>(m)];
+            const Cx<R> d = s[(2 * C + cc) * seq + spos<kEfast>(m)];
+            const size_t k = (size_t)col * Ly + m;
+            const double ar = a.re, ai = a.im, br = b.re, bi = b.im, dr = d.re, di = d.im;
+            acc[k] = old[u][0] + (ar * ar + ai * ai);
+            acc[Q + k] = old[u][1] + (br * br + bi * bi);
+            acc[2 * Q + k] = old[u][2] + (br * dr + bi * di);
+            acc[3 * Q + k] = old[u][3] + (bi * dr - br * di);
+        }
     }
 }
 
@@ -233,30 +387,20 @@ __global__ void fields_kernel(const T* __restrict__ buf, Geometry geo, DevCodec 
     }
 }
 
-// One CTA per row of each field (blockIdx.y): in-place radix-2 transform.
+// In-place transform of line blockIdx.x of each field (blockIdx.y) with a
+// power-of-two length 2^lgL: rows (elements `step` = 1 apart, lines Lx apart)
+// or columns (elements Lx apart, lines 1 apart).
 template <class R>
-__global__ void fft_rows_kernel(Cx<R>* F, int Lx, int Ly, int ps, const Cx<R>* tw) {
+__global__ void __launch_bounds__(1024) fft_lines_kernel(Cx<R>* F, int lgL, size_t step, size_t line,
+                                                         size_t field, const Cx<R>* __restrict__ tw) {
     extern __shared__ __align__(16) unsigned char raw[];
     Cx<R>* s = reinterpret_cast<Cx<R>*>(raw);
-    Cx<R>* row = F + ((size_t)blockIdx.y * Ly + blockIdx.x) * Lx;
-    const int bits = log2i(Lx);
-    for (int i = threadIdx.x; i < Lx; i += blockDim.x) s[pad(bitrev(i, bits), ps)] = row[i];
+    Cx<R>* p = F + blockIdx.y * field + blockIdx.x * line;
+    const int L = 1 << lgL;
+    for (int i = threadIdx.x; i < L; i += blockDim.x) s[spos<Elines<R>::E>(i)] = p[i * step];
     __syncthreads();
-    fft_pow2(s, bits, 1, 0, ps, tw);
-    for (int i = threadIdx.x; i < Lx; i += blockDim.x) row[i] = s[pad(i, ps)];
-}
-
-// One CTA per column of each field: in-place radix-2 transform.
-template <class R>
-__global__ void fft_cols_kernel(Cx<R>* F, int Lx, int Ly, int ps, const Cx<R>* tw) {
-    extern __shared__ __align__(16) unsigned char raw[];
-    Cx<R>* s = reinterpret_cast<Cx<R>*>(raw);
-    Cx<R>* col = F + (size_t)blockIdx.y * Ly * Lx + blockIdx.x;
-    const int bits = log2i(Ly);
-    for (int y = threadIdx.x; y < Ly; y += blockDim.x) s[pad(bitrev(y, bits), ps)] = col[(size_t)y * Lx];
-    __syncthreads();
-    fft_pow2(s, bits, 1, 0, ps, tw);
-    for (int y = threadIdx.x; y < Ly; y += blockDim.x) col[(size_t)y * Lx] = s[pad(y, ps)];
+    fft_seqs<Elines<R>::E>(s, lgL, 1, 0, tw);
+    for (int i = threadIdx.x; i < L; i += blockDim.x) p[i * step] = s[spos<Elines<R>::E>(i)];
 }
 
 // Direct transform of one row of each field (any L):
@@ -318,15 +462,11 @@ __global__ void accumulate_kernel(const Cx<R>* A, const Cx<R>* B, const Cx<R>* D
 
 bool pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
-// Padding shift for a transform of length L: one element every L / 32, so
-// that 32 consecutive bit-reversed indices land on distinct banks; none for
-// L < 32 (those indices are already distinct modulo 32).
-int pad_shift(int L) {
-    const int b = log2i(L);
-    return b >= 5 ? b - 5 : b;
+// Threads of a transform CTA: at least the threads one sequence takes.
+template <class R>
+int fft_threads(int L) {
+    return std::max(kThreads, L / Elines<R>::E);
 }
-
-size_t padded(int L, int ps) { return (size_t)L + ((size_t)L >> ps) + 1; }
 
 constexpr size_t kGeneralSmem = 160 * 1024;
 
@@ -350,16 +490,14 @@ namespace {
 
 template <class R>
 cudaError_t upload_twiddles(int L, void** out) {
-    // power of two: exp(-2 pi i m / L) for m < L/2; otherwise all m < L
-    const int n = pow2(L) ? std::max(1, L / 2) : L;
-    std::vector<Cx<R>> h(n);
-    for (int m = 0; m < n; ++m) {
+    // exp(-2 pi i m / L), m < L
+    std::vector<Cx<R>> h(L);
+    for (int m = 0; m < L; ++m) {
         const double a = -2.0 * M_PI * (double)m / (double)L;
         h[m] = {(R)std::cos(a), (R)std::sin(a)};
     }
-    cudaError_t ce = cudaMalloc(out, sizeof(Cx<R>) * n);
-    if (ce == cudaSuccess)
-        ce = cudaMemcpy(*out, h.data(), sizeof(Cx<R>) * n, cudaMemcpyHostToDevice);
+    cudaError_t ce = cudaMalloc(out, sizeof(Cx<R>) * L);
+    if (ce == cudaSuccess) ce = cudaMemcpy(*out, h.data(), sizeof(Cx<R>) * L, cudaMemcpyHostToDevice);
     return ce;
 }
 
@@ -367,12 +505,11 @@ template <class T, class R>
 cudaError_t sample_fast(StructSampler* s, const T* buf, const Geometry& geo, const DevCodec& codec,
                         const Ref9<R>& c, cudaStream_t st) {
     Cx<R>* H = (Cx<R>*)s->fields;
-    const int bx = log2i(s->Lx), by = log2i(s->Ly);
     cudaError_t ce = cudaFuncSetAttribute(rows_pair_kernel<T, R>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem_rows);
     if (ce != cudaSuccess) return ce;
     rows_pair_kernel<T, R><<<s->Ly / 2, kThreads, s->smem_rows, st>>>(
-        buf, geo, codec, c, bx, pad_shift(s->Lx), (const Cx<R>*)s->twx, H, s->Hx);
+        buf, geo, codec, c, log2i(s->Lx), (const Cx<R>*)s->twx, H, s->Hx);
     ce = cudaGetLastError();
     if (ce != cudaSuccess) return ce;
     ce = cudaFuncSetAttribute(cols_acc_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -380,8 +517,20 @@ cudaError_t sample_fast(StructSampler* s, const T* buf, const Geometry& geo, con
     if (ce != cudaSuccess) return ce;
     const int C = 1 << s->lc;
     cols_acc_kernel<R><<<(s->Hx + C - 1) / C, kThreads, s->smem_cols, st>>>(
-        H, s->Ly, s->Hx, by, pad_shift(s->Ly), s->lc, (const Cx<R>*)s->twy, s->acc);
+        H, log2i(s->Ly), s->Hx, s->lc, (const Cx<R>*)s->twy, s->acc);
     return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t fft_lines(Cx<R>* F, int L, size_t step, size_t line, int nlines, size_t field,
+                      const Cx<R>* tw, cudaStream_t st) {
+    const size_t sm = sizeof(Cx<R>) * padded_len<Elines<R>::E>(L);
+    cudaError_t ce = cudaFuncSetAttribute(fft_lines_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (ce == cudaSuccess) {
+        fft_lines_kernel<R><<<dim3(nlines, 3), fft_threads<R>(L), sm, st>>>(F, log2i(L), step, line, field, tw);
+        ce = cudaGetLastError();
+    }
+    return ce;
 }
 
 template <class T, class R>
@@ -396,29 +545,23 @@ cudaError_t sample_general(StructSampler* s, const T* buf, const Geometry& geo,
     cudaError_t ce = cudaGetLastError();
     if (ce == cudaSuccess && Lx > 1) {
         if (pow2(Lx)) {
-            const int ps = pad_shift(Lx);
-            const size_t sm = sizeof(Cx<R>) * padded(Lx, ps);
-            ce = cudaFuncSetAttribute(fft_rows_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            if (ce == cudaSuccess) fft_rows_kernel<R><<<dim3(Ly, 3), kThreads, sm, st>>>(F, Lx, Ly, ps, tx);
+            ce = fft_lines<R>(F, Lx, 1, Lx, Ly, N, tx, st);
         } else {
             const size_t sm = sizeof(Cx<R>) * Lx;
             ce = cudaFuncSetAttribute(dft_rows_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             if (ce == cudaSuccess) dft_rows_kernel<R><<<dim3(Ly, 3), 256, sm, st>>>(F, Lx, Ly, tx);
+            if (ce == cudaSuccess) ce = cudaGetLastError();
         }
-        if (ce == cudaSuccess) ce = cudaGetLastError();
     }
     if (ce == cudaSuccess && Ly > 1) {
         if (pow2(Ly)) {
-            const int ps = pad_shift(Ly);
-            const size_t sm = sizeof(Cx<R>) * padded(Ly, ps);
-            ce = cudaFuncSetAttribute(fft_cols_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            if (ce == cudaSuccess) fft_cols_kernel<R><<<dim3(Lx, 3), kThreads, sm, st>>>(F, Lx, Ly, ps, ty);
+            ce = fft_lines<R>(F, Ly, Lx, 1, Lx, N, ty, st);
         } else {
             const size_t sm = sizeof(Cx<R>) * Ly;
             ce = cudaFuncSetAttribute(dft_cols_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             if (ce == cudaSuccess) dft_cols_kernel<R><<<dim3(Lx, 3), 256, sm, st>>>(F, Lx, Ly, ty);
+            if (ce == cudaSuccess) ce = cudaGetLastError();
         }
-        if (ce == cudaSuccess) ce = cudaGetLastError();
     }
     if (ce == cudaSuccess) {
         accumulate_kernel<R><<<std::min(4096, (N + 255) / 256), 256, 0, st>>>(F, F + N, F + 2 * (size_t)N,
@@ -452,17 +595,23 @@ int structure_create(StructSampler** out, int Lx, int Ly, int rbytes) {
     s->Lx = Lx;
     s->Ly = Ly;
     s->rbytes = rbytes;
-    if (pow2(Lx) && pow2(Ly) && Lx >= 2 && Ly >= 2) {
-        s->smem_rows = 3 * cb * padded(Lx, pad_shift(Lx));
+    // fast path: one sequence's threads (L / E) fit one 512-thread CTA
+    if (pow2(Lx) && pow2(Ly) && Lx >= 2 && Ly >= 2 && Lx / kEfast <= kThreads && Ly / kEfast <= kThreads) {
+        s->smem_rows = 3 * cb * padded_len<kEfast>(Lx);
         // columns per CTA: the most that leave room for two CTAs per SM, else one
-        const size_t col = 3 * cb * padded(Ly, pad_shift(Ly));
+        const size_t col = 3 * cb * padded_len<kEfast>(Ly);
         s->lc = 0;
         while (s->lc < 2 && col << (s->lc + 1) <= (size_t)optin / 2) ++s->lc;
         s->smem_cols = col << s->lc;
         s->fast = s->smem_rows <= (size_t)optin && s->smem_cols <= (size_t)optin;
     }
     // the general path holds one row (column) of complex values per CTA
-    if (!s->fast && ((size_t)Lx * cb > kGeneralSmem || (size_t)Ly * cb > kGeneralSmem)) {
+    const auto fits = [&](int L) {
+        if (!pow2(L)) return (size_t)L * cb <= kGeneralSmem;
+        return rbytes == 4 ? L / Elines<float>::E <= 1024 && padded_len<Elines<float>::E>(L) * cb <= (size_t)optin
+                           : L / Elines<double>::E <= 1024 && padded_len<Elines<double>::E>(L) * cb <= (size_t)optin;
+    };
+    if (!s->fast && !(fits(Lx) && fits(Ly))) {
         delete s;
         return FLB_ERR_ARG;
     }
