@@ -72,6 +72,9 @@ def parse():
     ap.add_argument("--no-per-lattice", action="store_true",
                     help="skip the one-launch-per-lattice arm of the ensemble comparison")
     ap.add_argument("--graph-steps", type=int, default=25)
+    ap.add_argument("--no-structure", action="store_true",
+                    help="skip the structure-factor sampling measurement")
+    ap.add_argument("--structure-steps", type=int, default=100)
     return ap.parse_args()
 
 
@@ -174,6 +177,51 @@ def oracle_mlups(p, max_seconds=10.0, side=512):
     run.step(n)
     dt = time.perf_counter() - t0
     return side * side * n / dt / 1e6, f"{side}x{side} lattice, {n} steps (sampling on), same parameters", 1
+
+
+def bench_structure(args, p, stream, peak, peak_kind):
+    """Cost of one structure-factor sample (Eqs. sfactorr, sfactoru,
+    rcorrelator) on the bench lattice: steps with S_k sampled every step minus
+    steps without, per step. Algorithmic bytes of the power-of-two path per
+    node (FP32 transform): populations read (36) + half-spectrum write (12) in
+    the row kernel, half-spectrum read (12) + FP64 sums read and written (32)
+    in the column kernel."""
+    import torch
+
+    from paper_1204_6734_gb300 import flb
+
+    n = args.structure_steps
+    nodes = p.Lx * p.Ly
+    with flb.Lattice(p, stream=stream) as lat:
+        lat.set_sampling(0, args.sample_every)
+        lat.step(5)
+        lat.sync()
+
+        def timed():
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lat.step(n)
+            e1.record(stream)
+            lat.sync()
+            return e0.elapsed_time(e1) / n
+
+        base = timed()
+        lat.set_structure_sampling(0, 1)
+        lat.step(3)
+        lat.sync()
+        with_sk = timed()
+        ns = lat.structure_factors()[3]
+    per = with_sk - base
+    pow2 = p.Lx & (p.Lx - 1) == 0 and p.Ly & (p.Ly - 1) == 0 and max(p.Lx, p.Ly) <= 4096
+    out = {"ms_per_sample": per, "ms_per_step": base, "ms_per_step_sampled": with_sk,
+           "samples": ns, "path": "power-of-two (2 launches)" if pow2 else "general"}
+    if pow2 and p.precision == "fp32":
+        b = 92 * nodes
+        ach = b / (per * 1e-3) / 1e9
+        out["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                           "frac": ach / peak, "peak_kind": peak_kind, "algorithmic_bytes": b,
+                           "kernels": "rows_pair_kernel + cols_acc_kernel"}
+    return out
 
 
 def bench_batched(args, stream):
@@ -656,6 +704,10 @@ def main():
                  "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
                               "frac": ach / peak, "peak_kind": peak_kind}}
 
+    structure = None
+    if rank == 0 and world == 1 and not args.no_structure:
+        structure = bench_structure(args, p, stream, peak, peak_kind)
+
     batched = serving = None
     if rank == 0 and world == 1 and not args.no_batched and args.precision == "fp32":
         batched = bench_batched(args, stream)
@@ -687,6 +739,7 @@ def main():
             "mlups_roofline_frac": value / (peak * 1e9 / BYTES_PER_NODE[args.precision] / 1e6) / world,
             "n_samples": ns,
             "other_basis": other,
+            "structure_factors": structure,
             "batched": batched,
             "serving": serving,
         }
