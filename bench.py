@@ -56,7 +56,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched-ensemble comparison added to the JSON line")
     ap.add_argument("--batched-steps", type=int, default=200)
-    ap.add_argument("--workload", default="single", choices=["single", "ensemble", "serving", "precision", "sweep"],
+    ap.add_argument("--workload", default="single",
+                    choices=["single", "ensemble", "serving", "precision", "sweep", "sweep21"],
                     help="single: the 4096^2 lattice (with the ensemble comparison added); "
                          "ensemble: only the batched replica ensemble, as the main line")
     ap.add_argument("--replicas", type=int, default=256, help="replicas of the ensemble")
@@ -483,8 +484,7 @@ def run_sweep(args, rank, world, dist, dev):
     """--workload sweep: the u_x0 sweep of the 4096^2 lattice in both bases
     (--steps steps each, sampled every step after a tenth); the normalised
     moment variances <dM^a dM^a> / (kT rho0) - 1, measured in the run's own
-    basis at u0, fitted with l u_x0 + q u_x0^2 over |u_x0| <= 0.25 (the
-    paper's fit range) for every moment."""
+    basis at u0, and the quadratic coefficient q of each (fit_drift)."""
     import numpy as np
     import torch
 
@@ -507,15 +507,12 @@ def run_sweep(args, rank, world, dist, dev):
                 rows.append((u, dev_, np.diag(Cff) / (p.kT * feq_of(p))))
             us = np.array([r[0] for r in rows])
             D = np.array([r[1] for r in rows])
-            fit = us <= 0.25
-            A = np.stack([us[fit], us[fit] ** 2], axis=1)
-            coef, *_ = np.linalg.lstsq(A, D[fit], rcond=None)
+            q = fit_drift(us, D)
             res[basis] = {
                 "u_x0": [float(u) for u in us],
                 "moment_variance_minus_1": {MOMENT_NAMES[a]: [float(x) for x in D[:, a]] for a in range(9)},
                 "population_variance_over_kT_f0": [[float(x) for x in r[2]] for r in rows],
-                "fit_l": {MOMENT_NAMES[a]: float(coef[0, a]) for a in range(9)},
-                "fit_q": {MOMENT_NAMES[a]: float(coef[1, a]) for a in range(9)},
+                "fit_q": {MOMENT_NAMES[a]: float(q[a]) for a in range(9)},
                 "paper_q_21x21": PAPER_Q[basis],
             }
     if rank == 0:
@@ -527,6 +524,73 @@ def run_sweep(args, rank, world, dist, dev):
                                        f"sampled every step after {warm}",
                            "l2": "inputs larger than L2"},
                 "sweep": res, "clocks": clk.summary()}
+        print(json.dumps(line))
+
+
+def fit_drift(us, D):
+    """q of the least-squares fit l u + q u^2 over -0.25 <= u <= 0.25 (the
+    paper's range) of the diagonal variances D[point, a]: they are even in
+    u_x0 (x reflection of the lattice), so the points u >= 0 stand for their
+    mirror images, l = 0 and q = sum D u^2 / sum u^4."""
+    import numpy as np
+    us = np.asarray(us, dtype=float)
+    fit = us <= 0.25
+    D = np.asarray(D)[fit]
+    return (D * us[fit, None] ** 2).sum(axis=0) / (us[fit] ** 4).sum()
+
+
+def run_sweep21(args, rank, world, dist, dev):
+    """--workload sweep21: the u_x0 sweep on the paper's own 21 x 21 lattice.
+    --replicas independent copies per (u_x0, basis), all points of one basis in
+    one batch (one launch per step), --steps steps sampled every step after a
+    tenth; the moment variances of the pooled copies (flb_batch_correlations)
+    fitted as in the 4096^2 sweep. The table f-norm is not a batch basis; at
+    4096^2 it matches the local f-norm's q to 1 %."""
+    import numpy as np
+    import torch
+
+    from paper_1204_6734_gb300 import flb, inputs
+    stream = torch.cuda.Stream(device=dev)
+    warm = max(1, args.steps // 10)
+    R = args.replicas
+    res = {}
+    with ClockSampler(smi_id(dev)) as clk:
+        for basis in ("standard", "local"):
+            ps = [p for u in inputs.SWEEP_UX0 for p in inputs.small_sweep_replicas(u, basis, R)]
+            with flb.Batch(ps, stream=stream) as b:
+                b.set_sampling(warm, 1)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                b.step(args.steps)
+                e1.record(stream)
+                b.sync()
+                ms = e0.elapsed_time(e1)
+                rows = []
+                for iu, u in enumerate(inputs.SWEEP_UX0):
+                    slots = list(range(iu * R, (iu + 1) * R))
+                    Cff, CMM, mean, n = b.correlations(slots, "standard" if basis == "standard" else "local")
+                    p = ps[iu * R]
+                    rows.append((u, np.diag(CMM) / (p.kT * p.rho0) - 1.0, n))
+            us = [r[0] for r in rows]
+            D = np.array([r[1] for r in rows])
+            q = fit_drift(us, D)
+            nodes = sum(p.Lx * p.Ly for p in ps)
+            res[basis] = {
+                "u_x0": us, "node_samples_per_point": [int(r[2]) for r in rows],
+                "moment_variance_minus_1": {MOMENT_NAMES[a]: [float(x) for x in D[:, a]] for a in range(9)},
+                "fit_q": {MOMENT_NAMES[a]: float(q[a]) for a in range(9)},
+                "paper_q_21x21": PAPER_Q[basis],
+                "batch_ms_per_step": ms / args.steps, "mlups": nodes * args.steps / (ms * 1e-3) / 1e6,
+            }
+    if rank == 0:
+        line = {"metric": METRIC, "value": None, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": warm, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"u_x0 sweep {list(inputs.SWEEP_UX0)} on 21x21 lattices, {R} "
+                                       "independent copies per point pooled (kT=1e-4, shear 1.0, bulk 0.8, "
+                                       f"ghost 1.0), Hermite and f-norm, sampled every step after {warm}",
+                           "l2": "state fits L2 (small lattices)"},
+                "sweep21": res, "clocks": clk.summary()}
         print(json.dumps(line))
 
 
@@ -600,7 +664,7 @@ def main():
         if dist is not None:
             dist.barrier()
         run = {"ensemble": run_ensemble, "serving": run_serving, "precision": run_precision,
-               "sweep": run_sweep}
+               "sweep": run_sweep, "sweep21": run_sweep21}
         run[args.workload](args, rank, world, dist, dev)
         if dist is not None:
             dist.destroy_process_group()

@@ -327,6 +327,17 @@ int flb_batch_info(flb_batch b, int32_t* replicas, int64_t* tiles, size_t* pool_
  * (flb_raw_sums, flb_get_populations, flb_set_populations: 9 * Lx * Ly
  * doubles of that slot's lattice). Synchronous. */
 int flb_batch_raw_sums(flb_batch b, int32_t slot, double* S1, double* S2, int64_t* n_samples);
+
+/* Equal-time correlations pooled over the n replicas slots[0..n-1] (e.g. the
+ * same parameters with different seeds): their FP64 sums and sample counts
+ * are added, then finalised as flb_correlations does (Eqs. dfdef, efif0,
+ * dfidfj2dmadmb), the measurement basis at their common u0. The replicas
+ * must share rho0 and u0, since each one's sums are taken relative to
+ * f^0(rho0, u0). Synchronous. Errors: FLB_ERR_ARG (bad slot, rho0 or u0
+ * differ, measure_basis), FLB_ERR_STATE (no samples), a replica's recorded
+ * device error, FLB_ERR_OOM, FLB_ERR_CUDA. */
+int flb_batch_correlations(flb_batch b, int32_t n, const int32_t* slots, int32_t measure_basis,
+                           double* Cff, double* CMM, double* mean_dev, int64_t* n_samples);
 int flb_batch_get_populations(flb_batch b, int32_t slot, double* host_out);
 int flb_batch_set_populations(flb_batch b, int32_t slot, const double* host_in);
 

@@ -609,6 +609,36 @@ int flb_batch_raw_sums(flb_batch b, int32_t slot, double* S1, double* S2, int64_
     return FLB_OK;
 }
 
+int flb_batch_correlations(flb_batch b, int32_t n, const int32_t* slots, int32_t measure_basis,
+                           double* Cff, double* CMM, double* mean_dev, int64_t* n_samples) {
+    if (!b || n < 1 || !slots) return FLB_ERR_ARG;
+    for (int32_t q = 0; q < n; ++q) {
+        if (!slot_ok(b, slots[q])) return FLB_ERR_ARG;
+        const flb_params& a = b->slots[slots[0]].p;
+        const flb_params& c = b->slots[slots[q]].p;
+        if (c.rho0 != a.rho0 || c.ux0 != a.ux0 || c.uy0 != a.uy0) return FLB_ERR_ARG;
+    }
+    double pooled[kSums] = {0.0};
+    int64_t ns = 0;
+    for (int32_t q = 0; q < n; ++q) {
+        double acc[kSums];
+        cudaError_t ce = cudaMemcpyAsync(acc, b->acc + (size_t)slots[q] * kSums, sizeof(acc),
+                                         cudaMemcpyDeviceToHost, b->stream);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(b->stream);
+        if (ce != cudaSuccess) {
+            cudaGetLastError();
+            return FLB_ERR_CUDA;
+        }
+        const int rc = read_status(b, slots[q]);
+        if (rc) return rc;
+        for (int k = 0; k < kSums; ++k) pooled[k] += acc[k];
+        ns += b->slots[slots[q]].nsamp;
+    }
+    if (n_samples) *n_samples = ns;
+    const flb_params& p = b->slots[slots[0]].p;
+    return finalize_sums(pooled, ns, measure_basis, p.ux0, p.uy0, b->stream, Cff, CMM, mean_dev);
+}
+
 int flb_batch_get_populations(flb_batch b, int32_t slot, double* host_out) {
     if (!slot_ok(b, slot) || !host_out) return FLB_ERR_ARG;
     const BatchSlot& s = b->slots[slot];

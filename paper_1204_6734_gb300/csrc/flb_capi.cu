@@ -494,6 +494,40 @@ void lattice_forget(flb_lattice h) {
 
 }  // namespace flb
 
+namespace flb {
+
+int finalize_sums(const double* acc, int64_t nsamp, int32_t measure_basis, double ux0, double uy0,
+                  cudaStream_t st, double* Cff, double* CMM, double* mean_dev) {
+    if (measure_basis != FLB_BASIS_STANDARD && measure_basis != FLB_BASIS_LOCAL) return FLB_ERR_ARG;
+    if (nsamp <= 0) return FLB_ERR_STATE;
+    double* dev = nullptr;   // sums, basis, results
+    if (cudaMalloc(&dev, sizeof(double) * (kSums + 81 + 171)) != cudaSuccess) {
+        cudaGetLastError();
+        return FLB_ERR_OOM;
+    }
+    double host[171];
+    cudaError_t ce = cudaMemcpyAsync(dev, acc, sizeof(double) * kSums, cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess) {
+        measure_basis_kernel<<<1, 32, 0, st>>>(measure_basis, ux0, uy0, dev + kSums);
+        finalize_kernel<<<1, 96, 0, st>>>(dev, nsamp, dev + kSums, dev + kSums + 81);
+        ce = cudaGetLastError();
+    }
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(host, dev + kSums + 81, sizeof(host), cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    cudaFree(dev);
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        return FLB_ERR_CUDA;
+    }
+    if (Cff) std::memcpy(Cff, host, 81 * sizeof(double));
+    if (CMM) std::memcpy(CMM, host + 81, 81 * sizeof(double));
+    if (mean_dev) std::memcpy(mean_dev, host + 162, 9 * sizeof(double));
+    return FLB_OK;
+}
+
+}  // namespace flb
+
 extern "C" {
 
 int flb_version(void) { return 100; }
@@ -687,6 +721,7 @@ int flb_raw_sums(flb_lattice h, double* S1, double* S2, int64_t* n_samples) {
     if (n_samples) *n_samples = h->nsamp;
     return FLB_OK;
 }
+
 
 int flb_correlations(flb_lattice h, int32_t measure_basis, double* Cff, double* CMM,
                      double* mean_dev, int64_t* n_samples) {

@@ -1,6 +1,7 @@
-// flb_runtime.h -- what the request server (flb_server.cu) uses of batches and
-// lattice handles beyond the C ABI: creation without a host synchronisation,
-// asynchronous read-out of a replica's sums and error record, bookkeeping.
+// flb_runtime.h -- what the request server (flb_server.cu) and the batch code
+// use of batches and lattice handles beyond the C ABI: creation without a host
+// synchronisation, asynchronous read-out of a replica's sums and error record,
+// bookkeeping, the finalisation of correlation sums.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -45,5 +46,12 @@ int lut_tables(const float** t32, const double** t64);
 // waiting for its stream: the caller orders any reuse of the workspace after
 // the handle's last enqueued work.
 void lattice_forget(flb_lattice h);
+
+// <df df>, <dM dM> and the mean deviation from kSums running sums over nsamp
+// node-samples taken relative to f^0(rho0, u0) (as flb_correlations, with the
+// measurement basis at (ux0, uy0)); on a scratch buffer of its own, ordered on
+// stream st, synchronous. Any output pointer may be NULL.
+int finalize_sums(const double* acc, int64_t nsamp, int32_t measure_basis, double ux0, double uy0,
+                  cudaStream_t st, double* Cff, double* CMM, double* mean_dev);
 
 }  // namespace flb

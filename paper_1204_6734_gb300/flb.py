@@ -131,6 +131,7 @@ def load(build_if_missing: bool = True):
         "flb_batch_info": (C.c_int, [h, _i32p, _i64p, C.POINTER(C.c_size_t),
                                      C.POINTER(C.c_size_t)]),
         "flb_batch_raw_sums": (C.c_int, [h, C.c_int32, _dp, _dp, _i64p]),
+        "flb_batch_correlations": (C.c_int, [h, C.c_int32, _i32p, C.c_int32, _dp, _dp, _dp, _i64p]),
         "flb_batch_get_populations": (C.c_int, [h, C.c_int32, _dp]),
         "flb_batch_set_populations": (C.c_int, [h, C.c_int32, _dp]),
         "flb_server_create": (C.c_int, [C.c_int32, C.c_int32, C.c_size_t, C.c_int32, C.c_int32,
@@ -166,7 +167,8 @@ def exported_symbols():
             "flb_batch_replica_time", "flb_batch_info", "flb_batch_raw_sums",
             "flb_batch_get_populations", "flb_batch_set_populations", "flb_server_create",
             "flb_server_destroy", "flb_server_submit", "flb_server_poll", "flb_server_stats",
-            "flb_server_set_tile", "flb_set_structure_sampling", "flb_structure_factors"]
+            "flb_server_set_tile", "flb_set_structure_sampling", "flb_structure_factors",
+            "flb_batch_correlations"]
 
 
 def _check(rc: int, what: str):
@@ -499,6 +501,17 @@ def flb_batch_raw_sums(b, slot: int):
     return S1, S2, n.value
 
 
+def flb_batch_correlations(b, slots, measure_basis="local"):
+    """(Cff, CMM, mean, n) pooled over the given replicas (same rho0, u0)."""
+    sl = np.ascontiguousarray(np.asarray(slots, dtype=np.int32))
+    Cff, CMM, mean = np.zeros((9, 9)), np.zeros((9, 9)), np.zeros(9)
+    n = C.c_int64()
+    mb = BASIS[measure_basis] if isinstance(measure_basis, str) else int(measure_basis)
+    _check(load().flb_batch_correlations(b, len(sl), sl.ctypes.data_as(_i32p), mb, _ptr(Cff), _ptr(CMM),
+                                         _ptr(mean), C.byref(n)), "flb_batch_correlations")
+    return Cff, CMM, mean, n.value
+
+
 def flb_batch_get_populations(b, slot: int, Lx: int, Ly: int, out=None):
     if out is None:
         out = np.empty((9, Ly, Lx))
@@ -719,6 +732,9 @@ class Batch:
 
     def raw_sums(self, slot):
         return flb_batch_raw_sums(self.h, slot)
+
+    def correlations(self, slots, measure_basis="local"):
+        return flb_batch_correlations(self.h, slots, measure_basis)
 
     def populations(self, slot):
         p = self.params[slot]

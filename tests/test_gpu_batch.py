@@ -240,3 +240,52 @@ def test_full_ensemble_sampled_replicas():
         np.testing.assert_array_equal(f, ref)
         assert n == rn
         np.testing.assert_allclose(S2, R2, rtol=1e-4, atol=1e-6 * n * ps[k].kT)
+
+
+@pytest.mark.parametrize("basis", BASES)
+def test_pooled_correlations(basis):
+    """flb_batch_correlations over copies with one rho0, u0 (different seeds
+    and sizes): the covariance of the pooled raw sums (the definition, Eqs.
+    dfdef and efif0, evaluated here from the per-replica sums), and the moment
+    covariance m C m^T with the oracle's measurement basis at u0
+    (Eq. dfidfj2dmadmb). One slot alone equals flb_correlations of the same
+    lattice stepped alone."""
+    shapes = [(21, 21), (37, 8), (64, 16)]
+    ps = [inputs.LatticeParams(Lx, Ly, 1.0, 0.1, 0.0, 1e-4, inputs.omega_groups(1.0, 0.8, 1.0), basis, "fp32",
+                               seed=77 + r, replica=r) for r, (Lx, Ly) in enumerate(shapes)]
+    with flb.Batch(ps) as b:
+        b.set_sampling(10, 2)
+        b.step(60)
+        b.sync()
+        mb = "standard" if basis == inputs.STANDARD else "local"
+        Cff, CMM, mean, n = b.correlations([0, 1, 2], mb)
+        sums = [b.raw_sums(r) for r in range(3)]
+        one = b.correlations([1], mb)
+        with pytest.raises(flb.FlbError):
+            b.correlations([0, 7], mb)
+    S1 = sum(s[0] for s in sums)
+    S2 = sum(s[1] for s in sums)
+    ns = sum(s[2] for s in sums)
+    assert n == ns == sum(p.Lx * p.Ly for p in ps) * 25
+    mu = S1 / ns
+    C = S2 / ns - np.outer(mu, mu)
+    np.testing.assert_allclose(mean, mu, rtol=1e-12, atol=1e-18)
+    np.testing.assert_allclose(Cff, C, rtol=1e-9, atol=1e-9 * ps[0].kT)
+    m = oracle.local_basis(0.1, 0.0) if basis == inputs.LOCAL else oracle.tables()[3]
+    np.testing.assert_allclose(CMM, m @ C @ m.T, rtol=1e-7, atol=1e-9 * ps[0].kT)
+    with flb.Lattice(ps[1], kernel="pipelined") as lat:
+        lat.set_sampling(10, 2)
+        lat.step(60)
+        ref = lat.correlations(mb)
+    assert one[3] == ref[3]
+    for a, c in zip(one[:3], ref[:3]):
+        np.testing.assert_allclose(a, c, rtol=1e-4, atol=1e-6 * ps[0].kT)
+    # pooling needs one reference state f^0(rho0, u0)
+    q = [ps[0], inputs.LatticeParams(21, 21, 1.0, 0.2, 0.0, 1e-4, inputs.omega_groups(1.0, 0.8, 1.0), basis,
+                                     "fp32", seed=5)]
+    with flb.Batch(q) as b:
+        b.set_sampling(0, 1)
+        b.step(3)
+        with pytest.raises(flb.FlbError) as e:
+            b.correlations([0, 1], mb)
+        assert e.value.code == flb.ERR_ARG

@@ -1,14 +1,17 @@
 """The paper's Section 4 experiment on the GPU path: the drift of the moment
 variances with the background velocity, <dM^a dM^a>/(kT rho0) - 1 = l u + q u^2
-fitted over |u_x0| <= 0.25, in the Hermite norm and in the f-norm.
+fitted over -0.25 <= u_x0 <= 0.25, in the Hermite norm and in the f-norm.
+The diagonal variances are even in u_x0 (the lattice's x reflection), so the
+points u_x0 >= 0 stand for their mirror images, l = 0 and
+q = sum D u^2 / sum u^4.
 
 The paper prints q for rho, Pi_xx-yy and j_y on 21x21 lattices (Hermite
 1.9 / 1.6 / 1.14, f-norm look-up-table variant 0.47 / 0.54 / 0.75); its
 relaxation rates are not stated. Here (512^2, shear 1.0, bulk 0.8, ghost 1.0)
-the Hermite coefficients must land within 20 % of the printed ones and the
-f-norm must cut the density and stress drift at least twofold, with the
-linear terms small (|l| < 0.1): the qualitative and quantitative claim of
-Figs. 7 and 18. Statistical error of q at this size: about 0.02.
+both sets must land within 20 % of the printed ones and the f-norm must cut
+the density and stress drift at least twofold: the qualitative and
+quantitative claim of Figs. 7 and 18. Statistical error of q at this size:
+about 0.02.
 """
 import json
 import os
@@ -42,19 +45,17 @@ def sweep(basis, side=512, steps=3000, warm=300):
             _, CMM, _, _ = lat.correlations(basis)
         D.append(np.diag(CMM) / (p.kT * p.rho0) - 1.0)
     us = np.array(us)
-    A = np.stack([us, us ** 2], axis=1)
-    (l, q), *_ = np.linalg.lstsq(A, np.array(D), rcond=None)
-    return l, q
+    return (np.array(D) * us[:, None] ** 2).sum(axis=0) / (us ** 4).sum()
 
 
 def test_drift_coefficients():
     gold = json.load(open(GOLD))
     idx = gold["moments"]
-    lh, qh = sweep("standard")
-    lf, qf = sweep("local")
+    qh = sweep("standard")
+    qf = sweep("local")
     for name, a in idx.items():
         assert qh[a] == pytest.approx(gold["q_hermite"][name], rel=0.2)
-        assert abs(lh[a]) < 0.1 and abs(lf[a]) < 0.1
+        assert qf[a] == pytest.approx(gold["q_fnorm"][name], rel=0.2)
     for name in ("rho", "Pi_xx-yy"):
         a = idx[name]
         assert qf[a] < 0.5 * qh[a]
