@@ -33,6 +33,14 @@ BYTES_PER_NODE = {"fp32": 72, "fp64": 144}
 # dram__bytes_write.sum of the full-size launch (614.3 + 559.4 MB, averaged
 # over 23 launches). Valid only for the kernel version it was taken on.
 DRAM_TRAFFIC = {("fp32", "local", 4096): 614.3e6 + 559.4e6}
+# FP64 operations per node-step of the FP64 step kernel (f-norm, sampling
+# every step): 2 DFMA + DADD + DMUL thread instructions counted by ncu on a
+# 2048^2 launch (1669.3 M DFMA, 487.2 M DADD, 629.1 M DMUL over 4.19 M nodes;
+# the FP64 pipe 87.5 % busy). The FP64 kernel is bound by GB300's FP64 rate,
+# not by HBM: its roofline is reported against the nominal FP64 peak (there
+# is no measured FP64 peak).
+FP64_FLOPS_PER_NODE = {"local": 1062.2}
+FP64_NOMINAL_TFLOPS = 1.25
 
 
 def parse():
@@ -721,6 +729,14 @@ def main():
                 "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                 "kernel": kname, "algorithmic_bytes": algo_bytes,
                 "traffic_source": "ncu dram bytes of the full-size launch" if traffic else None}
+    if args.precision == "fp64" and args.basis in FP64_FLOPS_PER_NODE:
+        tf = FP64_FLOPS_PER_NODE[args.basis] * nodes / (step_ms * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": tf, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                    "frac": tf / FP64_NOMINAL_TFLOPS, "traffic": None,
+                    "peak_kind": "nominal FP64 rate (no measured FP64 peak)", "kernel": kname,
+                    "flops_per_node": FP64_FLOPS_PER_NODE[args.basis],
+                    "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                            "peak_kind": peak_kind}}
 
     Cff, CMM, mean, ns = lat.correlations(args.basis)
     lat.close()
