@@ -613,6 +613,16 @@ def feq_of(p):
     return p.rho0 * w * (1 + 3 * uv + 4.5 * uv ** 2 - 1.5 * usq)
 
 
+def single_config(p, args, world):
+    """The config object of the single-lattice line (both arms)."""
+    return {"workload": f"{p.Lx}x{p.Ly} periodic D2Q9 lattice, {args.precision} SoA, "
+                        f"{args.basis} basis, u_x0={p.ux0}, kT={p.kT}, "
+                        f"omega shear/bulk/ghost=1.0/0.8/1.0, correlations sampled every step",
+            "Lx": p.Lx, "Ly": p.Ly, "basis": args.basis, "precision": args.precision,
+            "parallelism": f"replicas x{world}",
+            "l2": "inputs larger than L2 (2 x 604 MB population buffers)"}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -629,15 +639,16 @@ def run_reference(args):
     run.step(args.steps)
     dt = time.perf_counter() - t0
     value = side * side * args.steps / dt / 1e6
+    cfg = single_config(inputs.single_lattice(args.ux0, args.basis, side=args.side,
+                                              precision=args.precision), args, world)
     out = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
-        "config": {"workload": f"{p.Lx}x{p.Ly} periodic D2Q9, {p.basis} basis, u_x0={p.ux0}",
-                   "sample": f"{side}x{side} lattice per step", "l2": "oracle on host cores"},
+        "data": "synthetic", "config": cfg,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{side}x{side} lattice, {args.steps} steps"},
+                         "sample": f"the same workload on a {side}x{side} lattice, FP64, one host "
+                                   f"thread, {args.steps} steps (MLUPS of the sample)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out))
@@ -805,12 +816,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
-            "config": {"workload": f"{p.Lx}x{p.Ly} periodic D2Q9 lattice, {args.precision} SoA, "
-                                   f"{args.basis} basis, u_x0={p.ux0}, kT={p.kT}, "
-                                   f"omega shear/bulk/ghost=1.0/0.8/1.0, correlations sampled every step",
-                       "Lx": p.Lx, "Ly": p.Ly, "basis": args.basis, "precision": args.precision,
-                       "parallelism": f"replicas x{world}",
-                       "l2": "inputs larger than L2 (2 x 604 MB population buffers)"},
+            "config": single_config(p, args, world),
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
