@@ -65,7 +65,8 @@ def parse():
                     help="skip the batched-ensemble comparison added to the JSON line")
     ap.add_argument("--batched-steps", type=int, default=200)
     ap.add_argument("--workload", default="single",
-                    choices=["single", "ensemble", "serving", "precision", "sweep", "sweep21"],
+                    choices=["single", "ensemble", "serving", "precision", "sweep", "sweep21",
+                             "structure"],
                     help="single: the 4096^2 lattice (with the ensemble comparison added); "
                          "ensemble: only the batched replica ensemble, as the main line")
     ap.add_argument("--replicas", type=int, default=256, help="replicas of the ensemble")
@@ -602,6 +603,54 @@ def run_sweep21(args, rank, world, dist, dev):
         print(json.dumps(line))
 
 
+def run_structure(args, rank, world, dist, dev):
+    """--workload structure: the anisotropy of the static structure factors
+    (Eqs. sfactorr, sfactoru, rcorrelator) at u_x0 = 0, 0.1, 0.2 in both norms
+    on a --side^2 lattice (default 64): S_k / (N kT) - 1 for rho and
+    S_k / (N kT / 3) - 1 for j_x (0 for the ideal gas at every k != 0), averaged
+    over the modes on the k_x axis (m_y = 0), on the k_y axis (m_x = 0) and
+    over all k != 0; |R_k| / (N kT / 3) likewise. Thermalised for --warmup
+    steps, then --steps steps with S_k sampled every 5."""
+    import numpy as np
+    import torch
+
+    from paper_1204_6734_gb300 import flb, inputs
+    side = args.side if args.side != 4096 else 64
+    every = 5
+    res = {}
+    t0 = time.perf_counter()
+    for basis in ("standard", "local"):
+        rows = {}
+        for u in (0.0, 0.1, 0.2):
+            p = inputs.single_lattice(u, basis, side=side)
+            with flb.Lattice(p) as lat:
+                lat.set_structure_sampling(args.warmup, every)
+                lat.step(args.warmup + args.steps)
+                Sr, Sx, R, n = lat.structure_factors()
+            N = side * side
+            a, b, c = Sr / (N * p.kT) - 1.0, Sx / (N * p.kT / 3.0) - 1.0, np.abs(R) / (N * p.kT / 3.0)
+            mask = np.ones_like(a, dtype=bool)
+            mask[0, 0] = False
+
+            def dirs(x):
+                return {"k_x_axis": float(x[0, 1:].mean()), "k_y_axis": float(x[1:, 0].mean()),
+                        "all_k": float(x[mask].mean()),
+                        "k_x_axis_min": float(x[0, 1:].min()), "k_x_axis_max": float(x[0, 1:].max())}
+            rows[str(u)] = {"samples": int(n), "S_rho_minus_1": dirs(a), "S_jx_minus_1": dirs(b),
+                            "abs_R": dirs(c)}
+        res[basis] = rows
+    if rank == 0:
+        line = {"metric": METRIC, "value": None, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"structure factors of the {side}^2 lattice (kT=1e-4, shear 1.0, "
+                                       "bulk 0.8, ghost 1.0) at u_x0 = 0, 0.1, 0.2, Hermite and f-norm, "
+                                       f"sampled every {every} steps after {args.warmup}",
+                           "l2": "state fits L2 (small lattice)"},
+                "structure": res, "wall_s": time.perf_counter() - t0}
+        print(json.dumps(line))
+
+
 def feq_of(p):
     """f_i^0(rho0, u0) of Eq. d2q9f0, to normalise the measured variances."""
     import numpy as np
@@ -683,7 +732,7 @@ def main():
         if dist is not None:
             dist.barrier()
         run = {"ensemble": run_ensemble, "serving": run_serving, "precision": run_precision,
-               "sweep": run_sweep, "sweep21": run_sweep21}
+               "sweep": run_sweep, "sweep21": run_sweep21, "structure": run_structure}
         run[args.workload](args, rank, world, dist, dev)
         if dist is not None:
             dist.destroy_process_group()
