@@ -418,7 +418,9 @@ int flb_server_set_tile(flb_server s, int32_t tile);
  *    FLB_KERNEL_GENERIC (one node per thread, plain loads) or
  *    FLB_KERNEL_PIPELINED (FP32 only). All give the same results up to rounding.
  *  FLB_OPT_PIPELINE_WARPS: consumer warps per CTA of the pipelined kernel
- *    (8 or 12; the tile is 128 x value/2 nodes). FP32 only.
+ *    (8 or 12; the tile is 128 x value/2 nodes) for every step. By default
+ *    sampling steps use 8 and, in the f-norm bases, steps without sampling
+ *    use 12. FP32 only.
  *  FLB_OPT_PIPELINE_SAMPLING: how the pipelined kernel accumulates the
  *    correlation sums on sampling steps -- 1 (default): dedicated sampler warps
  *    read the staged tile; 2: the colliding warps accumulate their own nodes.

@@ -165,18 +165,37 @@ def test_fp64_parity_lattice_full_run():
     np.testing.assert_allclose(mean, mean_ref, atol=1e-12)
 
 
-KERNELS = ["generic", "pipelined", "pipelined-samplers", "pipelined12"]
+KERNELS = ["generic", "pipelined", "pipelined-fused", "pipelined12", "pipelined8"]
 
 
 def lattice(p, kernel):
     """A lattice with the given FP32 step kernel: the generic one, or the
-    pipelined one (8 consumer warps with fused sampling by default; sampler
-    warps; 12 consumer warps)."""
+    pipelined one -- by default sampler warps and 8 colliding warps on
+    sampling steps, 12 colliding warps on the f-norm bases' other steps;
+    sums fused into the colliding warps; 12 or 8 colliding warps on every
+    step."""
     if kernel == "pipelined12":
         return flb.Lattice(p, kernel="pipelined", pipeline_warps=12)
-    if kernel == "pipelined-samplers":
-        return flb.Lattice(p, kernel="pipelined", pipeline_sampling=1)
+    if kernel == "pipelined8":
+        return flb.Lattice(p, kernel="pipelined", pipeline_warps=8)
+    if kernel == "pipelined-fused":
+        return flb.Lattice(p, kernel="pipelined", pipeline_sampling=2)
     return flb.Lattice(p, kernel=kernel)
+
+
+@pytest.mark.parametrize("basis", BASES)
+def test_warp_counts_give_identical_states(basis):
+    """8 and 12 colliding warps pair the same nodes (x, x + 64) in the same
+    packed arithmetic: identical populations, with and without sampling."""
+    p = inputs.LatticeParams(300, 37, 1.0, 0.15, 0.05, 1e-3, inputs.omega_groups(1.2, 0.8, 1.3), basis,
+                             "fp32", seed=8)
+    out = []
+    for kernel in ("pipelined", "pipelined8", "pipelined12"):
+        with lattice(p, kernel) as lat:
+            lat.set_sampling(10, 3)
+            lat.step(40)
+            out.append(lat.populations())
+    assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
@@ -254,7 +273,7 @@ def test_pipelined_equals_generic_fp32(basis):
             lat.set_sampling(2, 1)
             lat.step(30)
             out[kernel] = (lat.populations(), lat.raw_sums())
-    for k in ("pipelined", "pipelined-samplers", "pipelined12"):
+    for k in KERNELS[1:]:
         assert np.abs(out["generic"][0] - out[k][0]).max() < 1e-6
         np.testing.assert_allclose(out["generic"][1][1], out[k][1][1], rtol=1e-4)
 
