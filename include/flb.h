@@ -132,8 +132,8 @@ int flb_error_location(flb_lattice h, int64_t* node, int64_t* step);
 /* Forget a recorded device error (the state is left as it is). */
 int flb_reset_error(flb_lattice h);
 
-/* Equal-time correlations of the sampled pre-collision populations (a second
- * kernel reduces the per-block partial sums; all in FP64):
+/* Equal-time correlations of the sampled pre-collision populations (the step
+ * kernels accumulate FP64 sums; they are finalised on the device):
  *  Cff[81]   <df_i df_j> = centred covariance of f_i over nodes and samples
  *            (Eqs. dfdef, efif0; the mean is the sample mean);
  *  CMM[81]   <dM^a dM^b> = sum_ij m^a_i m^b_j <df_i df_j> (Eq. dfidfj2dmadmb),
@@ -179,11 +179,13 @@ int flb_state_difference(flb_lattice a, flb_lattice b, double out[3]);
  * delta rho(x) = rho(x) - rho0, delta j(x) = j(x) - rho0 u0, transforms them,
  * a(k) = sum_x a(x) exp(-i k.x) with k = 2 pi (m_x / Lx, m_y / Ly), and adds
  * |drho(k)|^2, |dj_x(k)|^2 and dj_x(k) conj(dj_y(k)) to FP64 sums. The
- * transform runs in FP64 for FP64 lattices, in FP32 otherwise: radix-2 FFTs
- * for power-of-two sides, a direct O(L^2) transform per row or column for
- * other sides. The first call with every > 0 allocates the library's own
- * device buffers (4 complex plus 4 double arrays of Lx*Ly values), freed by
- * flb_destroy. Errors: FLB_ERR_ARG (negative arguments; a side above 20480 in
+ * transform runs in FP64 for FP64 lattices, in FP32 otherwise: FFTs (Stockham
+ * passes in shared memory) for power-of-two sides, a direct O(L^2) transform
+ * per row or column for other sides; when both sides are powers of two up to
+ * 4096, two launches per sample and sums over half the k plane (the other
+ * half follows from S(-k) = S(k), R(-k) = conj R(k)). The first call with
+ * every > 0 allocates the library's own device buffers (at most 3 complex
+ * and 4 double arrays of Lx*Ly values), freed by flb_destroy. Errors: FLB_ERR_ARG (negative arguments; a side above 20480 in
  * FP32 or 10240 in FP64), FLB_ERR_OOM, a recorded device error (sticky). */
 int flb_set_structure_sampling(flb_lattice h, int64_t warmup, int64_t every);
 
