@@ -30,9 +30,9 @@ UNIT = "MLUPS"
 BYTES_PER_NODE = {"fp32": 72, "fp64": 144}
 # DRAM bytes (read + write) per launch of the FP32 step kernel at 4096^2,
 # f-norm basis, sampling every step: ncu dram__bytes_read.sum +
-# dram__bytes_write.sum of the full-size launch (614.3 + 559.4 MB, averaged
+# dram__bytes_write.sum of the full-size launch (616.7 + 559.0 MB, averaged
 # over 23 launches). Valid only for the kernel version it was taken on.
-DRAM_TRAFFIC = {("fp32", "local", 4096): 614.3e6 + 559.4e6}
+DRAM_TRAFFIC = {("fp32", "local", 4096): 616.7e6 + 559.0e6}
 # FP64 operations per node-step of the FP64 step kernel (f-norm, sampling
 # every step): 2 DFMA + DADD + DMUL thread instructions counted by ncu on a
 # 2048^2 launch (1669.3 M DFMA, 487.2 M DADD, 629.1 M DMUL over 4.19 M nodes;
