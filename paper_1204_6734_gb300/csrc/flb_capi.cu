@@ -613,21 +613,8 @@ int flb_structure_factors(flb_lattice h, double* S_rho, double* S_jx, double* R_
     if (n_samples) *n_samples = ns;
     if (!S_rho && !S_jx && !R_re && !R_im) return FLB_OK;
     if (!h->sk || ns == 0) return FLB_ERR_STATE;
-    const size_t N = (size_t)h->p.Lx * h->p.Ly;
-    std::vector<double> sums;
-    try {
-        sums.resize(4 * N);
-    } catch (const std::bad_alloc&) {
-        return FLB_ERR_OOM;
-    }
-    const int rc = structure_read(h->sk, sums.data(), h->stream);
-    if (rc) return rc;
-    const double k = 1.0 / ((double)ns * h->p.rho0);
-    double* out[4] = {S_rho, S_jx, R_re, R_im};
-    for (int q = 0; q < 4; ++q)
-        if (out[q])
-            for (size_t n = 0; n < N; ++n) out[q][n] = sums[q * N + n] * k;
-    return FLB_OK;
+    double* const out[4] = {S_rho, S_jx, R_re, R_im};
+    return structure_read(h->sk, out, 1.0 / ((double)ns * h->p.rho0), h->stream);
 }
 
 int flb_step(flb_lattice h, int64_t n) {

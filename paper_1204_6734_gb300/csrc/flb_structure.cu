@@ -664,34 +664,44 @@ cudaError_t structure_sample(StructSampler* s, const void* buf, int precision, c
     return ce;
 }
 
-int structure_read(StructSampler* s, double* out, cudaStream_t st) {
+int structure_read(StructSampler* s, double* const out[4], double scale, cudaStream_t st) {
     const size_t N = (size_t)s->Lx * s->Ly;
     if (!s->fast) {
-        cudaError_t ce = cudaMemcpyAsync(out, s->acc, 4 * N * sizeof(double), cudaMemcpyDeviceToHost, st);
+        cudaError_t ce = cudaSuccess;
+        for (int q = 0; q < 4 && ce == cudaSuccess; ++q)
+            if (out[q])
+                ce = cudaMemcpyAsync(out[q], s->acc + q * N, N * sizeof(double), cudaMemcpyDeviceToHost, st);
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
-        return ce == cudaSuccess ? FLB_OK : FLB_ERR_CUDA;
+        if (ce != cudaSuccess) return FLB_ERR_CUDA;
+        for (int q = 0; q < 4; ++q)
+            if (out[q])
+                for (size_t n = 0; n < N; ++n) out[q][n] *= scale;
+        return FLB_OK;
     }
+    // half plane [q][m_x][m_y], m_x = 0..Lx/2, one q at a time
+    const int Lx = s->Lx, Ly = s->Ly, Hx = s->Hx;
+    const size_t Q = (size_t)Hx * Ly;
     std::vector<double> half;
     try {
-        half.resize(s->acc_count);
+        half.resize(Q);
     } catch (const std::bad_alloc&) {
         return FLB_ERR_OOM;
     }
-    cudaError_t ce = cudaMemcpyAsync(half.data(), s->acc, s->acc_count * sizeof(double),
-                                     cudaMemcpyDeviceToHost, st);
-    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
-    if (ce != cudaSuccess) return FLB_ERR_CUDA;
-    const int Lx = s->Lx, Ly = s->Ly, Hx = s->Hx;
-    const size_t Q = (size_t)Hx * Ly;
-    for (int q = 0; q < 4; ++q)
-        for (int my = 0; my < Ly; ++my)
-            for (int mx = 0; mx < Lx; ++mx) {
-                // m_x > Lx/2: the value at -k; Im R changes sign there
-                const bool mirror = mx >= Hx;
-                const int hx = mirror ? Lx - mx : mx, hy = mirror ? (Ly - my) & (Ly - 1) : my;
-                const double v = half[q * Q + (size_t)hx * Ly + hy];
-                out[q * N + (size_t)my * Lx + mx] = (mirror && q == 3) ? -v : v;
-            }
+    for (int q = 0; q < 4; ++q) {
+        if (!out[q]) continue;
+        cudaError_t ce = cudaMemcpyAsync(half.data(), s->acc + q * Q, Q * sizeof(double),
+                                         cudaMemcpyDeviceToHost, st);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+        if (ce != cudaSuccess) return FLB_ERR_CUDA;
+        // m_x > Lx/2: the value at -k; Im R changes sign there
+        const double sm = q == 3 ? -scale : scale;
+        for (int my = 0; my < Ly; ++my) {
+            double* row = out[q] + (size_t)my * Lx;
+            for (int mx = 0; mx < Hx; ++mx) row[mx] = half[(size_t)mx * Ly + my] * scale;
+            const int ny = (Ly - my) & (Ly - 1);
+            for (int mx = Hx; mx < Lx; ++mx) row[mx] = half[(size_t)(Lx - mx) * Ly + ny] * sm;
+        }
+    }
     return FLB_OK;
 }
 

@@ -26,10 +26,10 @@ cudaError_t structure_reset(StructSampler* s, cudaStream_t st);
 // f^0(rho0, u0), the fields being sums of f_i - ref_i.
 cudaError_t structure_sample(StructSampler* s, const void* buf, int precision, const Geometry& geo,
                              const DevCodec& codec, const double* ref, cudaStream_t st);
-// The four FP64 sums [S_rho | S_jx | Re R | Im R], each Ly x Lx ([m_y][m_x]),
-// unnormalised, into host memory; synchronises the stream. FLB_OK,
-// FLB_ERR_OOM or FLB_ERR_CUDA.
-int structure_read(StructSampler* s, double* host4N, cudaStream_t st);
+// The four FP64 sums S_rho, S_jx, Re R, Im R, each Ly x Lx ([m_y][m_x]),
+// times `scale`, into the host arrays out[0..3] (a NULL entry is skipped);
+// synchronises the stream. FLB_OK, FLB_ERR_OOM or FLB_ERR_CUDA.
+int structure_read(StructSampler* s, double* const out[4], double scale, cudaStream_t st);
 int64_t structure_samples(const StructSampler* s);
 
 }  // namespace flb
