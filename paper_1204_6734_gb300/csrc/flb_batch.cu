@@ -48,6 +48,7 @@ struct BatchSlot {
 
 struct flb_batch_s {
     int basis = 0, cap = 0;
+    const float* lut = nullptr;   // velocity table (look-up-table f-norm)
     cudaStream_t stream = nullptr;
     char* pool = nullptr;
     Arena arena;
@@ -96,16 +97,20 @@ int64_t slot_time(const flb_batch_s* b, const BatchSlot& s) {
     return std::min<int64_t>(b->step - s.join, s.tend);
 }
 
-const void* kernel_for(const flb_batch_s* b, bool sample) {
-    return b->basis == FLB_BASIS_STANDARD ? batch_kernel_std(b->tile, sample)
-                                          : batch_kernel_loc(b->tile, sample);
+const void* kernel_of(int basis, int variant, bool sample) {
+    return basis == FLB_BASIS_STANDARD ? batch_kernel_std(variant, sample)
+           : basis == FLB_BASIS_LOCAL  ? batch_kernel_loc(variant, sample)
+                                       : batch_kernel_lut(variant, sample);
 }
+
+const void* kernel_for(const flb_batch_s* b, bool sample) { return kernel_of(b->basis, b->tile, sample); }
 
 cudaError_t launch(flb_batch_s* b, bool sample, cudaStream_t s) {
     BatchArgs a;
     a.desc = b->desc;
     a.tiles = b->tiles;
     a.ctl = b->ctl;
+    a.lut = b->lut;
     void* params[1] = {(void*)&a};
     const int warps = kBatchNW + (sample ? kSamplers : 1);
     return cudaLaunchKernel(kernel_for(b, sample), dim3(b->grid), dim3(warps * 32), params,
@@ -220,7 +225,8 @@ int flb_batch_open(int32_t basis, int32_t max_replicas, size_t pool_bytes, void*
                    flb_batch* out) {
     if (!out) return FLB_ERR_ARG;
     *out = nullptr;
-    if ((basis != FLB_BASIS_STANDARD && basis != FLB_BASIS_LOCAL) || max_replicas < 1 ||
+    if ((basis != FLB_BASIS_STANDARD && basis != FLB_BASIS_LOCAL && basis != FLB_BASIS_LOCAL_LUT) ||
+        max_replicas < 1 ||
         max_replicas > kMaxBatchReplicas || pool_bytes < Arena::kAlign)
         return FLB_ERR_ARG;
     flb_batch b = new (std::nothrow) flb_batch_s();
@@ -264,10 +270,11 @@ int flb_batch_open(int32_t basis, int32_t max_replicas, size_t pool_bytes, void*
     cudaError_t ce = cudaMemsetAsync(b->meta, 0, meta_bytes, b->stream);
     if (ce == cudaSuccess) ce = cudaGetDevice(&dev);
     if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (ce == cudaSuccess && b->basis == FLB_BASIS_LOCAL_LUT && lut_tables(&b->lut, nullptr) != FLB_OK)
+        ce = cudaErrorUnknown;
     for (int v = 0; v < kNumBatchVariants && ce == cudaSuccess; ++v)
         for (int smp = 0; smp < 2 && ce == cudaSuccess; ++smp) {
-            const void* fn = b->basis == FLB_BASIS_STANDARD ? batch_kernel_std(v, smp)
-                                                            : batch_kernel_loc(v, smp);
+            const void* fn = kernel_of(b->basis, v, smp);
             ce = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)batch_smem_bytes(v));
         }

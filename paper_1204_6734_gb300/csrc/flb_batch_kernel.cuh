@@ -65,6 +65,7 @@ struct BatchArgs {
     const ReplicaDesc* desc;
     const uint32_t* tiles;    // (replica << kLocalBits) | tile index within the replica
     BatchCtl* ctl;
+    const float* lut;         // velocity table of the look-up-table f-norm (BASIS 2)
 };
 
 constexpr int kLocalBits = 18;
@@ -351,9 +352,9 @@ batch_step_kernel(const BatchArgs a) {
             const bool inA = xA < geo.Lx && y < geo.Ly, inB = xB < geo.Lx && y < geo.Ly;
             const uint32_t nodeA = (uint32_t)xA + (uint32_t)geo.Lx * (uint32_t)y;
             f2 f[9];
-            const uint32_t stt = collide<f2, BASIS>(
+            const uint32_t stt = collide_basis<f2, BASIS>(
                 g, [&](f2* N) { node_normals(hs.cc.key, nodeA, nodeA + TW / 2, tr, N); }, load,
-                hs.cc, f);
+                a.lut, hs.cc, f);
             __syncwarp();
             if (lane_id == 0) mbar_arrive(&empty[s]);
             if (stt) {
@@ -383,8 +384,8 @@ batch_step_kernel(const BatchArgs a) {
             const bool in = x < geo.Lx && y < geo.Ly;
             const uint32_t node = (uint32_t)x + (uint32_t)geo.Lx * (uint32_t)y;
             float f[9];
-            const uint32_t stt = collide<float, BASIS>(
-                g, [&](float* N) { node_normals(hs.cc.key, node, tr, N); }, load, hs.cc, f);
+            const uint32_t stt = collide_basis<float, BASIS>(
+                g, [&](float* N) { node_normals(hs.cc.key, node, tr, N); }, load, a.lut, hs.cc, f);
             __syncwarp();
             if (lane_id == 0) mbar_arrive(&empty[s]);
             if (in) {
@@ -414,6 +415,7 @@ constexpr int kNumBatchVariants = 3;
 // Kernel of (variant, basis, sampling), instantiated in flb_batch_k<basis>.cu.
 const void* batch_kernel_std(int variant, bool sample);
 const void* batch_kernel_loc(int variant, bool sample);
+const void* batch_kernel_lut(int variant, bool sample);
 size_t batch_smem_bytes(int variant);
 
 }  // namespace flb

@@ -293,7 +293,7 @@ int flb_server_create(int32_t mode, int32_t basis, size_t pool_bytes, int32_t ma
     *out = nullptr;
     if ((mode != FLB_SERVE_BATCHED && mode != FLB_SERVE_PER_LATTICE) || max_slots < 1 ||
         max_slots > 16384 || chunk_steps < 1 || chunk_steps > 100000 || pool_bytes < 4096 ||
-        (basis != FLB_BASIS_STANDARD && basis != FLB_BASIS_LOCAL))
+        (basis != FLB_BASIS_STANDARD && basis != FLB_BASIS_LOCAL && basis != FLB_BASIS_LOCAL_LUT))
         return FLB_ERR_ARG;
     flb_server s = new (std::nothrow) flb_server_s();
     if (!s) return FLB_ERR_OOM;

@@ -53,7 +53,7 @@ def expected_samples(p, steps, warmup, every):
 
 def serve(reqs, mode="batched", pool=None, slots=4, chunk=8):
     pool = pool or sum(flb.flb_batch_replica_bytes(p) for p, *_ in reqs) * 2 + (64 << 20)
-    with flb.Server(inputs.LOCAL, pool, slots, chunk, mode=mode) as s:
+    with flb.Server(reqs[0][0].basis, pool, slots, chunk, mode=mode) as s:
         ids = [s.submit(p, n, w, e) for p, n, w, e in reqs]
         res = {r["id"]: r for r in s.drain()}
         st = s.stats()
@@ -80,8 +80,9 @@ def test_result_same_alone_and_in_the_mix(mode):
         close(got, {"status": flb.OK, "n_samples": nh, "S1": S1, "S2": S2}, ns, p.kT)
 
 
-def test_modes_agree():
-    reqs = mix(n=6, seed=3)
+@pytest.mark.parametrize("basis", [inputs.LOCAL, inputs.LUT])
+def test_modes_agree(basis):
+    reqs = mix(basis=basis, n=6, seed=3)
     a, _ = serve(reqs, mode="batched", slots=3)
     b, _ = serve(reqs, mode="per_lattice", slots=3)
     for (p, n, w, e), x, y in zip(reqs, a, b):
