@@ -82,10 +82,10 @@ SINGLE_LATTICE_STEPS = 2000
 def small_sweep_replicas(ux0: float, basis: str, n: int = 256, side: int = 21) -> List[LatticeParams]:
     """n independent copies of the paper's small lattice (side x side, the
     sweep's rates and kT as single_lattice) at one u_x0: seeds
-    0x21000000 + 4096 i_u + 1024 b + r (b = 0 standard, 1 local), so that
-    every replica of every sweep point draws its own noise."""
+    0x21000000 + 4096 i_u + 1024 b + r (b = 0 standard, 1 local, 2 table
+    f-norm), so that every replica of every sweep point draws its own noise."""
     iu = SWEEP_UX0.index(ux0) if ux0 in SWEEP_UX0 else 0
-    b = {STANDARD: 0, LOCAL: 1}[basis]
+    b = {STANDARD: 0, LOCAL: 1, LUT: 2}[basis]
     return [LatticeParams(side, side, 1.0, ux0, 0.0, 1e-4, omega_groups(1.0, 0.8, 1.0), basis, "fp32",
                           seed=0x21000000 + 4096 * iu + 1024 * b + r) for r in range(n)]
 
