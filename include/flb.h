@@ -64,8 +64,8 @@ extern "C" {
  * table (Section 4: the basis at the nearest table velocity u_g, spacing
  * 0.02, |u_g| <= 0.5; equilibrium moments projected onto it exactly; velocity
  * off the table or at a table point where some f_i^0(1, u_g) <= 0 is
- * FLB_ERR_INVALID_VELOCITY). FP64 and FP32 only for the table variant; batches
- * and the server (FP32) take all three. */
+ * FLB_ERR_INVALID_VELOCITY). Every precision takes every basis; batches and
+ * the server (FP32) take all three. */
 typedef enum { FLB_BASIS_STANDARD = 0, FLB_BASIS_LOCAL = 1, FLB_BASIS_LOCAL_LUT = 2 } flb_basis;
 typedef enum { FLB_FP64 = 0, FLB_FP32 = 1, FLB_FP16_DEV = 2 } flb_precision;
 

@@ -371,6 +371,7 @@ cudaError_t launch_step_fp16(flb_lattice h, bool sample) {
     a.tiles_x = a.ntiles = 0;
     a.acc = h->acc;
     a.err = h->err;
+    a.lut = h->lut32;
     const DevCodec c = dev_codec(h);
     a.scale = c.scale;
     a.inv_scale = 1.0f / c.scale;

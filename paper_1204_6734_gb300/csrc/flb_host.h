@@ -39,7 +39,6 @@ inline int valid_params(const flb_params* p) {
     if (p->precision != FLB_FP64 && p->precision != FLB_FP32 && p->precision != FLB_FP16_DEV)
         return 0;
     if (p->precision == FLB_FP16_DEV && !(p->kT > 0)) return 0;   // the store scale is sqrt(kT)
-    if (p->precision == FLB_FP16_DEV && p->basis == FLB_BASIS_LOCAL_LUT) return 0;
     if (p->reserved != 0) return 0;
     // the mean velocity must leave every f_i^0(1,u0) > 0 (Fig. 11)
     const double usq = p->ux0 * p->ux0 + p->uy0 * p->uy0;

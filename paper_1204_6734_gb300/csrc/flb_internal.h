@@ -54,6 +54,7 @@ struct HArgs {
     float ref[9];           // f^0(rho0, u0)
     float nref[9];          // -ref / scale
     float scale, inv_scale;
+    const float* lut;       // velocity table (look-up-table f-norm only)
 };
 
 // Tensor maps and launch shape of the FP16-store kernel; one step of it.

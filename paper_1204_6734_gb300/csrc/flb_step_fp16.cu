@@ -221,8 +221,8 @@ step_fp16_kernel(const __grid_constant__ CUtensorMap map, const HArgs a,
         const bool inA = xA < Lx && y < Ly, inB = xB < Lx && y < Ly;
         const uint32_t nodeA = (uint32_t)xA + (uint32_t)Lx * (uint32_t)y;
         f2 f[9];
-        const uint32_t stt = collide<f2, BASIS>(
-            g, [&](f2* N) { node_normals(cc.key, nodeA, nodeA + 64u, a.step, N); }, load, cc, f);
+        const uint32_t stt = collide_basis<f2, BASIS>(
+            g, [&](f2* N) { node_normals(cc.key, nodeA, nodeA + 64u, a.step, N); }, load, a.lut, cc, f);
         __syncwarp();
         if (lane_id == 0) mbar_arrive(&empty[s]);
         if (stt) {
@@ -253,7 +253,8 @@ step_fp16_kernel(const __grid_constant__ CUtensorMap map, const HArgs a,
 
 const void* fp16_kernel(int basis, bool sample) {
     if (basis == 0) return sample ? (const void*)step_fp16_kernel<0, true> : (const void*)step_fp16_kernel<0, false>;
-    return sample ? (const void*)step_fp16_kernel<1, true> : (const void*)step_fp16_kernel<1, false>;
+    if (basis == 1) return sample ? (const void*)step_fp16_kernel<1, true> : (const void*)step_fp16_kernel<1, false>;
+    return sample ? (const void*)step_fp16_kernel<2, true> : (const void*)step_fp16_kernel<2, false>;
 }
 
 }  // namespace
@@ -269,7 +270,7 @@ cudaError_t fp16_plan(TmaPlan* plan, void* buf0, void* buf1, const Geometry& g) 
     int dev = 0, sms = 0;
     cudaError_t ce = cudaGetDevice(&dev);
     if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    for (int basis = 0; basis < 2 && ce == cudaSuccess; ++basis)
+    for (int basis = 0; basis < 3 && ce == cudaSuccess; ++basis)
         for (int smp = 0; smp < 2 && ce == cudaSuccess; ++smp)
             ce = cudaFuncSetAttribute(fp16_kernel(basis, smp),
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -67,7 +67,7 @@ def test_roundtrip_is_the_fp16_encoding(shape):
     np.testing.assert_allclose(back, decode(encode(f, p), p), rtol=1e-15, atol=1e-15)
 
 
-@pytest.mark.parametrize("basis", BASES)
+@pytest.mark.parametrize("basis", BASES + [inputs.LUT])
 def test_one_step_is_fp32_then_rounded(basis):
     """From a state FP16 holds exactly, one FP16-store step equals the FP32 step
     up to the rounding of the encoded result."""
@@ -103,6 +103,23 @@ def test_trajectory_and_correlations_against_oracle(basis):
     C_ref, _ = run.covariance()
     assert np.abs(Cff - C_ref).max() < 0.01 * p.kT * 4.0 / 9.0
     assert np.abs(CMM - run.moment_covariance(basis)).max() < 0.01 * p.kT
+
+
+def test_table_basis_correlations_against_oracle():
+    """The look-up-table f-norm on the FP16 store: its table cell is an FP32
+    decision on the decoded state, which may differ from the FP64 oracle's at
+    a node near a cell edge, so the check is on the correlations (1 %)."""
+    p = params(inputs.LUT)
+    nsteps, warm = 300, 100
+    run = oracle.Run(p, warmup=warm, every=1).step(nsteps)
+    with flb.Lattice(p) as lat:
+        lat.set_sampling(warm, 1)
+        lat.step(nsteps)
+        Cff, CMM, mean, n = lat.correlations("local")
+    assert n == run.nsamp
+    C_ref, _ = run.covariance()
+    assert np.abs(Cff - C_ref).max() < 0.01 * p.kT * 4.0 / 9.0
+    assert np.abs(CMM - run.moment_covariance("local")).max() < 0.01 * p.kT
 
 
 def test_mass_and_momentum_drift_is_rounding_only():
