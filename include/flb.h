@@ -126,6 +126,18 @@ int flb_sync(flb_lattice h);
 /* Current time step t (number of collisions performed). */
 int flb_time(flb_lattice h, int64_t* t);
 
+/* Checkpoint and resume. A run continues exactly (the same noise draws, the
+ * same sampling schedule, the same sums up to FP64 rounding order) from its
+ * state f_i(x, t) (flb_get_populations), its time t (flb_time) and its raw
+ * sums (flb_raw_sums): on a new handle with the same parameters call
+ * flb_set_sampling (which clears the sums), then flb_set_raw_sums,
+ * flb_set_time and flb_set_populations. flb_set_time sets t, the step
+ * counter of the noise (0 <= t < 2^32); flb_set_raw_sums sets S1[9],
+ * S2[81] (the entries i <= j are used) and the node-sample count.
+ * Errors: FLB_ERR_ARG, FLB_ERR_CUDA. Structure-factor sums are not covered. */
+int flb_set_time(flb_lattice h, int64_t t);
+int flb_set_raw_sums(flb_lattice h, const double* S1, const double* S2, int64_t n_samples);
+
 /* Node and step of the first recorded device error (-1, -1 if none). */
 int flb_error_location(flb_lattice h, int64_t* node, int64_t* step);
 

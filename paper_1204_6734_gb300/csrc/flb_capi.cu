@@ -685,6 +685,26 @@ int flb_time(flb_lattice h, int64_t* t) {
     return FLB_OK;
 }
 
+int flb_set_time(flb_lattice h, int64_t t) {
+    if (!h || t < 0 || t > (int64_t)UINT32_MAX) return FLB_ERR_ARG;
+    h->t = t;
+    return FLB_OK;
+}
+
+int flb_set_raw_sums(flb_lattice h, const double* S1, const double* S2, int64_t n_samples) {
+    if (!h || !S1 || !S2 || n_samples < 0) return FLB_ERR_ARG;
+    double acc[kSums];
+    int k = 0;
+    for (int i = 0; i < 9; ++i) acc[k++] = S1[i];
+    for (int i = 0; i < 9; ++i)
+        for (int j = i; j < 9; ++j) acc[k++] = S2[i * 9 + j];
+    cudaError_t ce = cudaMemcpyAsync(h->acc, acc, sizeof(acc), cudaMemcpyHostToDevice, h->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
+    if (ce != cudaSuccess) return FLB_ERR_CUDA;
+    h->nsamp = n_samples;
+    return FLB_OK;
+}
+
 int flb_error_location(flb_lattice h, int64_t* node, int64_t* step) {
     if (!h) return FLB_ERR_ARG;
     DevError e;

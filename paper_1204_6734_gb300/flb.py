@@ -94,6 +94,8 @@ def load(build_if_missing: bool = True):
         "flb_step": (C.c_int, [h, C.c_int64]),
         "flb_sync": (C.c_int, [h]),
         "flb_time": (C.c_int, [h, _i64p]),
+        "flb_set_time": (C.c_int, [h, C.c_int64]),
+        "flb_set_raw_sums": (C.c_int, [h, _dp, _dp, C.c_int64]),
         "flb_error_location": (C.c_int, [h, _i64p, _i64p]),
         "flb_reset_error": (C.c_int, [h]),
         "flb_correlations": (C.c_int, [h, C.c_int32, _dp, _dp, _dp, _i64p]),
@@ -168,7 +170,7 @@ def exported_symbols():
             "flb_batch_get_populations", "flb_batch_set_populations", "flb_server_create",
             "flb_server_destroy", "flb_server_submit", "flb_server_poll", "flb_server_stats",
             "flb_server_set_tile", "flb_set_structure_sampling", "flb_structure_factors",
-            "flb_batch_correlations"]
+            "flb_batch_correlations", "flb_set_time", "flb_set_raw_sums"]
 
 
 def _check(rc: int, what: str):
@@ -252,6 +254,17 @@ def flb_step(h, n: int) -> None:
 
 def flb_sync(h) -> None:
     _check(load().flb_sync(h), "flb_sync")
+
+
+def flb_set_time(h, t: int) -> None:
+    _check(load().flb_set_time(h, int(t)), "flb_set_time")
+
+
+def flb_set_raw_sums(h, S1, S2, n_samples: int) -> None:
+    S1 = np.ascontiguousarray(S1, dtype=np.float64)
+    S2 = np.ascontiguousarray(S2, dtype=np.float64)
+    assert S1.size == 9 and S2.size == 81
+    _check(load().flb_set_raw_sums(h, _ptr(S1), _ptr(S2), int(n_samples)), "flb_set_raw_sums")
 
 
 def flb_time(h) -> int:
@@ -633,6 +646,19 @@ class Lattice:
 
     def raw_sums(self):
         return flb_raw_sums(self.h)
+
+    def checkpoint(self):
+        """(populations, t, (S1, S2, n)): what resume() needs to continue."""
+        return self.populations(), self.t, self.raw_sums()
+
+    def resume(self, state, warmup, every):
+        """Continue a checkpointed run on this handle (same parameters):
+        the sampling schedule, the sums, the time and the state."""
+        f, t, (S1, S2, n) = state
+        self.set_sampling(warmup, every)
+        flb_set_raw_sums(self.h, S1, S2, n)
+        flb_set_time(self.h, t)
+        self.set_populations(f)
 
     def set_structure_sampling(self, warmup, every):
         flb_set_structure_sampling(self.h, warmup, every)

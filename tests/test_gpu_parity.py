@@ -354,3 +354,30 @@ def test_full_size_sampled_nodes(basis, kernel):
             fs = oracle.collide_node(p, F0[:, ys_, xs_], int(xs_ + Lx * ys_), 20)
             err = max(err, abs(F1[i, y, x] - fs[i]))
     assert err < 2e-6
+
+
+@pytest.mark.parametrize("precision,basis", [("fp32", inputs.LOCAL), ("fp32", inputs.STANDARD),
+                                             ("fp64", inputs.LOCAL), ("fp16dev", inputs.LUT)])
+def test_checkpoint_resume_continues_exactly(precision, basis):
+    """A run checkpointed at t = 23 (state, time, raw sums) and resumed on a new
+    handle ends in the same state as the uninterrupted run (the noise counter
+    is the step), with the same sums up to FP64 summation order."""
+    p = inputs.LatticeParams(150, 41, 1.0, 0.1, -0.02, 1e-4, inputs.omega_groups(1.1, 0.8, 1.2), basis,
+                             precision, seed=77)
+    with flb.Lattice(p) as lat:
+        lat.set_sampling(5, 2)
+        lat.step(50)
+        f_ref, (S1r, S2r, nr) = lat.populations(), lat.raw_sums()
+    with flb.Lattice(p) as lat:
+        lat.set_sampling(5, 2)
+        lat.step(23)
+        state = lat.checkpoint()
+    with flb.Lattice(p) as lat:
+        lat.resume(state, 5, 2)
+        assert lat.t == 23
+        lat.step(27)
+        f, (S1, S2, n) = lat.populations(), lat.raw_sums()
+    np.testing.assert_array_equal(f, f_ref)
+    assert n == nr
+    np.testing.assert_allclose(S2, S2r, rtol=1e-12, atol=1e-12 * n * p.kT)
+    np.testing.assert_allclose(S1, S1r, rtol=1e-12, atol=1e-12 * n * np.sqrt(p.kT))
