@@ -221,6 +221,14 @@ int flb_structure_factors(flb_lattice h, double* S_rho, double* S_jx, double* R_
 int flb_run_host(const flb_params* p, const double* f_in, int64_t nsteps, int64_t warmup,
                  int64_t every, double* f_out, double* S1, double* S2, int64_t* n_samples);
 
+/* Failure detection, for testing: every wait of the pipelined kernels is
+ * bounded (about 2 s), after which the kernel records a timeout that the next
+ * flb_sync reports as FLB_ERR_TIMEOUT, and exits. Here one warp waits on a
+ * barrier that nothing completes, for limit_cycles (0 .. 4e9) SM cycles, on
+ * the legacy default stream: the call returns FLB_ERR_TIMEOUT without a
+ * fault or a hang, and the context stays usable. Synchronous. */
+int flb_wait_probe(int64_t limit_cycles);
+
 /* Noise draws of the device code, for testing: for each of n nodes, the six
  * 21-bit Philox fields and the six standard normals N^3..N^8 the step kernel
  * of the given precision (FLB_FP64 or FLB_FP32) uses at (seed, replica, node,

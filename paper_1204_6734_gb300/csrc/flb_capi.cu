@@ -995,4 +995,20 @@ int flb_collide_nodes(const flb_params* p, const double* g, const uint32_t* node
     return cuda_rc(ce);
 }
 
+int flb_wait_probe(int64_t limit_cycles) {
+    if (limit_cycles < 0 || limit_cycles > 4000000000LL) return FLB_ERR_ARG;
+    DevError* err = nullptr;
+    if (cudaMalloc(&err, sizeof(DevError)) != cudaSuccess) {
+        cudaGetLastError();
+        return FLB_ERR_OOM;
+    }
+    DevError e;
+    cudaError_t ce = cudaMemset(err, 0, sizeof(DevError));
+    if (ce == cudaSuccess) ce = wait_probe(limit_cycles, err, 0);
+    if (ce == cudaSuccess) ce = cudaMemcpy(&e, err, sizeof(e), cudaMemcpyDeviceToHost);
+    cudaFree(err);
+    if (ce != cudaSuccess) return FLB_ERR_CUDA;
+    return map_status(e.code);
+}
+
 }  // extern "C"

@@ -57,6 +57,10 @@ struct HArgs {
     const float* lut;       // velocity table (look-up-table f-norm only)
 };
 
+// One warp waits on an mbarrier nothing completes, for at most `limit` cycles
+// (<= the kernels' own bound), and records the timeout in err.
+cudaError_t wait_probe(long long limit, DevError* err, cudaStream_t s);
+
 // Tensor maps and launch shape of the FP16-store kernel; one step of it.
 cudaError_t fp16_plan(TmaPlan* plan, void* buf0, void* buf1, const Geometry& g);
 cudaError_t fp16_step(const TmaPlan& plan, int src, const HArgs& a, const CollideConst<float>& cc,

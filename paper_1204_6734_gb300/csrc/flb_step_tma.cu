@@ -332,6 +332,26 @@ step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
     }
 }
 
+// The bounded wait the pipelined kernels rely on, exercised alone: a warp
+// waits on an mbarrier that nothing completes, gives up after `limit` cycles
+// and records a timeout as a step kernel would (no fault, no hang).
+__global__ void wait_probe_kernel(long long limit, DevError* err) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const bool done = mbar_wait_for(&bar, 0, limit);
+    if (!done && threadIdx.x == 0) record_error(err, kStatusTimeout, -1, 0);
+}
+
+cudaError_t wait_probe(long long limit, DevError* err, cudaStream_t s) {
+    if (limit < 0 || limit > kWaitCycles) return cudaErrorInvalidValue;
+    wait_probe_kernel<<<1, 32, 0, s>>>(limit, err);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------

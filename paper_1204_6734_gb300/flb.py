@@ -95,6 +95,7 @@ def load(build_if_missing: bool = True):
         "flb_sync": (C.c_int, [h]),
         "flb_time": (C.c_int, [h, _i64p]),
         "flb_set_time": (C.c_int, [h, C.c_int64]),
+        "flb_wait_probe": (C.c_int, [C.c_int64]),
         "flb_set_raw_sums": (C.c_int, [h, _dp, _dp, C.c_int64]),
         "flb_error_location": (C.c_int, [h, _i64p, _i64p]),
         "flb_reset_error": (C.c_int, [h]),
@@ -170,7 +171,7 @@ def exported_symbols():
             "flb_batch_get_populations", "flb_batch_set_populations", "flb_server_create",
             "flb_server_destroy", "flb_server_submit", "flb_server_poll", "flb_server_stats",
             "flb_server_set_tile", "flb_set_structure_sampling", "flb_structure_factors",
-            "flb_batch_correlations", "flb_set_time", "flb_set_raw_sums"]
+            "flb_batch_correlations", "flb_set_time", "flb_set_raw_sums", "flb_wait_probe"]
 
 
 def _check(rc: int, what: str):
@@ -254,6 +255,12 @@ def flb_step(h, n: int) -> None:
 
 def flb_sync(h) -> None:
     _check(load().flb_sync(h), "flb_sync")
+
+
+def flb_wait_probe(limit_cycles: int) -> int:
+    """Return code of a bounded wait on a barrier nothing completes
+    (FLB_ERR_TIMEOUT expected)."""
+    return int(load().flb_wait_probe(int(limit_cycles)))
 
 
 def flb_set_time(h, t: int) -> None:
