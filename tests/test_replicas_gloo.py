@@ -58,3 +58,35 @@ def test_replica_streams_are_independent_draws():
 
 def test_single_rank_needs_no_process_group():
     assert replicas.max_over_ranks(3.25) == 3.25
+
+
+def _worker_failing(rank, world, port, out):
+    """Rank 1 fails before the end of the timed region (it returns without
+    joining the max over ranks, as a crashed rank would); rank 0 must get an
+    error from its collective within the group's timeout, not hang."""
+    import datetime
+    import time
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=5))
+    if rank == 1:
+        return
+    t0 = time.monotonic()
+    try:
+        replicas.max_over_ranks(1.0, dist)
+        out[rank] = ("no error", time.monotonic() - t0)
+    except Exception as e:   # the failure the surviving rank must see
+        out[rank] = (type(e).__name__, time.monotonic() - t0)
+
+
+@pytest.mark.timeout(120)
+def test_a_failed_rank_is_reported_not_waited_for():
+    world = 2
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_worker_failing, args=(world, _free_port(), out), nprocs=world, join=True)
+        res = dict(out)
+    kind, waited = res[0]
+    assert kind != "no error"
+    assert waited < 60
