@@ -5,12 +5,14 @@ TEST INFRASTRUCTURE. Only ``tests/``, ``__graft_entry__.smoke()`` and the
 ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
 package. The product (``paper_1204_6734_gb300``) never imports it, and it never
 imports the product: parameters are duck-typed objects with the attributes
-``Lx, Ly, rho0, ux0, uy0, kT, omega (9), basis ('standard'|'local'), seed,
-replica``.
+``Lx, Ly, rho0, ux0, uy0, kT, omega (9), basis ('standard'|'local'|'lut'),
+seed, replica``.
 
-The C part (``flb_oracle.c``) holds the method; the NumPy helpers here only
-reduce the sampled sums to covariances (Eq. dfidfj2dmadmb) with the oracle's
-own basis matrices.
+The C part (``flb_oracle.c``) holds the method; the NumPy helpers here reduce
+the sampled sums to covariances (Eq. dfidfj2dmadmb) with the oracle's own
+basis matrices, and form the static structure factors of Eqs. sfactorr,
+sfactoru, rcorrelator from the oracle's state (NumPy's forward FFT as the
+transform, pinned against the written-out double sum).
 """
 from __future__ import annotations
 
