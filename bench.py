@@ -799,7 +799,7 @@ def main():
                     "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                             "peak_kind": peak_kind}}
 
-    Cff, CMM, mean, ns = lat.correlations(args.basis)
+    Cff, CMM, mean, ns = lat.correlations("standard" if args.basis == "standard" else "local")
     lat.close()
 
     # end to end through the host-buffer entry point: upload the initial state
