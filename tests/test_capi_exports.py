@@ -60,3 +60,52 @@ def test_pure_host_entry_points():
     with pytest.raises(flb.FlbError):
         flb.flb_create(bad_omega)
     assert lib.flb_destroy(None) == 0
+
+
+def _compile_c_client(tmp_path):
+    """Build tests/helpers/capi_example.c with gcc as C99, linked to the library."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not found")
+    lib = build.build()
+    exe = str(tmp_path / "capi_example")
+    cmd = [gcc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"),
+           os.path.join(ROOT, "tests", "helpers", "capi_example.c"), "-o", exe,
+           "-L", os.path.dirname(lib), "-l:" + os.path.basename(lib), "-Wl,-rpath," + os.path.dirname(lib)]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    return exe
+
+
+def test_header_is_c99_and_links_from_c(tmp_path):
+    """The boundary is a C ABI: a C99 client compiles with warnings as errors
+    and links against the library (it is not run without a GPU)."""
+    assert os.path.exists(_compile_c_client(tmp_path))
+
+
+@pytest.mark.gpu
+def test_c_client_matches_the_binding(tmp_path):
+    import subprocess
+
+    import numpy as np
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    exe = _compile_c_client(tmp_path)
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    t, n, m, jx, jy, c00, cmm33 = r.stdout.split()
+    from paper_1204_6734_gb300 import inputs
+    p = inputs.LatticeParams(96, 40, 1.0, 0.1, 0.0, 1e-4, inputs.omega_groups(1.1, 0.8, 1.3), "local", "fp32",
+                             seed=2024)
+    with flb.Lattice(p) as lat:
+        lat.set_sampling(10, 1)
+        lat.step(50)
+        sums = lat.conservation()
+        Cff, CMM, _, nn = lat.correlations("local")
+    assert int(t) == 50 and int(n) == nn
+    np.testing.assert_allclose([float(m), float(jx), float(jy)], sums, rtol=1e-12, atol=1e-12)
+    assert float(c00) == pytest.approx(Cff[0, 0], rel=1e-9)
+    assert float(cmm33) == pytest.approx(CMM[3, 3], rel=1e-9)
