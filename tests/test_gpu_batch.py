@@ -245,7 +245,7 @@ def test_full_ensemble_sampled_replicas():
         np.testing.assert_allclose(S2, R2, rtol=1e-4, atol=1e-6 * n * ps[k].kT)
 
 
-@pytest.mark.parametrize("basis", BASES)
+@pytest.mark.parametrize("basis", ALL_BASES)
 def test_pooled_correlations(basis):
     """flb_batch_correlations over copies with one rho0, u0 (different seeds
     and sizes): the covariance of the pooled raw sums (the definition, Eqs.
@@ -274,7 +274,7 @@ def test_pooled_correlations(basis):
     C = S2 / ns - np.outer(mu, mu)
     np.testing.assert_allclose(mean, mu, rtol=1e-12, atol=1e-18)
     np.testing.assert_allclose(Cff, C, rtol=1e-9, atol=1e-9 * ps[0].kT)
-    m = oracle.local_basis(0.1, 0.0) if basis == inputs.LOCAL else oracle.tables()[3]
+    m = oracle.tables()[3] if basis == inputs.STANDARD else oracle.local_basis(0.1, 0.0)
     np.testing.assert_allclose(CMM, m @ C @ m.T, rtol=1e-7, atol=1e-9 * ps[0].kT)
     with flb.Lattice(ps[1], kernel="pipelined") as lat:
         lat.set_sampling(10, 2)
