@@ -3,8 +3,8 @@
 One benchmark step = one pass of the whole hot path over the 4096x4096 FP32
 lattice: pull streaming, density and velocity, the per-node basis, relaxation,
 Philox noise, back transform and store (the step kernel), with the equal-time
-correlation sums sampled on every step (fused into the step kernel) and reduced
-into the FP64 accumulators (second kernel). Inputs (two 604 MB population
+correlation sums sampled on every step and added to the FP64 accumulators, both
+inside the step kernel (one launch per step). Inputs (two 604 MB population
 buffers) are larger than L2 and stay resident in HBM.
 
 Prints one JSON line. Multi-GPU runs are independent replicas (one lattice per
