@@ -27,3 +27,23 @@ def test_fit_drift_recovers_a_pure_quadratic():
     us = [0.0, 0.05, 0.1, 0.2, 0.3]
     D = np.array([[1.7 * u * u, 0.5 * u * u] for u in us])
     np.testing.assert_allclose(bench.fit_drift(us, D), [1.7, 0.5], rtol=1e-12)
+
+
+def test_reference_arm_prints_the_contract_line():
+    """bench.py --impl reference (the oracle on the host cores) prints one JSON
+    line with the keys of the benchmark contract and the GPU arm's config."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "2",
+                        "--warmup", "1"], capture_output=True, text=True, timeout=600, cwd=root)
+    assert r.returncode == 0, r.stderr
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["value"] > 0 and line["steps"] == 2
+    assert line["config"]["Lx"] == 4096 and line["cpu_baseline"]["kind"] == "oracle"
+    assert line["e2e"]["h2d_bytes_per_step"] == 0
