@@ -457,12 +457,15 @@ int flb_set_option(flb_lattice h, int32_t option, int32_t value);
 
 /* The FP64 fused step with correlation sampling, for callers that cannot
  * allocate device memory. (The paper has no counterpart: this is an interface
- * for such callers.) Code that runs while a CUDA graph is being captured,
- * plugins whose host application owns every device allocation, and loops that
- * plan their memory ahead and cannot take the synchronisation of cudaMalloc
- * all fall in this group. The entry point calls no cudaMalloc, cudaFree or
- * allocating library routine.
- *  p        parameters; precision must be FLB_FP64; Lx*Ly <= 262144 nodes
+ * for such callers.) Plugins whose host application owns every device
+ * allocation through its own pool, and loops that plan their memory ahead and
+ * cannot take the synchronisation of cudaMalloc, fall in this group. The entry
+ * point calls no cudaMalloc, cudaFree or allocating library routine. It copies
+ * its sums to the host and synchronises the stream before it returns, so it
+ * cannot be recorded into a CUDA graph: a stream that is being captured is
+ * refused with FLB_ERR_ARG before anything is queued on it.
+ *  p        parameters, checked as flb_create checks them; precision must be
+ *           FLB_FP64, basis FLB_BASIS_STANDARD or FLB_BASIS_LOCAL; Lx*Ly <= 262144 nodes
  *           (larger lattices are rejected with FLB_ERR_ARG: the scratch below
  *           holds the partial sums of at most 1024 blocks of 256 nodes).
  *  dev_f    device array of 9*Lx*Ly doubles: on entry the pre-collision state
@@ -478,12 +481,13 @@ int flb_set_option(flb_lattice h, int32_t option, int32_t value);
  *  stream   cudaStream_t (as void*) or NULL; the call synchronises it.
  * Scratch: a fixed array of about 432 KB in this library's device memory, held
  * by every GPU that loads the library until the process exits. The first call
- * on a device looks up its address there (cudaGetSymbolAddress), so make that
- * first call before any stream capture. Every call shares the array and clears
+ * on a device looks up its address there (cudaGetSymbolAddress) with that
+ * device current. Every call shares the array and clears
  * the sums it needs at its start; calls that overlap on the GPU (other streams,
  * other host threads) race on it and must not be issued.
- * Errors: FLB_ERR_ARG, FLB_ERR_INVALID_VELOCITY / FLB_ERR_NONFINITE (a node
- * left the valid region; it was not collided), FLB_ERR_CUDA. */
+ * Errors: FLB_ERR_ARG (bad parameters, buffers, sizes, or a capturing stream),
+ * FLB_ERR_INVALID_VELOCITY / FLB_ERR_NONFINITE (a node left the valid region;
+ * it was not collided), FLB_ERR_CUDA. */
 int flb_step_noalloc(const flb_params* p, double* dev_f, double* dev_work, int64_t t0,
                      int64_t nsteps, double* host_S1, double* host_S2, void* stream);
 

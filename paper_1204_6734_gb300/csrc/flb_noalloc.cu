@@ -1,13 +1,15 @@
 // flb_noalloc.cu -- flb_step_noalloc: the FP64 fused step with correlation
 // sampling for callers that cannot allocate device memory.
 //
-// Some callers may not call cudaMalloc: code that runs while a CUDA graph is
-// being captured, plugins whose host application owns every device allocation
-// through its own pool, and real-time or serving loops that plan their memory
-// ahead of time and cannot take the implicit synchronisation of an allocation.
-// This entry point takes the two population buffers from the caller and keeps
-// its own scratch (per-block partial sums, the running sums, the error record)
-// in a fixed array in this file's device memory.
+// Some callers may not call cudaMalloc: plugins whose host application owns
+// every device allocation through its own pool, and real-time or serving loops
+// that plan their memory ahead of time and cannot take the implicit
+// synchronisation of an allocation. This entry point takes the two population
+// buffers from the caller and keeps its own scratch (per-block partial sums,
+// the running sums, the error record) in a fixed array in this file's device
+// memory. It ends by copying the sums to the host and synchronising the stream,
+// so it is not a call for a stream that is being captured: such a stream is
+// refused before anything is queued on it.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -16,6 +18,7 @@
 
 #include "../../include/flb.h"
 #include "flb_collide.cuh"
+#include "flb_host.h"
 #include "flb_kernels.cuh"
 
 namespace flb {
@@ -111,42 +114,35 @@ using namespace flb;
 extern "C" int flb_step_noalloc(const flb_params* p, double* dev_f, double* dev_work,
                                 int64_t t0, int64_t nsteps, double* host_S1, double* host_S2,
                                 void* stream) {
-    if (!p || !dev_f || !dev_work || dev_f == dev_work || t0 < 0 || nsteps < 0) return FLB_ERR_ARG;
+    // the checks flb_create makes, then this entry point's own limits
+    if (!valid_params(p)) return FLB_ERR_ARG;
+    if (!dev_f || !dev_work || dev_f == dev_work || t0 < 0 || nsteps < 0) return FLB_ERR_ARG;
     if (p->precision != FLB_FP64 || (p->basis != FLB_BASIS_STANDARD && p->basis != FLB_BASIS_LOCAL))
         return FLB_ERR_ARG;
-    if (p->Lx < 1 || p->Ly < 1) return FLB_ERR_ARG;
     const long long N = (long long)p->Lx * p->Ly;
     if (N > (long long)kNoallocThreads * kNoallocMaxBlocks) return FLB_ERR_ARG;
     if (t0 + nsteps > 0xFFFFFFFFLL) return FLB_ERR_ARG;
-    for (int a = 3; a < 9; ++a)
-        if (!(p->omega[a] > 0 && p->omega[a] < 2)) return FLB_ERR_ARG;
-    if (!(p->kT >= 0)) return FLB_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    // the call reads its results back and synchronises: refuse a stream under
+    // capture before queueing anything, so that the caller's capture survives
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return FLB_ERR_CUDA;
+    }
+    if (cap != cudaStreamCaptureStatusNone) return FLB_ERR_ARG;
 
     NoallocScratch* scratch = nullptr;
     int rc = scratch_on_current_device(&scratch);
     if (rc) return rc;
-    cudaStream_t s = (cudaStream_t)stream;
 
-    CollideConst<double> cc;
-    for (int a = 0; a < 6; ++a) {
-        const double om = p->omega[3 + a];
-        cc.nomega[a] = -om;
-        const double v = p->kT * om * (2.0 - om);
-        cc.amp[a] = v > 0 ? std::sqrt(v) : 0.0;
-    }
-    cc.key = make_noise_key(p->seed, p->replica);
+    const CollideConst<double> cc = collide_const<double>(p);
     Vec9 ref;
-    {
-        const double usq = p->ux0 * p->ux0 + p->uy0 * p->uy0;
-        for (int i = 0; i < 9; ++i) {
-            const double uv = p->ux0 * cvx(i) + p->uy0 * cvy(i);
-            const double wi = i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
-            ref.v[i] = p->rho0 * wi * (1.0 + 3.0 * uv + 4.5 * uv * uv - 1.5 * usq);
-        }
-    }
+    feq_host(p->rho0, p->ux0, p->uy0, ref.v);
 
     // the array keeps the previous call's contents: clear the sums and the error
-    cudaError_t ce = cudaMemsetAsync(scratch->acc, 0, sizeof(scratch->acc) + sizeof(DevError), s);
+    cudaError_t ce = cudaMemsetAsync(scratch->acc, 0, sizeof(scratch->acc), s);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(&scratch->err, 0, sizeof(DevError), s);
     const int blocks = (int)((N + kNoallocThreads - 1) / kNoallocThreads);
     double* in = dev_f;
     double* out = dev_work;
