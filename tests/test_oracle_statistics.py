@@ -5,20 +5,16 @@
   gas's (Eq. dfdf, scaled by kT): <df_i df_j> = kT rho0 w_i delta_ij, less the
   k = 0 contribution of the three exactly conserved modes (1/N of their share).
 * At u0 != 0 the Hermite-norm run drifts away from kT f_i^0(rho0,u0) while the
-  f-norm run stays close (Figs. 2-4 versus 12-14), and the quadratic drift of
-  the moment correlators matches the coefficients printed in Section 4
-  (tests/golden/paper_q_coefficients.json) within the looseness those numbers
-  carry (unstated relaxation rates, look-up-table variant).
+  f-norm run stays close (Figs. 2-4 versus 12-14). (The drift of the moment
+  correlators against the coefficients printed in Section 4 is pinned in
+  test_drift_fit.py.)
 """
-import json
-import os
 
 import numpy as np
 import pytest
 
 from paper_1204_6734_gb300 import inputs
 
-GOLD = os.path.join(os.path.dirname(__file__), "golden", "paper_q_coefficients.json")
 KT = 1e-4
 OMEGA = inputs.omega_groups(1.0, 0.8, 1.0)
 
@@ -55,25 +51,6 @@ def _drift(oracle, basis, u, seed):
     C, _ = run.covariance()
     CM = oracle.moment_covariance(C, basis, u, 0.0)
     return C, np.diag(CM) / KT - 1.0
-
-
-def test_galilean_drift_matches_printed_coefficients(oracle):
-    gold = json.load(open(GOLD))
-    idx = gold["moments"]
-    us = np.array([0.1, 0.15, 0.2, 0.25])
-    q = {}
-    for basis in ("standard", "local"):
-        d = np.array([_drift(oracle, basis, u, seed=40 + k)[1] for k, u in enumerate(us)])
-        # <dM^a dM^a> is even in u_x0, so l = 0 on the diagonal: fit d = q u^2
-        q[basis] = {name: float(np.sum(d[:, a] * us ** 2) / np.sum(us ** 4))
-                    for name, a in idx.items()}
-    for name in idx:
-        qh, qf = q["standard"][name], q["local"][name]
-        assert qh == pytest.approx(gold["q_hermite"][name], rel=0.3), (name, qh)
-        assert qf == pytest.approx(gold["q_fnorm"][name], rel=0.5), (name, qf)
-    # the f-norm reduces the drift of rho and Pi_xx-yy by more than 2x
-    assert q["standard"]["rho"] > 2.5 * q["local"]["rho"]
-    assert q["standard"]["Pi_xx-yy"] > 2 * q["local"]["Pi_xx-yy"]
 
 
 def test_fnorm_follows_f0_and_hermite_does_not(oracle):
