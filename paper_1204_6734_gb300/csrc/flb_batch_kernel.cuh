@@ -353,7 +353,7 @@ batch_step_kernel(const BatchArgs a) {
             const uint32_t nodeA = (uint32_t)xA + (uint32_t)geo.Lx * (uint32_t)y;
             f2 f[9];
             const uint32_t stt = collide_basis<f2, BASIS>(
-                g, [&](f2* N) { node_normals(hs.cc.key, nodeA, nodeA + TW / 2, tr, N); }, load,
+                g, PairNoise{hs.cc.key, nodeA, nodeA + TW / 2, tr}, load,
                 a.lut, hs.cc, f);
             __syncwarp();
             if (lane_id == 0) mbar_arrive(&empty[s]);
@@ -385,7 +385,7 @@ batch_step_kernel(const BatchArgs a) {
             const uint32_t node = (uint32_t)x + (uint32_t)geo.Lx * (uint32_t)y;
             float f[9];
             const uint32_t stt = collide_basis<float, BASIS>(
-                g, [&](float* N) { node_normals(hs.cc.key, node, tr, N); }, load, a.lut, hs.cc, f);
+                g, NodeNoise{hs.cc.key, node, tr}, load, a.lut, hs.cc, f);
             __syncwarp();
             if (lane_id == 0) mbar_arrive(&empty[s]);
             if (in) {

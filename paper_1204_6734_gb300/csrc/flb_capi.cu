@@ -212,7 +212,7 @@ __global__ void collide_nodes_kernel(const double* g, const uint32_t* ids, uint3
     for (int i = 0; i < 9; ++i) gg[i] = (T)g[k * 9 + i];
     const uint32_t id = ids[k];
     const int st = (int)(collide_basis<T, BASIS>(
-                             gg, [&](T* N) { node_normals(cc.key, id, step, N); },
+                             gg, NodeNoise{cc.key, id, step},
                              [&](T* g2) {
                                  for (int i = 0; i < 9; ++i) g2[i] = gg[i];
                              },
@@ -344,6 +344,9 @@ cudaError_t launch_step_tma(flb_lattice h, bool sample) {
     a.err = h->err;
     a.lut = h->lut32;
     for (int i = 0; i < 9; ++i) a.ref[i] = (float)h->ref[i];
+    a.s = tensor_sampling_ok(&h->p) ? gram_scale(&h->p) : 1.0;
+    a.sinv = (float)(1.0 / a.s);
+    for (int i = 0; i < 9; ++i) a.snref[i] = (float)(-h->ref[i] / a.s);
     const TmaPlan& plan = !sample && h->tma_quiet.ready ? h->tma_quiet : h->tma;
     return tma_step(plan, h->cur, a, collide_const<float>(&h->p), h->p.basis, sample, h->stream);
 }
@@ -460,13 +463,16 @@ int lattice_create(const flb_params* p, void* dev_workspace, size_t workspace_by
         ce = cudaGetLastError();
     }
     if (ce == cudaSuccess && sync) ce = cudaStreamSynchronize(h->stream);
-    h->tma.sample_mode = 0;   // library default
+    // sampling steps: the correlation sums on the tensor cores, 12 colliding
+    // warps, where the parameters allow it; otherwise the sampler warps
+    const bool tensor = tensor_sampling_ok(p);
+    h->tma.sample_mode = tensor ? kPlanTensorSampling : 0;
     if (ce == cudaSuccess && p->basis == FLB_BASIS_LOCAL_LUT &&
         lut_tables(&h->lut32, &h->lut64) != FLB_OK)
         ce = cudaErrorUnknown;
     h->tma_quiet.ready = false;
     if (ce == cudaSuccess && p->precision == FLB_FP32) {
-        ce = tma_plan(&h->tma, h->buf[0], h->buf[1], h->geo, 0);
+        ce = tma_plan(&h->tma, h->buf[0], h->buf[1], h->geo, tensor ? kTensorNW : 0);
         // steps without sampling in the f-norm bases: 12 colliding warps
         // (measured 56.7 against 53.5 GLUPS at 4096^2; the Hermite norm and
         // sampling steps are faster with 8)
@@ -654,8 +660,16 @@ int flb_set_option(flb_lattice h, int32_t option, int32_t value) {
         return FLB_OK;
     }
     if (option == FLB_OPT_PIPELINE_SAMPLING) {
-        if (h->p.precision != FLB_FP32 || (value != 1 && value != 2)) return FLB_ERR_ARG;
-        h->tma.sample_mode = value;
+        if (h->p.precision != FLB_FP32 || value < 1 || value > 3) return FLB_ERR_ARG;
+        if (value == kPlanTensorSampling && !tensor_sampling_ok(&h->p)) return FLB_ERR_ARG;
+        TmaPlan plan = h->tma;
+        plan.sample_mode = value;
+        const cudaError_t ce = tma_plan(&plan, h->buf[0], h->buf[1], h->geo, h->tma.nw);
+        if (ce != cudaSuccess || plan.sample_mode != value) {
+            cudaGetLastError();
+            return FLB_ERR_ARG;
+        }
+        h->tma = plan;
         return FLB_OK;
     }
     if (option == FLB_OPT_PIPELINE_WARPS) {
@@ -667,6 +681,7 @@ int flb_set_option(flb_lattice h, int32_t option, int32_t value) {
             cudaGetLastError();
             return FLB_ERR_ARG;
         }
+        if (plan.sample_mode == kPlanTensorSampling && !tensor_sampling_ok(&h->p)) return FLB_ERR_ARG;
         h->tma = plan;
         h->tma_quiet.ready = false;   // the given count for every step
         return FLB_OK;

@@ -2,8 +2,8 @@
 // float) or two nodes (V = f2), in the Hermite norm (BASIS 0) or the f-norm
 // (BASIS 1). The algebra is described at the top of flb_device.cuh; here it is
 // arranged so that every subtraction folds into a fused multiply-add:
-//  * the Gram matrix is evaluated negated (Gn = -G_NN) and so is the Schur
-//    complement (Sn = -S = Gn + e e^T + k1 k1^T + k2 k2^T);
+//  * the Schur complement S of the conserved block is evaluated negated
+//    (Sn = -S), each entry a closed-form polynomial in the velocity;
 //  * the Cholesky factor is stored negated (Ln = -L'): the products Ln Ln = L L
 //    keep their sign, so the factorisation and both triangular solves are
 //    chains of fma(Ln, ., .) followed by one scaling with 1/L'_jj.
@@ -12,6 +12,8 @@
 // so this holds iff every pivot of S is positive, i.e. iff all six 1/sqrt(pivot)
 // are finite. The kernel checks their sum.
 #pragma once
+
+#include <type_traits>
 
 #include "flb_device.cuh"
 #include "flb_vec.cuh"
@@ -58,11 +60,100 @@ __device__ __forceinline__ void node_normals(const NoiseKey& key, uint32_t nodeA
     for (int q = 0; q < 6; ++q) n[q] = f2(a[q], b[q]);
 }
 
-// Status per lane: bits [8k, 8k+8) hold the kStatus* code of lane k.
+// The six noise increments xi^a N^a = sqrt(rho) amp_a N^a (Eqs. FDT, noiseamp)
+// of the FP32 collisions, with sqrt(rho) and amp_a folded into the Box-Muller
+// radius: rho (-2 ln u1) is formed before the square root, with
+// -2 ln u1 = 2 ln2 (21 - log2(k + 1)) for u1 = (k + 1) 2^-21. One node (scalar
+// lanes) or a node pair (packed lanes) take the same operations per lane, so
+// both give bit-identical increments. FP64 uses unit normals (operator()).
+constexpr float kLn2x2 = 1.3862943611198906f;
+
+__device__ __forceinline__ float bm_radius2(uint32_t k) {
+    return fmaf(__log2f((float)(k + 1u)), -kLn2x2, 21.f * kLn2x2);
+}
+__device__ __forceinline__ float bm_angle(uint32_t k) {
+    return (float)((int)k - (1 << 20)) * (float)(kTwoPi * 0x1p-21);
+}
+
+struct NodeNoise {
+    const NoiseKey& key;
+    uint32_t node, step;
+    template <class T>
+    __device__ __forceinline__ void operator()(T n[6]) const {
+        node_normals(key, node, step, n);
+    }
+    __device__ __forceinline__ void scaled(float rho, const float (&amp)[6], float n[6]) const {
+        uint32_t k[6];
+        node_fields(key, node, step, k);
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+            const float r = sqr(bm_radius2(k[2 * p]) * rho);
+            float s, c;
+            __sincosf(bm_angle(k[2 * p + 1]), &s, &c);
+            // cos(t + pi) = -cos t, sin(t + pi) = -sin t
+            n[2 * p] = (r * -amp[2 * p]) * c;
+            n[2 * p + 1] = (r * -amp[2 * p + 1]) * s;
+        }
+    }
+};
+
+struct PairNoise {
+    const NoiseKey& key;
+    uint32_t nodeA, nodeB, step;
+    __device__ __forceinline__ void scaled(f2 rho, const float (&amp)[6], f2 n[6]) const {
+        uint32_t ka[6], kb[6];
+        node_fields(key, nodeA, step, ka);
+        node_fields(key, nodeB, step, kb);
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+            const f2 lg(__log2f((float)(ka[2 * p] + 1u)), __log2f((float)(kb[2 * p] + 1u)));
+            const f2 r = sqr(mad(lg, f2(-kLn2x2), f2(21.f * kLn2x2)) * rho);
+            const f2 t = f2((float)((int)ka[2 * p + 1] - (1 << 20)),
+                            (float)((int)kb[2 * p + 1] - (1 << 20))) * f2((float)(kTwoPi * 0x1p-21));
+            float sa, ca, sb, cb;
+            __sincosf(t.v.x, &sa, &ca);
+            __sincosf(t.v.y, &sb, &cb);
+            n[2 * p] = (r * f2(-amp[2 * p])) * f2(ca, cb);
+            n[2 * p + 1] = (r * f2(-amp[2 * p + 1])) * f2(sa, sb);
+        }
+    }
+};
+
+// xi^a N^a, a = 3..8: FP32 folds the amplitudes into the draw (NodeNoise,
+// PairNoise); FP64 scales unit normals (the arithmetic of the oracle's order).
+template <class V, class Noise>
+__device__ __forceinline__ void noise_increments(Noise& noise, V rho,
+                                                 const CollideConst<typename Elem<V>::type>& cc,
+                                                 V xi[6]) {
+    if constexpr (!std::is_same<V, double>::value) {
+        noise.scaled(rho, cc.amp, xi);
+    } else {
+        V N[6];
+        noise(N);
+        const V sr = sqr(rho);
+#pragma unroll
+        for (int a = 0; a < 6; ++a) xi[a] = (sr * N[a]) * V(cc.amp[a]);
+    }
+}
+
+// True when every lane has a finite positive density and (f-norm) a basis:
+// the common case, decided with one test instead of per-lane status codes.
+__device__ __forceinline__ bool all_ok(double rho, double invsum) {
+    return rho > 0 && rho < INFINITY && invsum < INFINITY;
+}
+__device__ __forceinline__ bool all_ok(float rho, float invsum) {
+    return rho > 0.f && rho < INFINITY && invsum < INFINITY;
+}
+__device__ __forceinline__ bool all_ok(f2 rho, f2 invsum) {
+    return fminf(rho.v.x, rho.v.y) > 0.f && fmaxf(rho.v.x, rho.v.y) < INFINITY &&
+           invsum.v.x + invsum.v.y < INFINITY;
+}
+
 __device__ __forceinline__ double rsq_neg(double x) { return rsq(-x); }
 __device__ __forceinline__ float rsq_neg(float x) { return rsq(-x); }
 __device__ __forceinline__ f2 rsq_neg(f2 a) { return f2(rsq(-a.v.x), rsq(-a.v.y)); }
 
+// Status per lane: bits [8k, 8k+8) hold the kStatus* code of lane k.
 template <class V>
 __device__ __forceinline__ uint32_t lane_status(V rho, V invsum, bool local) {
     uint32_t st = 0;
@@ -186,15 +277,13 @@ __device__ __forceinline__ uint32_t collide(const V g[9], Noise noise, Refetch r
     M[3] = mad(cx, V(S(kSqrt6)), d13 * V(S(-kSqrt3h)));
     M[4] = mad(cy, V(S(kSqrt6)), d24 * V(S(-kSqrt3h)));
     M[5] = mad(g[0], V(S(0.5)), c * V(S(2))) - s1234;
-    const V sr = sqr(rho);
 
     if (BASIS == 0) {
         // Hermite norm: D_a = -omega_a (M^a - M^{a,0}) + xi^a N^a, f* = g + w (.) P^T D
-        V N[6];
-        noise(N);
         V Dn[6];
+        noise_increments(noise, rho, cc, Dn);
 #pragma unroll
-        for (int a = 0; a < 6; ++a) Dn[a] = mad(V(cc.nomega[a]), M[a], (sr * N[a]) * V(cc.amp[a]));
+        for (int a = 0; a < 6; ++a) Dn[a] = mad(V(cc.nomega[a]), M[a], Dn[a]);
         V h[9];
         hermite_back<V, false>(V(S(0)), V(S(0)), V(S(0)), Dn, h);
         V gg[9];
@@ -204,6 +293,7 @@ __device__ __forceinline__ uint32_t collide(const V g[9], Noise noise, Refetch r
         for (int i = 1; i <= 4; ++i) f[i] = mad(h[i], V(S(1.0 / 9.0)), gg[i]);
 #pragma unroll
         for (int i = 5; i <= 8; ++i) f[i] = mad(h[i], V(S(1.0 / 36.0)), gg[i]);
+        if (all_ok(rho, V(S(0)))) return 0;
         const uint32_t st = lane_status(rho, rho, false);
         keep_invalid(st, gg, f);
         return st;
@@ -227,45 +317,42 @@ __device__ __forceinline__ uint32_t collide(const V g[9], Noise noise, Refetch r
         k2[4] = uxx * V(S(kSqrt2x3h));
     };
 
-    // Sn = -(G_NN - e e^T - k1 k1^T - k2 k2^T), upper triangle
+    // Sn = -S, S = G_NN - e e^T - k1 k1^T - k2 k2^T (upper triangle), in
+    // closed form: with X = ux^2, Y = uy^2, Z = ux uy, Q = X + Y, D = X - Y the
+    // entries are short polynomials (the rank-3 update cancels most terms of
+    // G_NN), e.g. S_00 = 1 - 9Q/4 + 27/4 D^2 (1 - Q), S_22 = 1 - 9Q/4 + 27/4 Q^2 (1 - Q),
+    // S_01 = 27/2 Z D (1 - Q), S_55 = 1 + 3Q/2.
     V Sn[6][6];
     {
-        const V r6x = ux * V(S(kSqrt6h));
-        const V n6x = ux * V(S(-kSqrt6)), n6y = uy * V(S(-kSqrt6));
-        const V g00 = mad(usq, V(S(-0.75)), V(S(-1)));
-        const V n6xy = uxy * V(S(-6));
-        Sn[0][0] = g00;
-        Sn[0][1] = V(S(0));
-        Sn[0][2] = t3 * V(S(-0.75));
-        Sn[0][3] = r6x;
-        Sn[0][4] = uy * V(S(-kSqrt6h));
+        const V Z2 = uxy * uxy, D2 = t3 * t3, Q2 = usq * usq;
+        const V nv = mad(usq, V(S(6.75)), V(S(-6.75)));      // -27/4 (1 - Q)
+        const V nv2 = mad(usq, V(S(13.5)), V(S(-13.5)));     // -27/2 (1 - Q)
+        const V nc1 = mad(usq, V(S(2.25)), V(S(-1)));        // -(1 - 9Q/4)
+        const V nw = mad(usq, V(S(-27)), V(S(18)));
+        const V ax = ux * V(S(kSqrt6 / 4)), ay = uy * V(S(kSqrt6 / 4));
+        Sn[0][0] = mad(D2, nv, nc1);
+        Sn[2][2] = mad(Q2, nv, nc1);
+        Sn[0][1] = (uxy * t3) * nv2;
+        Sn[1][1] = mad(Z2 + Z2, nv2, V(S(-1)));
+        Sn[1][2] = (uxy * usq) * nv2;
+        Sn[0][2] = (t3 * V(S(2.25))) * mad(mad(usq, V(S(3)), V(S(-3))), usq, V(S(1)));
         Sn[0][5] = t3 * V(S(1.5));
-        Sn[1][1] = mad(usq, V(S(-3)), V(S(-1)));
-        Sn[1][2] = n6xy;
-        Sn[1][3] = n6y;
-        Sn[1][4] = n6x;
-        Sn[1][5] = n6xy;
-        Sn[2][2] = g00;
-        Sn[2][3] = ux * V(S(-kSqrt6h));
-        Sn[2][4] = Sn[0][4];
+        Sn[1][5] = uxy * V(S(-6));
         Sn[2][5] = ne5;
-        Sn[3][3] = mad(uxx, V(S(-3)), mad(uyy, V(S(-1.5)), V(S(-1))));
-        Sn[3][4] = n6xy;
-        Sn[3][5] = n6x;
-        Sn[4][4] = mad(uxx, V(S(-1.5)), mad(uyy, V(S(-3)), V(S(-1))));
-        Sn[4][5] = n6y;
+        Sn[3][5] = ux * V(S(-kSqrt6));
+        Sn[4][5] = uy * V(S(-kSqrt6));
         Sn[5][5] = mad(usq, V(S(-1.5)), V(S(-1)));
-        const V e[3] = {ne3, ne4, ne5};   // e_a e_b = ne_a ne_b
-        V k1[5], k2[5];
-        rows(k1, k2);
-#pragma unroll
-        for (int a = 0; a < 5; ++a)
-#pragma unroll
-            for (int b = a; b < 5; ++b) {
-                V s = mad(k1[a], k1[b], mad(k2[a], k2[b], Sn[a][b]));
-                if (b < 3) s = mad(e[a], e[b], s);
-                Sn[a][b] = s;
-            }
+        Sn[3][4] = uxy * mad(usq, V(S(9)), V(S(-6)));
+        Sn[3][3] = mad(uyy, mad(uyy, V(S(4.5)), mad(uxx, V(S(18)), V(S(-1.5)))),
+                       mad(uxx, V(S(-3)), V(S(-1))));
+        Sn[4][4] = mad(uxx, mad(uxx, V(S(4.5)), mad(uyy, V(S(18)), V(S(-1.5)))),
+                       mad(uyy, V(S(-3)), V(S(-1))));
+        Sn[0][3] = ax * mad(uyy, mad(t3, V(S(-27)), V(S(-6))), V(S(2)));
+        Sn[0][4] = ay * mad(uxx, mad(t3, V(S(-27)), V(S(6))), V(S(-2)));
+        Sn[1][3] = ay * mad(Z2, V(S(-54)), mad(uxx, V(S(12)), mad(uyy, V(S(6)), V(S(-4)))));
+        Sn[1][4] = ax * mad(Z2, V(S(-54)), mad(uyy, V(S(12)), mad(uxx, V(S(6)), V(S(-4)))));
+        Sn[2][3] = ax * mad(uyy, nw, V(S(-2)));
+        Sn[2][4] = ay * mad(uxx, nw, V(S(-2)));
     }
 
     // Cholesky of S with the factor stored negated: Ln = -L'
@@ -296,11 +383,10 @@ __device__ __forceinline__ uint32_t collide(const V g[9], Noise noise, Refetch r
         y[j] = s * inv[j];
     }
     // increments: relaxation towards M~^{a,0} = 0 (Eq. fnormmeq) plus noise
-    V N[6];
-    noise(N);
     V z[6];
+    noise_increments(noise, rho, cc, z);
 #pragma unroll
-    for (int a = 0; a < 6; ++a) z[a] = mad(V(cc.nomega[a]), y[a], (sr * N[a]) * V(cc.amp[a]));
+    for (int a = 0; a < 6; ++a) z[a] = mad(V(cc.nomega[a]), y[a], z[a]);
     // D_N = L'^{-T} z
 #pragma unroll
     for (int j = 5; j >= 0; --j) {
@@ -342,6 +428,7 @@ __device__ __forceinline__ uint32_t collide(const V g[9], Noise noise, Refetch r
     refetch(gg);
 #pragma unroll
     for (int i = 0; i < 9; ++i) f[i] = mad(W[i], h[i], gg[i]);
+    if (all_ok(rho, invsum)) return 0;
     const uint32_t st = lane_status(rho, invsum, true);
     keep_invalid(st, gg, f);
     return st;
@@ -468,9 +555,8 @@ __device__ __forceinline__ uint32_t collide_lut(const V g[9], Noise noise,
         d[8] = g[8] - (tm + rm);
         d[6] = g[6] - (tm - rm);
     }
-    V N[6];
-    noise(N);
-    const V sr = sqr(rho);
+    V xi[6];
+    noise_increments(noise, rho, cc, xi);
     V h[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) h[i] = V(S(0));
@@ -481,7 +567,7 @@ __device__ __forceinline__ uint32_t collide_lut(const V g[9], Noise noise,
         V y = row[0] * d[0];
 #pragma unroll
         for (int i = 1; i < 9; ++i) y = mad(row[i], d[i], y);
-        const V D = mad(V(cc.nomega[a]), y, (sr * N[a]) * V(cc.amp[a]));
+        const V D = mad(V(cc.nomega[a]), y, xi[a]);
 #pragma unroll
         for (int i = 0; i < 9; ++i) h[i] = mad(row[i], D, h[i]);
     }

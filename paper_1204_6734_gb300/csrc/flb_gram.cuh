@@ -1,0 +1,115 @@
+// flb_gram.cuh -- the equal-time correlation sums of the nodes a warp collides,
+// accumulated on the tensor cores.
+//
+// The sums S1_i = sum_x d_i(x) and S2_ij = sum_x d_i(x) d_j(x) of the centred
+// pre-collision populations d = f - f^0(rho0, u0) (Eqs. dfdef, efif0) are one
+// Gram matrix: with H the 16 x K matrix whose rows 0..8 hold d_i / s over K
+// nodes, row 9 holds ones and rows 10..15 zeros, C = H H^T has
+// C_ij = S2_ij / s^2 and C_i9 = S1_i / s. A warp stages its 64 nodes (two per
+// thread) as FP16 (round to nearest) in a 16 x 64 shared-memory block
+// (gram_stage), loads the block back in the fragment layout of mma.m16n8k16
+// with ldmatrix and accumulates C in FP32 registers, 8 per thread (gram_mma);
+// every kGramFlushTiles tiles the FP32 partials are added to an FP64 16 x 16
+// matrix in shared memory (gram_flush).
+//
+// The scale s (sqrt(kT rho0)) makes the thermal fluctuations of order one in
+// FP16, whose rounding (relative 2^-12, unbiased) enters the sums as noise
+// far below their statistical error; it is chosen by the host only where
+// every deviation a valid state can hold stays in FP16's range, and the
+// sampler-warp path (FP32 products) is used otherwise.
+#pragma once
+
+#include <cuda_fp16.h>
+
+#include <cstdint>
+
+#include "flb_tma.cuh"
+#include "flb_vec.cuh"
+
+namespace flb {
+
+constexpr int kGramRowHalves = 72;                       // 64 nodes + 8 halves: 144-byte rows
+constexpr int kGramWarpHalves = 16 * kGramRowHalves;     // one warp's block: 2304 bytes
+constexpr int kGramFlushTiles = 16;                      // FP32 partials of <= 1024 products
+
+// Constant rows of a warp's block: row 9 ones, rows 10..15 zeros.
+__device__ __forceinline__ void gram_init(__half* blk) {
+    const int lane = threadIdx.x & 31;
+    uint32_t* w = reinterpret_cast<uint32_t*>(blk);
+#pragma unroll
+    for (int r = 9; r < 16; ++r) w[r * (kGramRowHalves / 2) + lane] = r == 9 ? 0x3C003C00u : 0u;
+}
+
+__device__ __forceinline__ void mma16816(float (&c)[8], int o, uint32_t a0, uint32_t a1,
+                                         uint32_t a2, uint32_t a3, uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(c[o]), "+f"(c[o + 1]), "+f"(c[o + 2]), "+f"(c[o + 3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// Stage the 64 nodes of this warp (h: node A of the thread in .x, node B in .y,
+// already scaled by 1/s and zero for nodes outside the lattice) in the block
+// at shared address blk: thread `lane` owns columns 2 lane (A) and 2 lane + 1
+// (B). The warp must have finished reading the block's previous contents.
+__device__ __forceinline__ void gram_stage(uint32_t blk, const f2 (&h)[9]) {
+    const uint32_t w = blk + 4u * (threadIdx.x & 31);
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const __half2 v = __floats2half2_rn(h[i].v.x, h[i].v.y);
+        asm volatile("st.shared.b32 [%0], %1;" ::"r"(w + 2u * kGramRowHalves * i),
+                     "r"(*reinterpret_cast<const uint32_t*>(&v)));
+    }
+}
+
+// Add the staged block to c: four 16-node steps of two mma.m16n8k16 each.
+__device__ __forceinline__ void gram_mma(uint32_t blk, float (&c)[8]) {
+    __syncwarp();
+    // ldmatrix.x4: threads 8m..8m+7 address the rows of matrix m; matrices
+    // (rows 0-7, k 0-7), (rows 8-15, k 0-7), (rows 0-7, k 8-15), (rows 8-15,
+    // k 8-15) of each 16-node step are the A fragment, and H^T's B fragments of
+    // the column blocks 0-7 and 8-15 are matrices (0, 2) and (1, 3).
+    const int lane = threadIdx.x & 31, m = lane >> 3, r = lane & 7;
+    const uint32_t a = blk + 2u * (((m & 1) * 8 + r) * kGramRowHalves + (m >> 1) * 8);
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        uint32_t d0, d1, d2, d3;
+        asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                     : "=r"(d0), "=r"(d1), "=r"(d2), "=r"(d3)
+                     : "r"(a + 32u * s));
+        mma16816(c, 0, d0, d1, d2, d3, d0, d2);
+        mma16816(c, 4, d0, d1, d2, d3, d1, d3);
+    }
+}
+
+// Add the FP32 partials to the FP64 matrix cm[16][16] (rows and columns 0..9
+// only) and clear them. Fragment of thread (g, q) = (lane / 4, lane % 4):
+// c[0..3] = C[g][2q], C[g][2q+1], C[g+8][2q], C[g+8][2q+1]; c[4..7] the same
+// with the columns + 8.
+__device__ __forceinline__ void gram_flush(float (&c)[8], double* cm) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int row = g + ((k & 2) ? 8 : 0);
+        const int col = 2 * q + (k & 1) + ((k & 4) ? 8 : 0);
+        if (row < 10 && col < 10) atomicAdd(&cm[row * 16 + col], (double)c[k]);
+        c[k] = 0.f;
+    }
+}
+
+// Sum q of the kSums layout (9 first moments, then the upper triangle of the
+// second moments row by row) from the FP64 Gram matrix: S1_i = s C[i][9],
+// S2_ij = s^2 C[i][j].
+__device__ __forceinline__ double gram_sum(const double* cm, int q, double s) {
+    if (q < 9) return s * cm[q * 16 + 9];
+    int k = q - 9, i = 0;
+    while (k >= 9 - i) {
+        k -= 9 - i;
+        ++i;
+    }
+    return s * s * cm[i * 16 + i + k];
+}
+
+}  // namespace flb

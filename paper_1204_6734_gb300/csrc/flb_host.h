@@ -63,6 +63,16 @@ CollideConst<T> collide_const(const flb_params* p) {
     return cc;
 }
 
+// Scale s of the tensor-core correlation sums (the nodes are staged as
+// (f - f^0(rho0, u0)) / s in FP16): s = sqrt(kT rho0) makes the thermal
+// fluctuations of order one. Used only where a deviation as large as a few
+// rho0 stays far inside FP16's range (|d| / s <= 4 sqrt(rho0 / kT) <= 16000);
+// otherwise, and at kT = 0, the sums are taken with FP32 products.
+inline bool tensor_sampling_ok(const flb_params* p) {
+    return p->kT > 0 && std::sqrt(p->rho0 / p->kT) <= 4000.0;
+}
+inline double gram_scale(const flb_params* p) { return std::sqrt(p->kT * p->rho0); }
+
 inline int grid_for(long long n) {
     long long b = (n + 255) / 256;
     if (b > 4096) b = 4096;

@@ -19,7 +19,14 @@ struct TmaArgs {
     DevError* err;
     const float* lut;       // velocity table (look-up-table f-norm only)
     float ref[9];           // f^0(rho0, u0) subtracted before sampling
+    // tensor-core sampling: nodes are staged as h = (f - ref) / s in FP16
+    float sinv;             // 1 / s
+    float snref[9];         // -ref / s
+    double s;               // s (the sums are rescaled in FP64)
 };
+
+constexpr int kPlanTensorSampling = 3;   // TmaPlan::sample_mode of the tensor-core sums
+constexpr int kTensorNW = 12;            // colliding warps of the tensor-sampling plan
 
 struct TmaPlan {
     CUtensorMap map[2];     // source tensor maps of buffer 0 and buffer 1
@@ -27,7 +34,8 @@ struct TmaPlan {
     int grid;               // persistent CTAs
     size_t smem;            // dynamic shared memory per CTA
     int tiles_x, ntiles;
-    int sample_mode;        // sampling steps: 1 sampler warps, 2 fused into the consumers
+    int sample_mode;        // sampling steps: 1 sampler warps, 2 fused into the consumers,
+                            // 3 tensor-core Gram sums in the consumers
     bool ready;
 };
 

@@ -109,7 +109,7 @@ step_kernel(StepArgs<T> a, CollideConst<T> cc) {
         }
         T f[9];
         const uint32_t st = collide_basis<T, BASIS>(
-            g, [&](T* N) { node_normals(cc.key, (uint32_t)n, a.step, N); },
+            g, NodeNoise{cc.key, (uint32_t)n, a.step},
             [&](T* gg) {
 #pragma unroll
                 for (int i = 0; i < 9; ++i) gg[i] = g[i];

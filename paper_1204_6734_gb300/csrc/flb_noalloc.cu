@@ -90,7 +90,7 @@ noalloc_step_kernel(const double* fin, double* fout, int Lx, int Ly, uint32_t st
             for (int j = i; j < 9; ++j) s[k++] = d[i] * d[j];
         }
         const uint32_t st = collide<double, BASIS>(
-            g, [&](double* Nn) { node_normals(cc.key, (uint32_t)n, step, Nn); }, cc, f);
+            g, NodeNoise{cc.key, (uint32_t)n, step}, cc, f);
         if (st != kStatusOk) record_error(&scratch->err, (int)(st & 0xFF), n, step);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {

@@ -222,7 +222,7 @@ step_fp16_kernel(const __grid_constant__ CUtensorMap map, const HArgs a,
         const uint32_t nodeA = (uint32_t)xA + (uint32_t)Lx * (uint32_t)y;
         f2 f[9];
         const uint32_t stt = collide_basis<f2, BASIS>(
-            g, [&](f2* N) { node_normals(cc.key, nodeA, nodeA + 64u, a.step, N); }, load, a.lut, cc, f);
+            g, PairNoise{cc.key, nodeA, nodeA + 64u, a.step}, load, a.lut, cc, f);
         __syncwarp();
         if (lane_id == 0) mbar_arrive(&empty[s]);
         if (stt) {

@@ -22,6 +22,7 @@
 #include <cstring>
 
 #include "flb_collide.cuh"
+#include "flb_gram.cuh"
 #include "flb_internal.h"
 #include "flb_pipeline.cuh"
 #include "flb_tma.cuh"
@@ -130,13 +131,30 @@ __device__ __forceinline__ void add_sums(float (&v)[kSums], const f2 (&d)[9]) {
 }
 
 // Sampling modes of the pipelined step.
-enum : int { kNoSampling = 0, kSamplerWarps = 1, kFusedSampling = 2 };
+enum : int { kNoSampling = 0, kSamplerWarps = 1, kFusedSampling = 2, kTensorSampling = 3 };
+
+// With 16 colliding warps the producer is thread 0 of the first colliding warp
+// (a 17th warp would cap every thread at 96 registers: one sub-partition would
+// hold five warps); it refills the stage of the tile before the one it has just
+// finished, which every warp has normally released by then.
+template <int NW, int MODE>
+constexpr bool embedded_producer() {
+    return NW >= 16 && (MODE == kNoSampling || MODE == kTensorSampling);
+}
 
 template <int MODE>
 struct WarpCount {
     template <int NW>
-    static constexpr int extra() { return MODE == kSamplerWarps ? kSamplers : (MODE == kFusedSampling ? 0 : 1); }
+    static constexpr int extra() {
+        return MODE == kSamplerWarps ? kSamplers
+                                     : (MODE == kFusedSampling || embedded_producer<NW, MODE>() ? 0 : 1);
+    }
 };
+
+// Shared memory of the tensor-sampling mode beyond the ring and the reduction
+// buffer: one Gram block per colliding warp.
+template <int NW>
+constexpr size_t gram_smem_bytes() { return (size_t)NW * kGramWarpHalves * sizeof(__half); }
 
 // Warp roles. kNoSampling: NW consumer warps + one producer warp.
 // kSamplerWarps: NW consumers + kSamplers sampler warps (sampler w reads rows
@@ -144,6 +162,8 @@ struct WarpCount {
 // sums in packed registers); the first sampler lane produces.
 // kFusedSampling: NW consumers that also accumulate the sums of their own
 // nodes; lane 0 of warp 0 produces.
+// kTensorSampling: NW consumers that accumulate the sums of their own nodes as
+// a Gram matrix on the tensor cores (flb_gram.cuh) + one producer warp.
 template <int BASIS, int MODE, int NW>
 __global__ void __launch_bounds__((NW + WarpCount<MODE>::template extra<NW>()) * 32, 1)
 step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
@@ -157,6 +177,9 @@ step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * TS::STAGE);
     uint64_t* empty = full + kStages;
     double* red = reinterpret_cast<double*>(empty + kStages);
+    constexpr bool kTensor = MODE == kTensorSampling;
+    // tensor sampling: FP64 Gram matrix (16 x 16) in red, the warps' blocks after it
+    __half* gram = reinterpret_cast<__half*>(red + TS::RED * kSums);
 
     const int warp = threadIdx.x >> 5, lane_id = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -166,11 +189,16 @@ step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
         }
         fence_mbar_init();
     }
+    if (kTensor) {
+        if (threadIdx.x < 256) red[threadIdx.x] = 0.0;
+        if (warp < NW) gram_init(gram + warp * kGramWarpHalves);
+    }
     __syncthreads();
 
     const int Lx = a.geo.Lx, Ly = a.geo.Ly;
 
-    if (MODE == kNoSampling && warp == NW) {
+    constexpr bool kEmbed = embedded_producer<NW, MODE>();
+    if ((MODE == kNoSampling || kTensor) && !kEmbed && warp == NW) {
         // ---------------- producer warp
         if (lane_id == 0) {
             Producer<NW, kWalk> prod(a);
@@ -258,7 +286,7 @@ step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
     const int c = threadIdx.x;          // 0 .. 32 NW - 1
     const int ty = c >> 6, r = c & 63;
     constexpr bool kFused = MODE == kFusedSampling;
-    const bool producer = kFused && c == 0;
+    const bool producer = (kFused || kEmbed) && c == 0;
     Producer<NW, kWalk> prod(a);
     if (producer) prod.prologue(smem, &map, a, full);
     float v[kFused ? kSums : 1];
@@ -266,6 +294,13 @@ step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
 #pragma unroll
         for (int q = 0; q < kSums; ++q) v[q] = 0.f;
     }
+    float gc[kTensor ? 8 : 1];
+    if (kTensor) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) gc[q] = 0.f;
+    }
+    int gtiles = 0;
+    const uint32_t gblk = smem_u32(gram + warp * kGramWarpHalves);
     int k = 0;
     TileWalk w(blockIdx.x, gridDim.x, a.tiles_x);
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++k, w.next()) {
@@ -299,11 +334,35 @@ step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
             }
             add_sums(reinterpret_cast<float(&)[kSums]>(v), d);
         }
+        // tensor sampling: stage this tile's nodes when the collision reads
+        // them a second time (the table f-norm reads them once: stage now)
+        auto stage = [&](const f2* gs) {
+            f2 hs[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) hs[i] = mad(gs[i], f2(a.sinv), f2(a.snref[i]));
+            if (!(inA && inB)) {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) hs[i] = f2(inA ? hs[i].v.x : 0.f, inB ? hs[i].v.y : 0.f);
+            }
+            gram_stage(gblk, hs);
+        };
+        auto refetch = [&](f2* gg) {
+            load(gg);
+            if (kTensor && BASIS != 2) stage(gg);
+        };
+        if (kTensor && BASIS == 2) stage(g);
         const uint32_t nodeA = (uint32_t)xA + (uint32_t)Lx * (uint32_t)y;
         f2 f[9];
         const uint32_t stt = collide_basis<f2, BASIS>(
-            g, [&](f2* N) { node_normals(cc.key, nodeA, nodeA + 64u, a.step, N); }, load, a.lut,
+            g, PairNoise{cc.key, nodeA, nodeA + 64u, a.step}, refetch, a.lut,
             cc, f);
+        if (kTensor) {
+            gram_mma(gblk, reinterpret_cast<float(&)[8]>(gc));
+            if (++gtiles == kGramFlushTiles) {
+                gram_flush(reinterpret_cast<float(&)[8]>(gc), red);
+                gtiles = 0;
+            }
+        }
         // the stage is held until g was read the second time
         __syncwarp();
         if (lane_id == 0) mbar_arrive(&empty[s]);
@@ -324,11 +383,22 @@ step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
             if (inA) store_lane(a.dst, a.geo, xA, y, f, 0);
             if (inB) store_lane(a.dst, a.geo, xB, y, f, 1);
         }
-        if (producer) prod.refill(smem, &map, a, full, empty, s, n);
+        if (producer) {
+            if (!kEmbed)
+                prod.refill(smem, &map, a, full, empty, s, n);
+            else if (k > 0)
+                prod.refill(smem, &map, a, full, empty, (k - 1) % kStages, (k - 1) / kStages);
+        }
     }
+    if (kEmbed && producer) prod.drain(a, full, k);
     if (kFused) {
         if (producer) prod.drain(a, full, k);
         publish_sums(reinterpret_cast<float(&)[kSums]>(v), 0, NW * 32, red, a);
+    }
+    if (kTensor) {
+        gram_flush(reinterpret_cast<float(&)[8]>(gc), red);
+        named_sync(1, NW * 32);
+        if (c < kSums) atomicAdd(&a.acc[c], gram_sum(red, c, a.s));
     }
 }
 
@@ -389,27 +459,37 @@ const void* kernel_ptr_m(int basis) {
 
 template <int NW>
 const void* kernel_ptr(int basis, int mode) {
-    if (mode == kSamplerWarps) return kernel_ptr_m<NW, kSamplerWarps>(basis);
-    if (mode == kFusedSampling) return kernel_ptr_m<NW, kFusedSampling>(basis);
-    return kernel_ptr_m<NW, kNoSampling>(basis);
+    if (mode == kTensorSampling) return kernel_ptr_m<NW, kTensorSampling>(basis);
+    if constexpr (NW > 12) {
+        return mode == kNoSampling ? kernel_ptr_m<NW, kNoSampling>(basis) : nullptr;
+    } else {
+        if (mode == kSamplerWarps) return kernel_ptr_m<NW, kSamplerWarps>(basis);
+        if (mode == kFusedSampling) return kernel_ptr_m<NW, kFusedSampling>(basis);
+        return kernel_ptr_m<NW, kNoSampling>(basis);
+    }
 }
 
 const void* kernel_for(int nw, int basis, int mode) {
     switch (nw) {
         case 8: return kernel_ptr<8>(basis, mode);
         case 12: return kernel_ptr<12>(basis, mode);
+        case 16: return kernel_ptr<16>(basis, mode);
         default: return nullptr;
     }
 }
 
 int warps_for(int nw, int mode) {
-    return nw + (mode == kSamplerWarps ? kSamplers : (mode == kFusedSampling ? 0 : 1));
+    if (mode == kSamplerWarps) return nw + kSamplers;
+    if (mode == kFusedSampling || nw >= 16) return nw;
+    return nw + 1;
 }
 
+// Dynamic shared memory of a plan (the largest of its modes).
 size_t smem_for(int nw) {
     switch (nw) {
-        case 8: return TileShape<8>::smem_bytes();
-        case 12: return TileShape<12>::smem_bytes();
+        case 8: return TileShape<8>::smem_bytes() + gram_smem_bytes<8>();
+        case 12: return TileShape<12>::smem_bytes() + gram_smem_bytes<12>();
+        case 16: return TileShape<16>::smem_bytes() + gram_smem_bytes<16>();
         default: return 0;
     }
 }
@@ -449,8 +529,9 @@ cudaError_t tma_plan(TmaPlan* plan, void* buf0, void* buf1, const Geometry& g, i
     if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int per_sm = 2;
     for (int basis = 0; basis < 3 && ce == cudaSuccess; ++basis)
-        for (int mode = 0; mode < 3 && ce == cudaSuccess; ++mode) {
+        for (int mode = 0; mode < 4 && ce == cudaSuccess; ++mode) {
             const void* fn = kernel_for(nw, basis, mode);
+            if (!fn) continue;
             ce = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             int n = 0;
             if (ce == cudaSuccess)
@@ -467,8 +548,10 @@ cudaError_t tma_plan(TmaPlan* plan, void* buf0, void* buf1, const Geometry& g, i
     int grid = sms * per_sm;
     if (grid > plan->ntiles) grid = plan->ntiles;
     plan->grid = grid < 1 ? 1 : grid;
-    if (plan->sample_mode != kSamplerWarps && plan->sample_mode != kFusedSampling)
+    if (plan->sample_mode != kSamplerWarps && plan->sample_mode != kFusedSampling &&
+        plan->sample_mode != kTensorSampling)
         plan->sample_mode = kDefaultSampling;
+    if (!kernel_for(nw, 0, plan->sample_mode)) plan->sample_mode = kTensorSampling;
     plan->ready = true;
     return cudaSuccess;
 }

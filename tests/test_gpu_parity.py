@@ -17,6 +17,7 @@ import numpy as np
 import pytest
 
 import oracle
+from tolerances import assert_sums_close, staged_corr_bounds
 from paper_1204_6734_gb300 import flb, inputs
 
 pytestmark = pytest.mark.gpu
@@ -143,13 +144,24 @@ def test_fp64_trajectory_small_lattices(shape, basis):
     np.testing.assert_allclose(S2, run.S2, rtol=1e-9, atol=1e-12 * n * 1e-6)
 
 
-@pytest.mark.slow
-def test_fp64_parity_lattice_full_run():
-    """32x32 FP64 f-norm lattice, u0 = (0.1, 0), 10^4 steps, sampled every step
-    after 10^3: populations within 1e-12 relative, correlations to 1e-9."""
+@pytest.fixture(scope="module")
+def parity_run():
+    """The oracle's run of the 32x32 parity workload (u0 = (0.1, 0), all rates 1,
+    f-norm, seed 1): 10^4 steps sampled every step after 10^3, computed once for
+    the FP64 and FP32 checks below (the oracle is FP64 whatever the precision
+    the GPU runs in, and draws the same noise)."""
     p = inputs.fp64_parity_lattice()
     T, W = inputs.FP64_PARITY_STEPS, inputs.FP64_PARITY_WARMUP
     run = oracle.Run(p, warmup=W, every=1).step(T)
+    C_ref, mean_ref = run.covariance()
+    return p, T, W, run, C_ref, mean_ref, run.moment_covariance("local")
+
+
+@pytest.mark.slow
+def test_fp64_parity_lattice_full_run(parity_run):
+    """32x32 FP64 f-norm lattice, u0 = (0.1, 0), 10^4 steps, sampled every step
+    after 10^3: populations within 1e-12 relative, correlations to 1e-9."""
+    p, T, W, run, C_ref, mean_ref, CM_ref = parity_run
     with flb.Lattice(p) as lat:
         lat.set_sampling(W, 1)
         lat.step(T)
@@ -157,27 +169,50 @@ def test_fp64_parity_lattice_full_run():
         f = lat.populations()
         Cff, CMM, mean, n = lat.correlations("local")
     assert np.abs(f - run.f).max() / np.abs(run.f).max() < 1e-12
-    C_ref, mean_ref = run.covariance()
     assert n == run.nsamp == (T - W) * 32 * 32
     assert np.abs(Cff - C_ref).max() < 1e-9 * np.abs(C_ref).max()
-    CM_ref = run.moment_covariance("local")
     assert np.abs(CMM - CM_ref).max() < 1e-9 * np.abs(CM_ref).max()
     np.testing.assert_allclose(mean, mean_ref, atol=1e-12)
 
 
-KERNELS = ["generic", "pipelined", "pipelined-fused", "pipelined12", "pipelined8"]
+@pytest.mark.slow
+@pytest.mark.parametrize("kernel", ["generic", "pipelined", "pipelined-samplers", "pipelined16"])
+def test_fp32_parity_lattice_full_run(parity_run, kernel):
+    """The same workload with FP32 populations and arithmetic, over the full 10^4
+    steps: every population within 1e-5 of the oracle's FP64 trajectory (same
+    draws) and the correlations within 1% (of kT w_max for <df_i df_j>, of kT for
+    <dM^a dM^b>), for the generic kernel and the pipelined one with each way of
+    accumulating the sums."""
+    p64, T, W, run, C_ref, mean_ref, CM_ref = parity_run
+    p = inputs.LatticeParams(p64.Lx, p64.Ly, p64.rho0, p64.ux0, p64.uy0, p64.kT, p64.omega,
+                             p64.basis, "fp32", seed=p64.seed)
+    with lattice(p, kernel) as lat:
+        lat.set_sampling(W, 1)
+        lat.step(T)
+        lat.sync()
+        f = lat.populations()
+        Cff, CMM, mean, n = lat.correlations("local")
+    assert n == run.nsamp
+    assert np.abs(f - run.f).max() < 1e-5
+    assert np.abs(Cff - C_ref).max() < 0.01 * p.kT * 4.0 / 9.0
+    assert np.abs(CMM - CM_ref).max() < 0.01 * p.kT
+
+
+KERNELS = ["generic", "pipelined", "pipelined-samplers", "pipelined-fused", "pipelined16",
+           "pipelined8"]
 
 
 def lattice(p, kernel):
     """A lattice with the given FP32 step kernel: the generic one, or the
-    pipelined one -- by default sampler warps and 8 colliding warps on
-    sampling steps, 12 colliding warps on the f-norm bases' other steps;
-    sums fused into the colliding warps; 12 or 8 colliding warps on every
-    step."""
-    if kernel == "pipelined12":
-        return flb.Lattice(p, kernel="pipelined", pipeline_warps=12)
+    pipelined one -- by default the sums on the tensor cores and 12 colliding
+    warps; sampler warps with 8 colliding warps; sums fused into the colliding
+    warps; 16 or 8 colliding warps with the tensor-core sums."""
+    if kernel == "pipelined16":
+        return flb.Lattice(p, kernel="pipelined", pipeline_warps=16)
     if kernel == "pipelined8":
         return flb.Lattice(p, kernel="pipelined", pipeline_warps=8)
+    if kernel == "pipelined-samplers":
+        return flb.Lattice(p, kernel="pipelined", pipeline_sampling=1, pipeline_warps=8)
     if kernel == "pipelined-fused":
         return flb.Lattice(p, kernel="pipelined", pipeline_sampling=2)
     return flb.Lattice(p, kernel=kernel)
@@ -185,17 +220,18 @@ def lattice(p, kernel):
 
 @pytest.mark.parametrize("basis", BASES)
 def test_warp_counts_give_identical_states(basis):
-    """8 and 12 colliding warps pair the same nodes (x, x + 64) in the same
+    """8, 12 and 16 colliding warps pair the same nodes (x, x + 64) in the same
     packed arithmetic: identical populations, with and without sampling."""
     p = inputs.LatticeParams(300, 37, 1.0, 0.15, 0.05, 1e-3, inputs.omega_groups(1.2, 0.8, 1.3), basis,
                              "fp32", seed=8)
     out = []
-    for kernel in ("pipelined", "pipelined8", "pipelined12"):
+    for kernel in ("pipelined", "pipelined8", "pipelined16", "pipelined-samplers"):
         with lattice(p, kernel) as lat:
             lat.set_sampling(10, 3)
             lat.step(40)
             out.append(lat.populations())
-    assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])
+    for o in out[1:]:
+        assert np.array_equal(out[0], o)
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
@@ -257,8 +293,7 @@ def test_fp32_kernels_agree_with_oracle_step_by_step(shape, basis, kernel):
         S1, S2, n = lat.raw_sums()
     assert np.abs(f - run.f).max() < 2e-6
     assert n == run.nsamp
-    np.testing.assert_allclose(S2, run.S2, rtol=2e-4, atol=1e-9 * n)
-    np.testing.assert_allclose(S1, run.S1, rtol=2e-4, atol=1e-7 * n)
+    assert_sums_close(S1, S2, run.S1, run.S2, n, 2e-4, 1e-7 * n, 1e-9 * n)
 
 
 @pytest.mark.parametrize("basis", BASES)
@@ -275,7 +310,9 @@ def test_pipelined_equals_generic_fp32(basis):
             out[kernel] = (lat.populations(), lat.raw_sums())
     for k in KERNELS[1:]:
         assert np.abs(out["generic"][0] - out[k][0]).max() < 1e-6
-        np.testing.assert_allclose(out["generic"][1][1], out[k][1][1], rtol=1e-4)
+        g1, g2, gn = out["generic"][1]
+        assert_sums_close(out[k][1][0], out[k][1][1], g1, g2, gn, 1e-4, 3e-6 * gn * np.sqrt(p.kT),
+                          1e-6 * gn * p.kT)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])

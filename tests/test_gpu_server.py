@@ -12,6 +12,7 @@ sample counts exactly.
 import numpy as np
 import pytest
 
+from tolerances import assert_sums_close, staged_corr_bounds
 from paper_1204_6734_gb300 import flb, inputs
 
 pytestmark = pytest.mark.gpu
@@ -43,8 +44,9 @@ def mix(basis=inputs.LOCAL, n=10, seed=21):
 def close(a, b, n, kT):
     assert a["status"] == b["status"] == flb.OK
     assert a["n_samples"] == b["n_samples"] == n
-    np.testing.assert_allclose(a["S2"], b["S2"], rtol=1e-4, atol=1e-6 * n * kT)
-    np.testing.assert_allclose(a["S1"], b["S1"], rtol=1e-4, atol=3e-6 * n * np.sqrt(kT))
+    # per-lattice requests take their sums from the tensor cores (FP16-staged
+    # deviations), batched ones from FP32 products
+    assert_sums_close(a["S1"], a["S2"], b["S1"], b["S2"], n, 1e-4, 3e-6 * n * np.sqrt(kT), 1e-6 * n * kT)
 
 
 def expected_samples(p, steps, warmup, every):
