@@ -85,6 +85,14 @@ def parse():
     ap.add_argument("--no-structure", action="store_true",
                     help="skip the structure-factor sampling measurement")
     ap.add_argument("--structure-steps", type=int, default=100)
+    ap.add_argument("--min-seconds", type=float, default=1.0,
+                    help="repeat the timed block of --steps steps until it spans this much device time")
+    ap.add_argument("--max-repeats", type=int, default=1000)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 kernel measurement")
+    ap.add_argument("--no-precision", action="store_true", help="skip the precision study")
+    ap.add_argument("--precision-side", type=int, default=8192)
+    ap.add_argument("--no-serving-70", action="store_true",
+                    help="skip the serving run at 70 %% of the measured capacity")
     return ap.parse_args()
 
 
@@ -171,22 +179,65 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_mlups(p, max_seconds=10.0, side=512):
-    """Oracle (plain FP64 C, one thread) on a side x side sample of the workload's
-    parameters: calibrate one step, then run enough steps to fill ~max_seconds."""
+def cpu_model():
+    """Model name of the host CPU (lscpu; /proc/cpuinfo as a fallback)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                if ln.lower().startswith("model name"):
+                    return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_runs(p, side, steps, threads, precision="fp64"):
+    """The oracle as it stands (plain FP64 C, one lattice per host thread) on
+    `threads` independent side x side lattices of the workload's parameters
+    with distinct seeds, `steps` steps each with sampling on; ctypes releases
+    the GIL, so the threads run on separate cores. Returns aggregate MLUPS and
+    the wall time."""
+    import concurrent.futures as cf
+
     import oracle as O
     from paper_1204_6734_gb300 import inputs
-    q = inputs.LatticeParams(side, side, p.rho0, p.ux0, p.uy0, p.kT, p.omega, p.basis, "fp64",
-                             seed=p.seed)
-    run = O.Run(q, warmup=0, every=1)
+    runs = [O.Run(inputs.LatticeParams(side, side, p.rho0, p.ux0, p.uy0, p.kT, p.omega, p.basis,
+                                       precision, seed=p.seed + 7919 * k), warmup=0, every=1)
+            for k in range(threads)]
     t0 = time.perf_counter()
-    run.step(1)
-    one = time.perf_counter() - t0
-    n = max(1, int(max_seconds / max(one, 1e-6)) - 1)
-    t0 = time.perf_counter()
-    run.step(n)
+    with cf.ThreadPoolExecutor(threads) as ex:
+        list(ex.map(lambda r: r.step(steps), runs))
     dt = time.perf_counter() - t0
-    return side * side * n / dt / 1e6, f"{side}x{side} lattice, {n} steps (sampling on), same parameters", 1
+    return threads * side * side * steps / dt / 1e6, dt
+
+
+def oracle_mlups(p, max_seconds=15.0, side=1024):
+    """The CPU baseline of the line: the oracle on every host core at once, one
+    independent side x side lattice per core, with the step count calibrated
+    (one step on one core) to about max_seconds of wall time."""
+    cores = host_cores()
+    one, dt1 = oracle_runs(p, side, 1, 1)
+    n = max(1, int(max_seconds / max(dt1, 1e-6)))
+    v, dt = oracle_runs(p, side, n, cores)
+    sample = (f"{cores} independent {side}x{side} lattices of the workload's parameters (FP64 "
+              f"oracle, one per host thread, distinct seeds), {n} steps each with sampling on, "
+              f"{dt:.1f} s wall; CPU: {cpu_model()}; one thread alone: {one:.2f} MLUPS")
+    return v, sample, cores
 
 
 def bench_structure(args, p, stream, peak, peak_kind):
@@ -421,66 +472,112 @@ def run_serving(args, rank, world, dist, dev):
         print(json.dumps(out))
 
 
-def run_precision(args, rank, world, dist, dev):
-    """--workload precision: the same lattice (8192^2 by default, u_x0 = 0.2,
-    kT = 1e-4, all rates 1, f-norm, seed 4) run --steps steps in FP64, FP32 and
-    the FP16 deviation store with the same draws, sampled every step after a
-    tenth of the steps; errors of the FP32 and FP16 states and of <df_i df_j>
-    against the FP64 run, and the throughput of each."""
+def bench_precision(stream, side, steps):
+    """The same lattice (u_x0 = 0.2, kT = 1e-4, all rates 1, f-norm, seed 4) run
+    `steps` steps in FP64, FP32 and the FP16 deviation store with the same
+    draws, sampled every step after a tenth of the steps; errors of the FP32 and
+    FP16 states and of <df_i df_j>, <dM dM> against the FP64 run, and the
+    throughput of each (CUDA events on the launching stream)."""
     import numpy as np
     import torch
 
     from paper_1204_6734_gb300 import flb, inputs
-    stream = torch.cuda.Stream(device=dev)
-    side = args.side if args.side != 4096 else 8192
-    warm = args.steps // 10
+    warm = steps // 10
     lats, res = {}, {}
-    with ClockSampler(smi_id(dev)) as clk:
+    try:
         for prec in ("fp64", "fp32", "fp16dev"):
             p = inputs.precision_lattice(prec, side=side)
             lat = flb.Lattice(p, stream=stream)
+            lats[prec] = lat
             lat.set_sampling(warm, 1)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
             e0.record(stream)
-            lat.step(args.steps)
+            lat.step(steps)
             e1.record(stream)
             lat.sync()
-            ms = e0.elapsed_time(e1) / args.steps
+            ms = e0.elapsed_time(e1) / steps
             Cff, CMM, mean, n = lat.correlations("local")
-            lats[prec] = lat
             res[prec] = {"ms_per_step": ms, "mlups": p.Lx * p.Ly / ms / 1e3,
                          "bytes_per_node": {"fp64": 144, "fp32": 72, "fp16dev": 36}[prec],
                          "Cff": Cff, "CMM": CMM, "n_samples": n}
-    kT, wmax = 1e-4, 4.0 / 9.0
-    out = {}
-    for prec in ("fp64", "fp32", "fp16dev"):
-        r = res[prec]
-        o = {"mlups": r["mlups"], "ms_per_step": r["ms_per_step"], "bytes_per_node": r["bytes_per_node"]}
-        if prec != "fp64":
-            mx, rms, fmax = flb.flb_state_difference(lats[prec].h, lats["fp64"].h)
-            o["population_error_max"] = mx
-            o["population_error_rms"] = rms
-            o["corr_error_max_over_kT_wmax"] = float(np.abs(r["Cff"] - res["fp64"]["Cff"]).max() / (kT * wmax))
-            o["moment_corr_error_max_over_kT"] = float(np.abs(r["CMM"] - res["fp64"]["CMM"]).max() / kT)
-        out[prec] = o
-    for lat in lats.values():
-        lat.close()
+        kT, wmax = 1e-4, 4.0 / 9.0
+        out = {"workload": f"{side}x{side} periodic, u_x0=0.2, kT=1e-4, all rates 1, f-norm basis, "
+                           f"seed 4, {steps} steps, sampled every step after {warm}; errors against "
+                           "the FP64 run on the GPU (same draws)",
+               "steps": steps, "n_samples": int(res["fp32"]["n_samples"])}
+        for prec in ("fp64", "fp32", "fp16dev"):
+            r = res[prec]
+            o = {"mlups": r["mlups"], "ms_per_step": r["ms_per_step"],
+                 "bytes_per_node": r["bytes_per_node"]}
+            if prec != "fp64":
+                mx, rms, fmax = flb.flb_state_difference(lats[prec].h, lats["fp64"].h)
+                o["population_error_max"] = mx
+                o["population_error_rms"] = rms
+                o["corr_error_max_over_kT_wmax"] = float(
+                    np.abs(r["Cff"] - res["fp64"]["Cff"]).max() / (kT * wmax))
+                o["moment_corr_error_max_over_kT"] = float(
+                    np.abs(r["CMM"] - res["fp64"]["CMM"]).max() / kT)
+            out[prec] = o
+    finally:
+        for lat in lats.values():
+            lat.close()
+    return out
+
+
+def run_precision(args, rank, world, dist, dev):
+    """--workload precision: bench_precision on the 8192^2 lattice (--side) for
+    --steps steps, as the main line."""
+    import torch
+    stream = torch.cuda.Stream(device=dev)
+    side = args.side if args.side != 4096 else 8192
+    with ClockSampler(smi_id(dev)) as clk:
+        out = bench_precision(stream, side, args.steps)
     if rank == 0:
         line = {"metric": METRIC, "value": out["fp32"]["mlups"], "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": 0, "ms_per_step": out["fp32"]["ms_per_step"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
-                "config": {"workload": f"precision study: {side}x{side} periodic, u_x0=0.2, kT=1e-4, "
-                                       "all rates 1, f-norm basis, seed 4, FP64 / FP32 / FP16 "
-                                       f"deviation store, sampled every step after {warm}",
+                "config": {"workload": "precision study: " + out["workload"],
                            "l2": "inputs larger than L2"},
-                "precision": out, "clocks": clk.summary(),
-                "n_samples": int(res["fp32"]["n_samples"])}
+                "precision": out, "clocks": clk.summary(), "n_samples": out["n_samples"]}
         print(json.dumps(line))
 
 
-MOMENT_NAMES = ("rho", "j_x", "j_y", "Pi_xx-yy", "Pi_xy", "Pi_xx+yy", "q_x", "q_y", "eps")
+def bench_fp64(stream, p64, steps, peak, peak_kind):
+    """The FP64 parity-mode kernel on the bench lattice (f-norm or Hermite,
+    sampling every step): MLUPS, against the FP64 pipe (its bound) and HBM."""
+    import torch
+
+    from paper_1204_6734_gb300 import flb
+    nodes = p64.Lx * p64.Ly
+    with flb.Lattice(p64, stream=stream) as lat:
+        lat.set_sampling(0, 1)
+        lat.step(2)
+        lat.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lat.step(steps)
+        e1.record(stream)
+        lat.sync()
+        ms = e0.elapsed_time(e1) / steps
+    hbm = BYTES_PER_NODE["fp64"] * nodes / (ms * 1e-3) / 1e9
+    out = {"workload": f"{p64.Lx}x{p64.Ly}, FP64 populations, the same parameters, sampled every step",
+           "mlups": nodes / ms / 1e3, "ms_per_step": ms, "steps": steps,
+           "kernel": "step_kernel<f64,%s,sample>" % p64.basis,
+           "hbm": {"achieved": hbm, "peak": peak, "unit": "GB/s", "frac": hbm / peak,
+                   "peak_kind": peak_kind}}
+    fl = FP64_FLOPS_PER_NODE.get(p64.basis)
+    if fl:
+        tf = fl * nodes / (ms * 1e-3) / 1e12
+        out["roofline"] = {"bound": "alu", "achieved": tf, "peak": FP64_NOMINAL_TFLOPS,
+                           "unit": "TFLOP/s", "frac": tf / FP64_NOMINAL_TFLOPS,
+                           "peak_kind": "nominal FP64 rate (no measured FP64 peak)",
+                           "flops_per_node": fl}
+    return out
+
+
+MOMENT_NAMES = ("rho", "j_x", "j_y", "Pi_xx-yy", "Pi_xy", "Pi_xx+yy", "q_x", "q_y", "eps")   # drift.MOMENTS
 # Quadratic coefficients q the paper prints for 21x21 lattices (Section 4,
 # after Figs. 19-21): Hermite norm measured in the Hermite norm, f-norm (its
 # look-up-table variant) measured in the f-norm at u0.
@@ -492,12 +589,13 @@ PAPER_Q = {"standard": {"rho": 1.9, "Pi_xx-yy": 1.6, "j_y": 1.14},
 def run_sweep(args, rank, world, dist, dev):
     """--workload sweep: the u_x0 sweep of the 4096^2 lattice in both bases
     (--steps steps each, sampled every step after a tenth); the normalised
-    moment variances <dM^a dM^a> / (kT rho0) - 1, measured in the run's own
-    basis at u0, and the quadratic coefficient q of each (fit_drift)."""
+    moment correlators <dM^a dM^b> / (kT rho0) - delta^{ab}, measured in the
+    run's own basis at u0, and the paper's fit l u + q u^2 of all 45 of them
+    (paper_1204_6734_gb300.drift)."""
     import numpy as np
     import torch
 
-    from paper_1204_6734_gb300 import flb, inputs
+    from paper_1204_6734_gb300 import drift, flb, inputs
     stream = torch.cuda.Stream(device=dev)
     warm = max(1, args.steps // 10)
     res = {}
@@ -512,16 +610,19 @@ def run_sweep(args, rank, world, dist, dev):
                     lat.step(args.steps)
                     lat.sync()
                     Cff, CMM, mean, n = lat.correlations(mb)
-                dev_ = np.diag(CMM) / (p.kT * p.rho0) - 1.0
-                rows.append((u, dev_, np.diag(Cff) / (p.kT * feq_of(p))))
+                rows.append((u, drift.normalised(CMM, p.kT, p.rho0),
+                             np.diag(Cff) / (p.kT * feq_of(p))))
             us = np.array([r[0] for r in rows])
-            D = np.array([r[1] for r in rows])
-            q = fit_drift(us, D)
+            DM = np.array([r[1] for r in rows])
+            D = np.array([np.diag(m) for m in DM])
+            l, q = drift.fit_lq(us, DM)
             res[basis] = {
                 "u_x0": [float(u) for u in us],
                 "moment_variance_minus_1": {MOMENT_NAMES[a]: [float(x) for x in D[:, a]] for a in range(9)},
                 "population_variance_over_kT_f0": [[float(x) for x in r[2]] for r in rows],
-                "fit_q": {MOMENT_NAMES[a]: float(q[a]) for a in range(9)},
+                "fit_q": {MOMENT_NAMES[a]: float(q[a, a]) for a in range(9)},
+                "fit_lq": drift.as_table(l, q),
+                "max_abs_l_odd_pairs": float(np.abs(l).max()),
                 "paper_q_21x21": PAPER_Q[basis],
             }
     if rank == 0:
@@ -536,18 +637,6 @@ def run_sweep(args, rank, world, dist, dev):
         print(json.dumps(line))
 
 
-def fit_drift(us, D):
-    """q of the least-squares fit l u + q u^2 over -0.25 <= u <= 0.25 (the
-    paper's range) of the diagonal variances D[point, a]: they are even in
-    u_x0 (x reflection of the lattice), so the points u >= 0 stand for their
-    mirror images, l = 0 and q = sum D u^2 / sum u^4."""
-    import numpy as np
-    us = np.asarray(us, dtype=float)
-    fit = us <= 0.25
-    D = np.asarray(D)[fit]
-    return (D * us[fit, None] ** 2).sum(axis=0) / (us[fit] ** 4).sum()
-
-
 def run_sweep21(args, rank, world, dist, dev):
     """--workload sweep21: the u_x0 sweep on the paper's own 21 x 21 lattice.
     --replicas independent copies per (u_x0, basis), all points of one basis in
@@ -558,7 +647,7 @@ def run_sweep21(args, rank, world, dist, dev):
     import numpy as np
     import torch
 
-    from paper_1204_6734_gb300 import flb, inputs
+    from paper_1204_6734_gb300 import drift, flb, inputs
     stream = torch.cuda.Stream(device=dev)
     warm = max(1, args.steps // 10)
     R = args.replicas
@@ -579,15 +668,18 @@ def run_sweep21(args, rank, world, dist, dev):
                     slots = list(range(iu * R, (iu + 1) * R))
                     Cff, CMM, mean, n = b.correlations(slots, "standard" if basis == "standard" else "local")
                     p = ps[iu * R]
-                    rows.append((u, np.diag(CMM) / (p.kT * p.rho0) - 1.0, n))
+                    rows.append((u, drift.normalised(CMM, p.kT, p.rho0), n))
             us = [r[0] for r in rows]
-            D = np.array([r[1] for r in rows])
-            q = fit_drift(us, D)
+            DM = np.array([r[1] for r in rows])
+            D = np.array([np.diag(m) for m in DM])
+            l, q = drift.fit_lq(us, DM)
             nodes = sum(p.Lx * p.Ly for p in ps)
             res[basis] = {
                 "u_x0": us, "node_samples_per_point": [int(r[2]) for r in rows],
                 "moment_variance_minus_1": {MOMENT_NAMES[a]: [float(x) for x in D[:, a]] for a in range(9)},
-                "fit_q": {MOMENT_NAMES[a]: float(q[a]) for a in range(9)},
+                "fit_q": {MOMENT_NAMES[a]: float(q[a, a]) for a in range(9)},
+                "fit_lq": drift.as_table(l, q),
+                "max_abs_l_odd_pairs": float(np.abs(l).max()),
                 "paper_q_21x21": PAPER_Q[basis],
                 "batch_ms_per_step": ms / args.steps, "mlups": nodes * args.steps / (ms * 1e-3) / 1e6,
             }
@@ -674,31 +766,36 @@ def single_config(p, args, world):
 
 
 def run_reference(args):
+    """The reference arm: the oracle (the method written plainly from the paper,
+    FP64, one lattice per host thread) on every host core, each timed step one
+    step of 256x256 lattices of the workload's parameters on every core."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
     from paper_1204_6734_gb300 import inputs
     p = inputs.single_lattice(args.ux0, args.basis, side=args.side, precision="fp64")
-    import oracle as O
     side = 256
-    q = inputs.LatticeParams(side, side, p.rho0, p.ux0, p.uy0, p.kT, p.omega, p.basis, "fp64",
-                             seed=p.seed)
-    run = O.Run(q, warmup=0, every=1)
-    run.step(args.warmup)
-    t0 = time.perf_counter()
-    run.step(args.steps)
-    dt = time.perf_counter() - t0
-    value = side * side * args.steps / dt / 1e6
+    cores = host_cores()
+    oracle_runs(p, side, args.warmup, cores)
+    value, dt = oracle_runs(p, side, args.steps, cores)
     cfg = single_config(inputs.single_lattice(args.ux0, args.basis, side=args.side,
                                               precision=args.precision), args, world)
+    cfg.update({"Lx": side, "Ly": side, "precision": "fp64", "replicas": cores,
+                "sample_of": cfg["workload"],
+                "workload": f"{cores} independent {side}x{side} periodic D2Q9 lattices (one per "
+                            f"host core), FP64 oracle, {args.basis} basis, u_x0={p.ux0}, kT={p.kT}, "
+                            "omega shear/bulk/ghost=1.0/0.8/1.0, correlations sampled every step",
+                "parallelism": f"host threads x{cores}",
+                "l2": "CPU run"})
     out = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / max(args.steps, 1) * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": cfg,
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"the same workload on a {side}x{side} lattice, FP64, one host "
-                                   f"thread, {args.steps} steps (MLUPS of the sample)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{cores} independent {side}x{side} lattices, FP64, one per "
+                                   f"host thread, {args.steps} steps each (aggregate MLUPS); "
+                                   f"CPU: {cpu_model()}"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out))
@@ -748,32 +845,43 @@ def main():
                       pipeline_sampling=args.pipeline_sampling if args.pipeline_sampling else None)
     lat.set_sampling(0, args.sample_every)   # sample (and reduce) every step by default
 
-    # warm-up
-    lat.step(args.warmup)
-    lat.sync()
-
     def barrier():
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
 
+    # warm-up (also gives the length of one step, to size the repeats)
+    w0, w1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    w0.record(stream)
+    lat.step(args.warmup)
+    w1.record(stream)
+    lat.sync()
+    warm_ms = w0.elapsed_time(w1) / max(args.warmup, 1)
+    # the timed region: blocks of exactly --steps steps, each bracketed by a
+    # barrier and a device synchronisation, repeated until they span at least
+    # --min-seconds of device time (and at least 3 times); the line reports the
+    # median block (max over ranks), and the clocks sampled across all of them
+    repeats = max(3, int(math.ceil(args.min_seconds * 1e3 / max(warm_ms * args.steps, 1e-3))))
+    repeats = min(repeats, args.max_repeats)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     t_all0 = torch.cuda.Event(enable_timing=True)
     t_all1 = torch.cuda.Event(enable_timing=True)
-    barrier()
+    block_ms, per_step = [], []
     with ClockSampler(smi_id(dev)) as clk:
-        t_all0.record(stream)
-        for k in range(args.steps):
-            starts[k].record(stream)
-            flb.flb_step(lat.h, 1)
-            ends[k].record(stream)
-        t_all1.record(stream)
-        barrier()
+        for _ in range(repeats):
+            barrier()
+            t_all0.record(stream)
+            for k in range(args.steps):
+                starts[k].record(stream)
+                flb.flb_step(lat.h, 1)
+                ends[k].record(stream)
+            t_all1.record(stream)
+            barrier()
+            block_ms.append(replicas.max_over_ranks(t_all0.elapsed_time(t_all1), dist, device="cuda"))
+            per_step += [a.elapsed_time(b) for a, b in zip(starts, ends)]
     lat.sync()
-    total_ms = t_all0.elapsed_time(t_all1)
-    per_step = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = replicas.max_over_ranks(total_ms, dist, device="cuda")
+    total_ms = statistics.median(block_ms)
     value = replicas.whole_job_rate(nodes * args.steps, world, total_ms * 1e-3) / 1e6
     step_ms = statistics.mean(per_step)
 
@@ -849,11 +957,23 @@ def main():
     if rank == 0 and world == 1 and not args.no_structure:
         structure = bench_structure(args, p, stream, peak, peak_kind)
 
-    batched = serving = None
+    batched = serving = fp64 = precision = None
     if rank == 0 and world == 1 and not args.no_batched and args.precision == "fp32":
         batched = bench_batched(args, stream)
     if rank == 0 and world == 1 and not args.no_serving and args.precision == "fp32":
         serving = bench_serving(args, stream)
+        if not args.no_serving_70:
+            # the same requests arriving at 70 % of the batched server's
+            # measured node-update capacity
+            work = serving["node_steps"] / args.serve_requests
+            rate70 = 0.7 * serving["batched"]["mlups"] * 1e6 / work
+            serving["at_70pct_capacity"] = bench_serving(args, stream, rate_hz=rate70)
+    if rank == 0 and world == 1 and not args.no_fp64 and args.precision == "fp32":
+        p64 = replicas.rank_params(inputs.single_lattice(args.ux0, args.basis, side=args.side,
+                                                         precision="fp64"), rank)
+        fp64 = bench_fp64(stream, p64, max(3, min(args.steps, 20)), peak, peak_kind)
+    if rank == 0 and world == 1 and not args.no_precision and args.precision == "fp32":
+        precision = bench_precision(stream, args.precision_side, max(10, args.steps))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -870,7 +990,9 @@ def main():
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": (1 if pipelined else 2) * args.steps,
+            "gpu_launches": (1 if pipelined else 2) * args.steps * repeats,
+            "repeats": repeats,
+            "block_ms": block_ms,
             "clocks": clk.summary(),
             "mlups_roofline_frac": value / (peak * 1e9 / BYTES_PER_NODE[args.precision] / 1e6) / world,
             "n_samples": ns,
@@ -878,6 +1000,8 @@ def main():
             "structure_factors": structure,
             "batched": batched,
             "serving": serving,
+            "fp64": fp64,
+            "precision": precision,
         }
         print(json.dumps(out))
     if dist is not None:
