@@ -267,12 +267,22 @@ typedef struct flb_batch_s* flb_batch;
 /* Tile shapes of the batched kernel (flb_batch_set_tile, flb_batch_autotune):
  * 128 x 4 nodes, 2 nodes per thread (default);
  * 64 x 8 nodes, 2 nodes per thread (wastes less on narrow lattices);
- * 128 x 2 nodes, 1 node per thread.
- * All run 8 colliding warps per CTA and one CTA per SM. */
+ * 128 x 2 nodes, 1 node per thread;
+ *   (these three: 8 colliding warps per CTA beside 4 sampler warps on
+ *   sampling steps, FP32 products)
+ * 128 x 6 and 64 x 12 nodes, 2 nodes per thread, 12 colliding warps that add
+ *   their own nodes to the correlation sums on the tensor cores (deviations
+ *   staged in FP16, as FLB_OPT_PIPELINE_SAMPLING 3 of a lattice): only when
+ *   every replica has kT > 0 and sqrt(rho0 / kT) <= 4000 (FLB_ERR_ARG from
+ *   flb_batch_set_tile otherwise, and from flb_batch_add of a replica that
+ *   breaks it; flb_batch_autotune skips them and reports -1 for their time).
+ * One CTA per SM. */
 #define FLB_TILE_128x4 0
 #define FLB_TILE_64x8 1
 #define FLB_TILE_128x2 2
-#define FLB_TILE_COUNT 3
+#define FLB_TILE_128x6 3
+#define FLB_TILE_64x12 4
+#define FLB_TILE_COUNT 5
 
 /* Open an empty batch for replicas in `basis` (flb_basis): at most
  * max_replicas (1 .. 16384) at a time, population buffers carved from one
@@ -439,13 +449,22 @@ int flb_server_set_tile(flb_server s, int32_t tile);
  *    pipelined TMA kernel for FP32, the generic kernel for FP64),
  *    FLB_KERNEL_GENERIC (one node per thread, plain loads) or
  *    FLB_KERNEL_PIPELINED (FP32 only). All give the same results up to rounding.
- *  FLB_OPT_PIPELINE_WARPS: consumer warps per CTA of the pipelined kernel
- *    (8 or 12; the tile is 128 x value/2 nodes) for every step. By default
- *    sampling steps use 8 and, in the f-norm bases, steps without sampling
- *    use 12. FP32 only.
+ *  FLB_OPT_PIPELINE_WARPS: colliding warps per CTA of the pipelined kernel
+ *    (8, 12 or 16; the tile is 128 x value/2 nodes) for every step. By
+ *    default sampling steps use 12 (8 with sampler warps) and steps without
+ *    sampling 12 in the f-norm bases, 8 in the Hermite norm. 16 exists with
+ *    the tensor-core sums and without sampling only. FP32 only.
  *  FLB_OPT_PIPELINE_SAMPLING: how the pipelined kernel accumulates the
- *    correlation sums on sampling steps -- 1 (default): dedicated sampler warps
- *    read the staged tile; 2: the colliding warps accumulate their own nodes.
+ *    correlation sums on sampling steps -- 1: dedicated sampler warps read the
+ *    staged tile (FP32 products; the default for the look-up-table f-norm and
+ *    where 3 is not allowed); 2: the colliding warps accumulate their own nodes
+ *    (FP32 products); 3 (default): the colliding warps stage their nodes'
+ *    deviations (f - f^0(rho0, u0)) / sqrt(kT rho0) in FP16 and add them to a
+ *    Gram matrix on the tensor cores, FP32 partials of at most 1024 products
+ *    summed in FP64 (each sum within (2^-10 + 2^-14) sqrt(S2_ii S2_jj), resp.
+ *    (2^-11 + 2^-14) sqrt(n S2_ii), of the exact one). 3 requires kT > 0 and
+ *    sqrt(rho0 / kT) <= 4000 (every deviation a valid state holds stays far
+ *    inside FP16's range).
  * Errors: FLB_ERR_ARG for an unknown option or value. */
 #define FLB_OPT_KERNEL 0
 #define FLB_OPT_PIPELINE_WARPS 1
@@ -454,6 +473,37 @@ int flb_server_set_tile(flb_server s, int32_t tile);
 #define FLB_KERNEL_GENERIC 1
 #define FLB_KERNEL_PIPELINED 2
 int flb_set_option(flb_lattice h, int32_t option, int32_t value);
+
+/* Slab decomposition of one periodic lattice along y (the step is local plus
+ * streaming, Eq. LBE1, so a lattice of Lx x Ly_total nodes splits into slabs
+ * of whole rows that exchange only the populations crossing their y
+ * boundaries). flb_set_slab makes handle h (of Lx x Ly nodes) hold rows
+ * y0 .. y0 + Ly - 1 of such a lattice: its noise counters and error locations
+ * use the global node x + Lx (y0 + y), so a decomposed run draws exactly what
+ * the whole lattice does, and its y boundaries are open to the caller's halo
+ * exchange instead of periodic within the handle. Call it before the first
+ * step; Lx Ly_total <= 2^32. A slab samples the correlations and the
+ * conservation sums of its own nodes (the slabs' sums add up to the lattice's);
+ * structure factors are not available on a slab. Errors: FLB_ERR_ARG.
+ *
+ * The exchange, after every step (the state from flb_create or
+ * flb_set_populations needs none), for every slab:
+ *   flb_halo_pack(h, lo, hi)   -- writes f*_i of the slab's row 0 for the
+ *       populations moving down (i = 4, 7, 8) to the device buffer lo, and of
+ *       its row Ly - 1 for those moving up (i = 2, 5, 6) to hi: each buffer 3
+ *       rows of Lx values of the state's precision, flb_halo_bytes(h) bytes;
+ *   the caller moves the slab below's hi and the slab above's lo (periodic in
+ *       y) into this slab's receive buffers (a device copy, or a send and a
+ *       receive between GPUs);
+ *   flb_halo_unpack(h, lo, hi) -- lo (the slab below's hi) fills the ghost row
+ *       the slab's row 0 pulls from, hi (the slab above's lo) the one its row
+ *       Ly - 1 pulls from, with the lattice's periodicity in x.
+ * Both are enqueued on the handle's stream; the buffers are the caller's
+ * device memory. Errors: FLB_ERR_ARG (not a slab, null buffer), FLB_ERR_CUDA. */
+int flb_set_slab(flb_lattice h, int32_t Ly_total, int32_t y0);
+size_t flb_halo_bytes(flb_lattice h);
+int flb_halo_pack(flb_lattice h, void* dev_lo, void* dev_hi);
+int flb_halo_unpack(flb_lattice h, const void* dev_lo, const void* dev_hi);
 
 /* The FP64 fused step with correlation sampling, for callers that cannot
  * allocate device memory. (The paper has no counterpart: this is an interface

@@ -112,7 +112,8 @@ cudaError_t launch(flb_batch_s* b, bool sample, cudaStream_t s) {
     a.ctl = b->ctl;
     a.lut = b->lut;
     void* params[1] = {(void*)&a};
-    const int warps = kBatchNW + (sample ? kSamplers : 1);
+    const BatchVariant& v = kBatchVariants[b->tile];
+    const int warps = v.nw + (sample && !v.tensor() ? kSamplers : 1);
     return cudaLaunchKernel(kernel_for(b, sample), dim3(b->grid), dim3(warps * 32), params,
                             batch_smem_bytes(b->tile), s);
 }
@@ -296,6 +297,8 @@ int flb_batch_add(flb_batch b, const flb_params* p, int64_t nsteps, int32_t* slo
     if (!valid_params(p) || p->precision != FLB_FP32 || p->basis != b->basis ||
         p->Lx > kMaxSide || p->Ly > kMaxSide)
         return FLB_ERR_ARG;
+    // the tensor-core shapes stage deviations in FP16: every replica must allow it
+    if (kBatchVariants[b->tile].tensor() && !tensor_sampling_ok(p)) return FLB_ERR_ARG;
     int k = 0;
     while (k < b->cap && b->slots[k].used) ++k;
     if (k == b->cap) return FLB_ERR_OOM;
@@ -324,6 +327,8 @@ int flb_batch_add(flb_batch b, const flb_params* p, int64_t nsteps, int32_t* slo
     }
     h.Lx = p->Lx;
     h.Ly = p->Ly;
+    h.gram_s = tensor_sampling_ok(p) ? (float)gram_scale(p) : 0.f;
+    h.gram_inv = h.gram_s > 0.f ? (float)(1.0 / gram_scale(p)) : 0.f;
     h.t0 = 0;
     h.join = (int)(unsigned)b->step;
     h.warmup = 0;
@@ -436,9 +441,17 @@ int flb_batch_set_graph(flb_batch b, int32_t steps) {
     return FLB_OK;
 }
 
+// Whether every replica of the batch allows the tensor-core sums.
+static bool batch_tensor_ok(const flb_batch_s* b) {
+    for (const BatchSlot& s : b->slots)
+        if (s.used && !tensor_sampling_ok(&s.p)) return false;
+    return true;
+}
+
 int flb_batch_set_tile(flb_batch b, int32_t tile) {
     if (!b || tile < 0 || tile >= kNumBatchVariants) return FLB_ERR_ARG;
     if (tile == b->tile) return FLB_OK;
+    if (kBatchVariants[tile].tensor() && !batch_tensor_ok(b)) return FLB_ERR_ARG;
     b->tile = tile;
     cudaError_t ce = cudaSuccess;
     for (int k = 0; k < b->cap && ce == cudaSuccess; ++k) {
@@ -515,6 +528,10 @@ int flb_batch_autotune(flb_batch b, int32_t trial_steps, int32_t* tile, double* 
     int best = b->tile, rc = FLB_OK;
     float best_ms = 0.f;
     for (int v = 0; v < kNumBatchVariants && ce == cudaSuccess && rc == FLB_OK; ++v) {
+        if (kBatchVariants[v].tensor() && !batch_tensor_ok(b)) {   // not a candidate
+            if (ms_per_step) ms_per_step[v] = -1.0;
+            continue;
+        }
         rc = flb_batch_set_tile(b, v);
         if (rc == FLB_OK) rc = flb_batch_step(b, 2);   // upload the table, warm the caches
         if (rc != FLB_OK) break;

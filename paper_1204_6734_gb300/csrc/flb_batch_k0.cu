@@ -15,6 +15,12 @@ const void* batch_kernel_std(int variant, bool sample) {
         case 2:
             return sample ? (const void*)batch_step_kernel<0, true, 128, 1>
                           : (const void*)batch_step_kernel<0, false, 128, 1>;
+        case 3:
+            return sample ? (const void*)batch_step_kernel<0, true, 128, 2, kBatchNWTensor>
+                          : (const void*)batch_step_kernel<0, false, 128, 2, kBatchNWTensor>;
+        case 4:
+            return sample ? (const void*)batch_step_kernel<0, true, 64, 2, kBatchNWTensor>
+                          : (const void*)batch_step_kernel<0, false, 64, 2, kBatchNWTensor>;
         default:
             return nullptr;
     }
@@ -29,6 +35,8 @@ size_t batch_smem_bytes(int variant) {
         case 0: return BatchShape<128, 2>::smem_bytes();
         case 1: return BatchShape<64, 2>::smem_bytes();
         case 2: return BatchShape<128, 1>::smem_bytes();
+        case 3: return BatchShape<128, 2, kBatchNWTensor>::smem_bytes();
+        case 4: return BatchShape<64, 2, kBatchNWTensor>::smem_bytes();
         default: return 0;
     }
 }

@@ -15,6 +15,12 @@ const void* batch_kernel_loc(int variant, bool sample) {
         case 2:
             return sample ? (const void*)batch_step_kernel<1, true, 128, 1>
                           : (const void*)batch_step_kernel<1, false, 128, 1>;
+        case 3:
+            return sample ? (const void*)batch_step_kernel<1, true, 128, 2, kBatchNWTensor>
+                          : (const void*)batch_step_kernel<1, false, 128, 2, kBatchNWTensor>;
+        case 4:
+            return sample ? (const void*)batch_step_kernel<1, true, 64, 2, kBatchNWTensor>
+                          : (const void*)batch_step_kernel<1, false, 64, 2, kBatchNWTensor>;
         default:
             return nullptr;
     }

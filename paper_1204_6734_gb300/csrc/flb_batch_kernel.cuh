@@ -18,11 +18,15 @@
 // graph of k launches can be replayed while the host changes the membership
 // between replays: replica r is at time t_r = t0_r + (step - join_r).
 //
-// Tile shapes (the autotuner's choices): TW x TH nodes, 8 consumer warps,
+// Tile shapes (the autotuner's choices): TW x TH nodes, NW consumer warps,
 // NPT nodes per consumer thread (2: packed FP32x2 pairs at columns r and
-// r + TW/2; 1: scalar), TH = 8 * 32 * NPT / TW. The register file bounds the
-// warp count: a consumer needs about 160 registers in the f-norm, a sampler
-// 108 for its packed sums, and 8 consumers + 4 samplers fill the SM.
+// r + TW/2; 1: scalar), TH = NW * 32 * NPT / TW. The register file bounds the
+// warp count: with 8 consumers (about 160 registers each in the f-norm) the
+// correlation sums come from 4 sampler warps (108 registers for their packed
+// sums); with 12 consumers (at most 128 registers) the consumers add their own
+// nodes to a Gram matrix on the tensor cores (flb_gram.cuh), flushed per run
+// of tiles of one replica into FP64 sums in shared memory (the first
+// kRunSlots runs of the CTA) or straight into the replica's FP64 sums.
 #pragma once
 
 #include <cuda.h>
@@ -30,6 +34,7 @@
 
 #include <cstdint>
 
+#include "flb_gram.cuh"
 #include "flb_pipeline.cuh"
 
 namespace flb {
@@ -37,7 +42,8 @@ namespace flb {
 struct __align__(16) ReplicaHot {
     CollideConst<float> cc;   // -omega, amplitudes, Philox round keys
     float ref[9];             // f^0(rho0, u0), subtracted before sampling
-    int Lx, Ly, tiles_x, pad0;
+    int Lx, Ly, tiles_x;
+    float gram_inv;           // 1 / s of the tensor-core sums (0: not allowed)
     int t0, join;             // replica time t0 at batch step `join`
     int warmup, every;        // sampling schedule (every = 0: off)
     long long pitch, plane;
@@ -45,7 +51,7 @@ struct __align__(16) ReplicaHot {
     double* acc;              // kSums running sums
     DevError* err;
     int tend;                 // the replica stops before time tend
-    int pad1;
+    float gram_s;             // s = sqrt(kT rho0): nodes are staged as (f - ref) / s
 };
 static_assert(sizeof(ReplicaHot) == 256, "the hot block is copied as 256 bytes");
 
@@ -72,11 +78,14 @@ constexpr int kLocalBits = 18;
 constexpr uint32_t kLocalMask = (1u << kLocalBits) - 1u;
 constexpr int kMaxBatchReplicas = 1 << (32 - kLocalBits);
 
-constexpr int kBatchNW = 8;   // consumer warps
+constexpr int kBatchNW = 8;       // consumer warps beside sampler warps
+constexpr int kBatchNWTensor = 12;  // consumer warps with the tensor-core sums
+constexpr int kRunSlots = 4;        // runs of one replica whose sums a CTA keeps in shared memory
 
-template <int TW, int NPT>
+template <int TW, int NPT, int NW_ = kBatchNW>
 struct BatchShape {
-    static constexpr int NW = kBatchNW;
+    static constexpr int NW = NW_;
+    static constexpr bool TENSOR = NW > kBatchNW;
     static constexpr int TH = NW * 32 * NPT / TW;                // rows per tile
     static constexpr int BW = TW + 8;                            // box width: x0 - 4 .. x0 + TW + 3
     static constexpr int RW = TW / NPT;                          // consumer threads per row
@@ -87,8 +96,9 @@ struct BatchShape {
     static constexpr int STAGE = 9 * SPLANE + HOT + INFO;
     static constexpr int FIT = 163840 / (4 * STAGE);             // about 160 KB of stages
     static constexpr int STAGES = FIT < 16 ? FIT : 16;
+    static constexpr size_t GRAM = TENSOR ? (size_t)NW * kGramWarpHalves * 2 + kRunSlots * 256 * 8 + kRunSlots * 16 : 0;
     static constexpr size_t smem_bytes() {
-        return sizeof(float) * (size_t)STAGES * STAGE + 2 * STAGES * sizeof(uint64_t) + 16;
+        return sizeof(float) * (size_t)STAGES * STAGE + 2 * STAGES * sizeof(uint64_t) + 16 + GRAM;
     }
 };
 
@@ -117,9 +127,9 @@ struct TileFetch {
 // The global reads behind one tile (its code, then its replica's time and
 // geometry): done one tile ahead of the issue, so their latency overlaps the
 // producer's wait for the stage.
-template <int TW, int NPT>
+template <int TW, int NPT, int NW>
 __device__ __forceinline__ TileFetch batch_fetch(const BatchArgs& a, unsigned step, int t) {
-    using BS = BatchShape<TW, NPT>;
+    using BS = BatchShape<TW, NPT, NW>;
     TileFetch f;
     const uint32_t code = __ldg(&a.tiles[t]);
     f.d = a.desc + (code >> kLocalBits);
@@ -134,9 +144,9 @@ __device__ __forceinline__ TileFetch batch_fetch(const BatchArgs& a, unsigned st
     return f;
 }
 
-template <int TW, int NPT>
+template <int TW, int NPT, int NW>
 __device__ __forceinline__ void batch_issue(float* smem, const TileFetch& f, int s, uint64_t* full) {
-    using BS = BatchShape<TW, NPT>;
+    using BS = BatchShape<TW, NPT, NW>;
     float* st = smem + s * BS::STAGE;
     *reinterpret_cast<int4*>(st + 9 * BS::SPLANE + BS::HOT) = make_int4(f.x0, f.y0, f.tr, f.live ? 1 : 0);
     if (!f.live) {
@@ -152,20 +162,44 @@ __device__ __forceinline__ void batch_issue(float* smem, const TileFetch& f, int
     bulk_load(st + 9 * BS::SPLANE, &f.d->hot, sizeof(ReplicaHot), &full[s]);
 }
 
-// Warp roles: NW consumer warps, then one producer warp (SAMPLE = false) or
-// kSamplers sampler warps whose first lane also produces (SAMPLE = true).
-template <int BASIS, bool SAMPLE, int TW, int NPT>
-__global__ void __launch_bounds__((kBatchNW + (SAMPLE ? kSamplers : 1)) * 32, 1)
+// Add a thread's Gram partials (gram_flush's fragment) straight to a
+// replica's FP64 sums, scaled by s (first moments) and s^2 (second moments).
+__device__ __forceinline__ void gram_flush_global(float (&c)[8], double* acc, double sc) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int row = g + ((k & 2) ? 8 : 0);
+        const int col = 2 * q + (k & 1) + ((k & 4) ? 8 : 0);
+        if (row < 9 && col == 9)
+            atomicAdd(&acc[row], sc * (double)c[k]);
+        else if (row <= col && col < 9)
+            atomicAdd(&acc[9 + row * 9 - row * (row - 1) / 2 + (col - row)], sc * sc * (double)c[k]);
+        c[k] = 0.f;
+    }
+}
+
+// Warp roles: NW consumer warps, then one producer warp (SAMPLE = false, or
+// the tensor-core sums) or kSamplers sampler warps whose first lane also
+// produces (SAMPLE = true with 8 consumer warps).
+template <int BASIS, bool SAMPLE, int TW, int NPT, int NWC = kBatchNW>
+__global__ void __launch_bounds__((NWC + (SAMPLE && NWC == kBatchNW ? kSamplers : 1)) * 32, 1)
 batch_step_kernel(const BatchArgs a) {
-    using BS = BatchShape<TW, NPT>;
-    constexpr int NW = kBatchNW;
+    using BS = BatchShape<TW, NPT, NWC>;
+    constexpr int NW = NWC;
+    constexpr bool kTensor = SAMPLE && BS::TENSOR;
     constexpr int BW = BS::BW;
     constexpr int TH = BS::TH;
     constexpr int S = BS::STAGES;
-    constexpr int NX = SAMPLE ? kSamplers : 1;
+    constexpr int NX = SAMPLE && !kTensor ? kSamplers : 1;
     extern __shared__ __align__(128) float smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * BS::STAGE);
     uint64_t* empty = full + S;
+    // tensor-core sums: per-run FP64 Gram matrices (16 x 16, rows and columns
+    // 0..9 used), their replicas and scales, then the consumer warps' blocks
+    double* run_cm = reinterpret_cast<double*>(empty + S + 2);
+    double** run_acc = reinterpret_cast<double**>(run_cm + kRunSlots * 256);
+    double* run_s = reinterpret_cast<double*>(run_acc + kRunSlots);
+    __half* gram = reinterpret_cast<__half*>(run_s + kRunSlots);
 
     const int warp = threadIdx.x >> 5, lane_id = threadIdx.x & 31;
     const unsigned step = __ldcg(&a.ctl->step);
@@ -173,9 +207,13 @@ batch_step_kernel(const BatchArgs a) {
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], NW + (SAMPLE ? NX : 0));
+            mbar_init(&empty[s], NW + (SAMPLE && !kTensor ? NX : 0));
         }
         fence_mbar_init();
+    }
+    if (kTensor) {
+        for (int k = threadIdx.x; k < kRunSlots * 256; k += blockDim.x) run_cm[k] = 0.0;
+        if (warp < NW) gram_init(gram + warp * kGramWarpHalves);
     }
     __syncthreads();
 
@@ -191,10 +229,10 @@ batch_step_kernel(const BatchArgs a) {
         TileFetch nxt{};
         if (producer) {
             for (; issued < S && issued < ntile; ++issued)
-                batch_issue<TW, NPT>(smem, batch_fetch<TW, NPT>(a, step, tbeg + issued), issued, full);
-            if (issued < ntile) nxt = batch_fetch<TW, NPT>(a, step, tbeg + issued);
+                batch_issue<TW, NPT, NWC>(smem, batch_fetch<TW, NPT, NWC>(a, step, tbeg + issued), issued, full);
+            if (issued < ntile) nxt = batch_fetch<TW, NPT, NWC>(a, step, tbeg + issued);
         }
-        if (!SAMPLE) {
+        if (!SAMPLE || kTensor) {
             if (producer) {
                 for (; k < ntile && issued < ntile; ++k) {
                     const int s = k % S;
@@ -202,8 +240,8 @@ batch_step_kernel(const BatchArgs a) {
                         ok = false;
                         break;
                     }
-                    batch_issue<TW, NPT>(smem, nxt, s, full);
-                    if (++issued < ntile) nxt = batch_fetch<TW, NPT>(a, step, tbeg + issued);
+                    batch_issue<TW, NPT, NWC>(smem, nxt, s, full);
+                    if (++issued < ntile) nxt = batch_fetch<TW, NPT, NWC>(a, step, tbeg + issued);
                 }
                 if (!ok) {
                     record_error(first_err(), kStatusTimeout, -1, step);
@@ -297,8 +335,8 @@ batch_step_kernel(const BatchArgs a) {
                     ok = false;
                     break;
                 }
-                batch_issue<TW, NPT>(smem, nxt, s, full);
-                if (++issued < ntile) nxt = batch_fetch<TW, NPT>(a, step, tbeg + issued);
+                batch_issue<TW, NPT, NWC>(smem, nxt, s, full);
+                if (++issued < ntile) nxt = batch_fetch<TW, NPT, NWC>(a, step, tbeg + issued);
             }
         }
         flush();
@@ -314,6 +352,26 @@ batch_step_kernel(const BatchArgs a) {
     // ---------------- consumers
     const int c = threadIdx.x;
     const int ty = c / BS::RW, r = c % BS::RW;
+    // tensor-core sums: this warp's FP32 partials belong to run `run` (the
+    // run-th replica this CTA samples; every warp sees the same sequence)
+    float gc[kTensor ? 8 : 1];
+    if (kTensor) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) gc[q] = 0.f;
+    }
+    int run = -1, gtiles = 0;
+    const double* run_key = nullptr;
+    double run_scale = 0.0;
+    double* run_glob = nullptr;
+    const GramLane gl(kTensor ? smem_u32(gram + (c >> 5) * kGramWarpHalves) : 0u);
+    auto gram_out = [&]() {
+        if (run < 0) return;
+        if (run < kRunSlots)
+            gram_flush(reinterpret_cast<float(&)[8]>(gc), run_cm + run * 256);
+        else
+            gram_flush_global(reinterpret_cast<float(&)[8]>(gc), run_glob, run_scale);
+        gtiles = 0;
+    };
     for (int k = 0; k < ntile; ++k) {
         const int s = k % S;
         if (!mbar_wait(&full[s], (k / S) & 1)) {
@@ -351,10 +409,44 @@ batch_step_kernel(const BatchArgs a) {
             const int xA = info.x + r, xB = xA + TW / 2;
             const bool inA = xA < geo.Lx && y < geo.Ly, inB = xB < geo.Lx && y < geo.Ly;
             const uint32_t nodeA = (uint32_t)xA + (uint32_t)geo.Lx * (uint32_t)y;
+            const bool smp = kTensor && sampled_at(hs, (int)tr);
+            if (smp && hs.acc != run_key) {   // a new run of sampled tiles
+                gram_out();
+                ++run;
+                run_key = hs.acc;
+                run_glob = hs.acc;
+                run_scale = (double)hs.gram_s;
+                if (run < kRunSlots && lane_id == 0) {
+                    run_acc[run] = hs.acc;
+                    run_s[run] = run_scale;
+                }
+            }
+            // stage the nodes when the collision reads them a second time (the
+            // table f-norm reads them once: stage now)
+            auto stage = [&](const f2* gs) {
+                const float inv = hs.gram_inv;
+                f2 hv[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) hv[i] = mad(gs[i], f2(inv), f2(-hs.ref[i] * inv));
+                if (!(inA && inB)) {
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) hv[i] = f2(inA ? hv[i].v.x : 0.f, inB ? hv[i].v.y : 0.f);
+                }
+                gram_stage(gl, hv);
+            };
+            auto refetch = [&](f2* gg) {
+                load(gg);
+                if (kTensor && BASIS != 2 && smp) stage(gg);
+            };
+            if (kTensor && BASIS == 2 && smp) stage(g);
             f2 f[9];
             const uint32_t stt = collide_basis<f2, BASIS>(
-                g, PairNoise{hs.cc.key, nodeA, nodeA + TW / 2, tr}, load,
+                g, PairNoise{hs.cc.key, nodeA, nodeA + TW / 2, tr}, refetch,
                 a.lut, hs.cc, f);
+            if (kTensor && smp) {
+                gram_mma(gl, reinterpret_cast<float(&)[8]>(gc));
+                if (++gtiles == kGramFlushTiles) gram_out();
+            }
             __syncwarp();
             if (lane_id == 0) mbar_arrive(&empty[s]);
             if (stt) {
@@ -394,6 +486,15 @@ batch_step_kernel(const BatchArgs a) {
             }
         }
     }
+    if (kTensor) {
+        gram_out();
+        named_sync(1, NW * 32);
+        const int nrun = run + 1 < kRunSlots ? run + 1 : kRunSlots;
+        for (int k = c; k < nrun * kSums; k += NW * 32) {
+            const int j = k / kSums, q = k - j * kSums;
+            atomicAdd(&run_acc[j][q], gram_sum(run_cm + j * 256, q, run_s[j]));
+        }
+    }
     // the last CTA to finish advances the batch step (every CTA read it at its start)
     if (c == 0) {
         __threadfence();
@@ -404,13 +505,16 @@ batch_step_kernel(const BatchArgs a) {
     }
 }
 
-// Tile shapes the batch can run; index = FLB_TILE_* of flb.h.
+// Tile shapes the batch can run; index = FLB_TILE_* of flb.h. Shapes with 12
+// consumer warps take their correlation sums on the tensor cores.
 struct BatchVariant {
-    int tw, npt;
-    __host__ __device__ constexpr int th() const { return kBatchNW * 32 * npt / tw; }
+    int tw, npt, nw;
+    __host__ __device__ constexpr int th() const { return nw * 32 * npt / tw; }
+    __host__ __device__ constexpr bool tensor() const { return nw > kBatchNW; }
 };
-constexpr BatchVariant kBatchVariants[3] = {{128, 2}, {64, 2}, {128, 1}};
-constexpr int kNumBatchVariants = 3;
+constexpr BatchVariant kBatchVariants[5] = {{128, 2, kBatchNW}, {64, 2, kBatchNW}, {128, 1, kBatchNW},
+                                            {128, 2, kBatchNWTensor}, {64, 2, kBatchNWTensor}};
+constexpr int kNumBatchVariants = 5;
 
 // Kernel of (variant, basis, sampling), instantiated in flb_batch_k<basis>.cu.
 const void* batch_kernel_std(int variant, bool sample);

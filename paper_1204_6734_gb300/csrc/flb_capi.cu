@@ -88,11 +88,11 @@ __global__ void __launch_bounds__(kStepThreads)
 conservation_kernel(const T* src, Geometry geo, double* partials, DevCodec codec) {
     const long long N = (long long)geo.Lx * geo.Ly;
     double r = 0.0, jx = 0.0, jy = 0.0;
-    // the interior of the buffer is a permutation of the pre-collision state
+    // the pre-collision state f_i(x) = f*_i(x - v_i)
     for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < (int)N; n += gridDim.x * blockDim.x) {
         const int y = n / geo.Lx, x = n - y * geo.Lx;
         for (int i = 0; i < 9; ++i) {
-            const double v = pop_value(src, at(geo, i, x, y), i, codec);
+            const double v = pop_value(src, pull_at(geo, i, x, y), i, codec);
             r += v;
             jx += v * cvx(i);
             jy += v * cvy(i);
@@ -134,7 +134,7 @@ struct StateView {
     Geometry geo;
     DevCodec codec;
     __device__ __forceinline__ double get(int i, int x, int y) const {
-        const long long k = at(geo, i, wrap(x - cvx(i), geo.Lx), wrap(y - cvy(i), geo.Ly));
+        const long long k = pull_at(geo, i, x, y);
         if (prec == FLB_FP64) return ((const double*)buf)[k];
         if (prec == FLB_FP32) return (double)((const float*)buf)[k];
         return dev_decode(codec, i, ((const __half*)buf)[k]);
@@ -230,6 +230,41 @@ __global__ void collide_nodes_kernel(const double* g, const uint32_t* ids, uint3
 
 using namespace flb;
 
+// Halo of a slab (flb_set_slab): the populations that cross its y boundaries.
+// Moving up (v_y = +1): 2, 5, 6; moving down (v_y = -1): 4, 7, 8.
+__device__ __constant__ int kHaloUp[3] = {2, 5, 6};
+__device__ __constant__ int kHaloDown[3] = {4, 7, 8};
+
+// lo: f*_i(x, 0) for i moving down (to the slab below); hi: f*_i(x, Ly - 1) for
+// i moving up (to the slab above); each 3 rows of Lx values.
+template <class T>
+__global__ void halo_pack_kernel(const T* buf, Geometry geo, T* lo, T* hi) {
+    const int Lx = geo.Lx;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < 6 * Lx; k += gridDim.x * blockDim.x) {
+        const int q = k / Lx, x = k - q * Lx;
+        if (q < 3)
+            lo[k] = buf[at(geo, kHaloDown[q], x, 0)];
+        else
+            hi[k - 3 * Lx] = buf[at(geo, kHaloUp[q - 3], x, geo.Ly - 1)];
+    }
+}
+
+// The ghost rows the next pull reads across the y boundaries: row -1 (i moving
+// up) from the slab below's hi, row Ly (i moving down) from the slab above's
+// lo, columns -1 .. Lx with the lattice's periodicity in x.
+template <class T>
+__global__ void halo_unpack_kernel(T* buf, Geometry geo, const T* lo, const T* hi) {
+    const int Lx = geo.Lx, W = Lx + 2;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < 6 * W; k += gridDim.x * blockDim.x) {
+        const int q = k / W, c = k - q * W - 1;
+        const int x = wrap(c, Lx);
+        if (q < 3)
+            buf[at(geo, kHaloUp[q], c, -1)] = lo[q * Lx + x];
+        else
+            buf[at(geo, kHaloDown[q - 3], c, geo.Ly)] = hi[(q - 3) * Lx + x];
+    }
+}
+
 struct flb_lattice_s {
     flb_params p;
     int elem;            // bytes per population value
@@ -255,6 +290,11 @@ struct flb_lattice_s {
     double ref[9];
     StructSampler* sk = nullptr;      // structure factors (allocated on demand)
     int64_t sk_warmup = 0, sk_every = 0;
+    // slab of a larger periodic lattice (flb_set_slab): rows y0 .. y0 + Ly - 1
+    // of Ly_total; node0 = Lx y0 offsets the noise counters
+    bool slab = false;
+    int slab_y0 = 0, slab_Ly_total = 0;
+    uint32_t node0 = 0;
 };
 
 namespace {
@@ -315,6 +355,7 @@ cudaError_t launch_step_t(flb_lattice h) {
     a.dst = (T*)h->buf[h->cur ^ 1];
     a.geo = h->geo;
     a.step = (uint32_t)h->t;
+    a.node0 = h->node0;
     a.partials = h->partials;
     a.err = h->err;
     a.lut = (const T*)(sizeof(T) == 8 ? (const void*)h->lut64 : (const void*)h->lut32);
@@ -339,6 +380,7 @@ cudaError_t launch_step_tma(flb_lattice h, bool sample) {
     a.dst = (float*)h->buf[h->cur ^ 1];
     a.geo = h->geo;
     a.step = (uint32_t)h->t;
+    a.node0 = h->node0;
     a.tiles_x = a.ntiles = 0;
     a.acc = h->acc;
     a.err = h->err;
@@ -371,6 +413,7 @@ cudaError_t launch_step_fp16(flb_lattice h, bool sample) {
     a.dst = (__half*)h->buf[h->cur ^ 1];
     a.geo = h->geo;
     a.step = (uint32_t)h->t;
+    a.node0 = h->node0;
     a.tiles_x = a.ntiles = 0;
     a.acc = h->acc;
     a.err = h->err;
@@ -464,8 +507,10 @@ int lattice_create(const flb_params* p, void* dev_workspace, size_t workspace_by
     }
     if (ce == cudaSuccess && sync) ce = cudaStreamSynchronize(h->stream);
     // sampling steps: the correlation sums on the tensor cores, 12 colliding
-    // warps, where the parameters allow it; otherwise the sampler warps
-    const bool tensor = tensor_sampling_ok(p);
+    // warps, where the parameters allow it; otherwise, and for the table
+    // f-norm (whose table rows take the registers 12 warps leave), the sampler
+    // warps beside 8 colliding warps
+    const bool tensor = tensor_sampling_ok(p) && p->basis != FLB_BASIS_LOCAL_LUT;
     h->tma.sample_mode = tensor ? kPlanTensorSampling : 0;
     if (ce == cudaSuccess && p->basis == FLB_BASIS_LOCAL_LUT &&
         lut_tables(&h->lut32, &h->lut64) != FLB_OK)
@@ -473,11 +518,12 @@ int lattice_create(const flb_params* p, void* dev_workspace, size_t workspace_by
     h->tma_quiet.ready = false;
     if (ce == cudaSuccess && p->precision == FLB_FP32) {
         ce = tma_plan(&h->tma, h->buf[0], h->buf[1], h->geo, tensor ? kTensorNW : 0);
-        // steps without sampling in the f-norm bases: 12 colliding warps
-        // (measured 56.7 against 53.5 GLUPS at 4096^2; the Hermite norm and
-        // sampling steps are faster with 8)
-        if (ce == cudaSuccess && p->basis != FLB_BASIS_STANDARD &&
-            tma_plan(&h->tma_quiet, h->buf[0], h->buf[1], h->geo, 12) != cudaSuccess) {
+        // steps without sampling: 12 colliding warps in the f-norm bases
+        // (measured 56.7 against 53.5 GLUPS at 4096^2 with 8), 8 in the
+        // Hermite norm (73-79 GLUPS)
+        const int quiet_nw = p->basis == FLB_BASIS_STANDARD ? 8 : 12;
+        if (ce == cudaSuccess && quiet_nw != h->tma.nw &&
+            tma_plan(&h->tma_quiet, h->buf[0], h->buf[1], h->geo, quiet_nw) != cudaSuccess) {
             cudaGetLastError();
             h->tma_quiet.ready = false;
         }
@@ -547,6 +593,33 @@ int finalize_sums(const double* acc, int64_t nsamp, int32_t measure_basis, doubl
 
 }  // namespace flb
 
+namespace {
+template <class T>
+cudaError_t halo_call(flb_lattice h, bool pack, void* lo, void* hi) {
+    const int n = 6 * (h->p.Lx + 2);
+    const int grid = (n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024;
+    if (pack)
+        halo_pack_kernel<T><<<grid, 256, 0, h->stream>>>((const T*)h->buf[h->cur], h->geo, (T*)lo,
+                                                          (T*)hi);
+    else
+        halo_unpack_kernel<T><<<grid, 256, 0, h->stream>>>((T*)h->buf[h->cur], h->geo,
+                                                            (const T*)lo, (const T*)hi);
+    return cudaGetLastError();
+}
+int halo(flb_lattice h, bool pack, void* lo, void* hi) {
+    if (!h || !lo || !hi || !h->slab) return FLB_ERR_ARG;
+    if (h->sticky) return h->sticky;
+    cudaError_t ce;
+    if (h->p.precision == FLB_FP64)
+        ce = halo_call<double>(h, pack, lo, hi);
+    else if (h->p.precision == FLB_FP32)
+        ce = halo_call<float>(h, pack, lo, hi);
+    else
+        ce = halo_call<__half>(h, pack, lo, hi);
+    return cuda_rc(ce);
+}
+}  // namespace
+
 extern "C" {
 
 int flb_version(void) { return 100; }
@@ -602,6 +675,7 @@ int flb_set_sampling(flb_lattice h, int64_t warmup, int64_t every) {
 
 int flb_set_structure_sampling(flb_lattice h, int64_t warmup, int64_t every) {
     if (!h || warmup < 0 || every < 0) return FLB_ERR_ARG;
+    if (h->slab && every > 0) return FLB_ERR_ARG;   // the transform spans the whole lattice
     if (h->sticky) return h->sticky;
     if (every > 0 && !h->sk) {
         const int rc = structure_create(&h->sk, h->p.Lx, h->p.Ly,
@@ -687,6 +761,28 @@ int flb_set_option(flb_lattice h, int32_t option, int32_t value) {
         return FLB_OK;
     }
     return FLB_ERR_ARG;
+}
+
+int flb_set_slab(flb_lattice h, int32_t Ly_total, int32_t y0) {
+    if (!h || y0 < 0 || Ly_total < 1 || (long long)y0 + h->p.Ly > Ly_total) return FLB_ERR_ARG;
+    if ((long long)h->p.Lx * Ly_total > 0xFFFFFFFFLL) return FLB_ERR_ARG;
+    if (h->sk_every > 0) return FLB_ERR_ARG;   // structure factors are whole-lattice quantities
+    h->slab = true;
+    h->slab_y0 = y0;
+    h->slab_Ly_total = Ly_total;
+    h->node0 = (uint32_t)h->p.Lx * (uint32_t)y0;
+    return FLB_OK;
+}
+
+size_t flb_halo_bytes(flb_lattice h) {
+    if (!h) return 0;
+    return (size_t)3 * h->p.Lx * elem_size(h->p.precision);
+}
+
+int flb_halo_pack(flb_lattice h, void* dev_lo, void* dev_hi) { return halo(h, true, dev_lo, dev_hi); }
+
+int flb_halo_unpack(flb_lattice h, const void* dev_lo, const void* dev_hi) {
+    return halo(h, false, const_cast<void*>(dev_lo), const_cast<void*>(dev_hi));
 }
 
 int flb_sync(flb_lattice h) {

@@ -62,18 +62,13 @@ __device__ __forceinline__ void node_normals(const NoiseKey& key, uint32_t nodeA
 
 // The six noise increments xi^a N^a = sqrt(rho) amp_a N^a (Eqs. FDT, noiseamp)
 // of the FP32 collisions, with sqrt(rho) and amp_a folded into the Box-Muller
-// radius: rho (-2 ln u1) is formed before the square root, with
-// -2 ln u1 = 2 ln2 (21 - log2(k + 1)) for u1 = (k + 1) 2^-21. One node (scalar
-// lanes) or a node pair (packed lanes) take the same operations per lane, so
-// both give bit-identical increments. FP64 uses unit normals (operator()).
+// radius: r = sqrt(rho (-2 ln2) log2(u1)), u1 = (k + 1) 2^-21 formed exactly,
+// so that log2 is taken where the SFU is accurate in absolute terms (near
+// u1 = 1, the draws with the smallest radius; u1 = 1 gives r = 0 exactly). One
+// node (scalar lanes) or a node pair (packed lanes) take the same operations
+// per lane, so both give bit-identical increments. FP64 uses unit normals
+// (operator()).
 constexpr float kLn2x2 = 1.3862943611198906f;
-
-__device__ __forceinline__ float bm_radius2(uint32_t k) {
-    return fmaf(__log2f((float)(k + 1u)), -kLn2x2, 21.f * kLn2x2);
-}
-__device__ __forceinline__ float bm_angle(uint32_t k) {
-    return (float)((int)k - (1 << 20)) * (float)(kTwoPi * 0x1p-21);
-}
 
 struct NodeNoise {
     const NoiseKey& key;
@@ -85,11 +80,14 @@ struct NodeNoise {
     __device__ __forceinline__ void scaled(float rho, const float (&amp)[6], float n[6]) const {
         uint32_t k[6];
         node_fields(key, node, step, k);
+        const float nr = rho * -kLn2x2;
 #pragma unroll
         for (int p = 0; p < 3; ++p) {
-            const float r = sqr(bm_radius2(k[2 * p]) * rho);
+            const float u1 = (float)(k[2 * p] + 1u) * 0x1p-21f;
+            const float r = sqr(__log2f(u1) * nr);
+            const float t = (float)((int)k[2 * p + 1] - (1 << 20)) * (float)(kTwoPi * 0x1p-21);
             float s, c;
-            __sincosf(bm_angle(k[2 * p + 1]), &s, &c);
+            __sincosf(t, &s, &c);
             // cos(t + pi) = -cos t, sin(t + pi) = -sin t
             n[2 * p] = (r * -amp[2 * p]) * c;
             n[2 * p + 1] = (r * -amp[2 * p + 1]) * s;
@@ -104,10 +102,11 @@ struct PairNoise {
         uint32_t ka[6], kb[6];
         node_fields(key, nodeA, step, ka);
         node_fields(key, nodeB, step, kb);
+        const f2 nr = rho * f2(-kLn2x2);
 #pragma unroll
         for (int p = 0; p < 3; ++p) {
-            const f2 lg(__log2f((float)(ka[2 * p] + 1u)), __log2f((float)(kb[2 * p] + 1u)));
-            const f2 r = sqr(mad(lg, f2(-kLn2x2), f2(21.f * kLn2x2)) * rho);
+            const f2 u1 = f2((float)(ka[2 * p] + 1u), (float)(kb[2 * p] + 1u)) * f2(0x1p-21f);
+            const f2 r = sqr(f2(__log2f(u1.v.x), __log2f(u1.v.y)) * nr);
             const f2 t = f2((float)((int)ka[2 * p + 1] - (1 << 20)),
                             (float)((int)kb[2 * p + 1] - (1 << 20))) * f2((float)(kTwoPi * 0x1p-21));
             float sa, ca, sb, cb;

@@ -49,39 +49,62 @@ __device__ __forceinline__ void mma16816(float (&c)[8], int o, uint32_t a0, uint
         : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
-// Stage the 64 nodes of this warp (h: node A of the thread in .x, node B in .y,
-// already scaled by 1/s and zero for nodes outside the lattice) in the block
-// at shared address blk: thread `lane` owns columns 2 lane (A) and 2 lane + 1
-// (B). The warp must have finished reading the block's previous contents.
-__device__ __forceinline__ void gram_stage(uint32_t blk, const f2 (&h)[9]) {
-    const uint32_t w = blk + 4u * (threadIdx.x & 31);
-    __syncwarp();
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const __half2 v = __floats2half2_rn(h[i].v.x, h[i].v.y);
-        asm volatile("st.shared.b32 [%0], %1;" ::"r"(w + 2u * kGramRowHalves * i),
-                     "r"(*reinterpret_cast<const uint32_t*>(&v)));
+// Shared addresses of one thread in its warp's block, computed once: the
+// word it stages (column pair 2 lane, 2 lane + 1 of row 0) and the row its
+// ldmatrix lanes address (threads 8m..8m+7 give the rows of matrix m; the
+// matrices (rows 0-7, k 0-7), (rows 8-15, k 0-7), (rows 0-7, k 8-15),
+// (rows 8-15, k 8-15) of a 16-node step are the A fragment of
+// mma.m16n8k16, and H^T's B fragments of the column blocks 0-7 and 8-15 are
+// matrices (0, 2) and (1, 3)).
+struct GramLane {
+    uint32_t st, ld;
+    __device__ __forceinline__ explicit GramLane(uint32_t blk) {
+        const int lane = threadIdx.x & 31, m = lane >> 3, r = lane & 7;
+        st = blk + 4u * lane;
+        ld = blk + 2u * (((m & 1) * 8 + r) * kGramRowHalves + (m >> 1) * 8);
     }
+};
+
+template <int I>
+__device__ __forceinline__ void gram_store(uint32_t st, f2 h) {
+    const __half2 v = __floats2half2_rn(h.v.x, h.v.y);
+    asm volatile("st.shared.b32 [%0+%1], %2;" ::"r"(st), "n"(2 * kGramRowHalves * I),
+                 "r"(*reinterpret_cast<const uint32_t*>(&v)));
+}
+
+template <int S>
+__device__ __forceinline__ void gram_step(uint32_t ld, float (&c)[8]) {
+    uint32_t d0, d1, d2, d3;
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4+%5];"
+                 : "=r"(d0), "=r"(d1), "=r"(d2), "=r"(d3)
+                 : "r"(ld), "n"(32 * S));
+    mma16816(c, 0, d0, d1, d2, d3, d0, d2);
+    mma16816(c, 4, d0, d1, d2, d3, d1, d3);
+}
+
+// Stage the 64 nodes of this warp (h: node A of the thread in .x, node B in .y,
+// already scaled by 1/s and zero for nodes outside the lattice). The warp must
+// have finished reading the block's previous contents.
+__device__ __forceinline__ void gram_stage(const GramLane& g, const f2 (&h)[9]) {
+    __syncwarp();
+    gram_store<0>(g.st, h[0]);
+    gram_store<1>(g.st, h[1]);
+    gram_store<2>(g.st, h[2]);
+    gram_store<3>(g.st, h[3]);
+    gram_store<4>(g.st, h[4]);
+    gram_store<5>(g.st, h[5]);
+    gram_store<6>(g.st, h[6]);
+    gram_store<7>(g.st, h[7]);
+    gram_store<8>(g.st, h[8]);
 }
 
 // Add the staged block to c: four 16-node steps of two mma.m16n8k16 each.
-__device__ __forceinline__ void gram_mma(uint32_t blk, float (&c)[8]) {
+__device__ __forceinline__ void gram_mma(const GramLane& g, float (&c)[8]) {
     __syncwarp();
-    // ldmatrix.x4: threads 8m..8m+7 address the rows of matrix m; matrices
-    // (rows 0-7, k 0-7), (rows 8-15, k 0-7), (rows 0-7, k 8-15), (rows 8-15,
-    // k 8-15) of each 16-node step are the A fragment, and H^T's B fragments of
-    // the column blocks 0-7 and 8-15 are matrices (0, 2) and (1, 3).
-    const int lane = threadIdx.x & 31, m = lane >> 3, r = lane & 7;
-    const uint32_t a = blk + 2u * (((m & 1) * 8 + r) * kGramRowHalves + (m >> 1) * 8);
-#pragma unroll
-    for (int s = 0; s < 4; ++s) {
-        uint32_t d0, d1, d2, d3;
-        asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-                     : "=r"(d0), "=r"(d1), "=r"(d2), "=r"(d3)
-                     : "r"(a + 32u * s));
-        mma16816(c, 0, d0, d1, d2, d3, d0, d2);
-        mma16816(c, 4, d0, d1, d2, d3, d1, d3);
-    }
+    gram_step<0>(g.ld, c);
+    gram_step<1>(g.ld, c);
+    gram_step<2>(g.ld, c);
+    gram_step<3>(g.ld, c);
 }
 
 // Add the FP32 partials to the FP64 matrix cm[16][16] (rows and columns 0..9

@@ -14,6 +14,7 @@ struct TmaArgs {
     float* dst;             // buffer receiving f*(t)
     Geometry geo;
     uint32_t step;
+    uint32_t node0;         // noise counter of node (0, 0) (slabs: Lx y0)
     int tiles_x, ntiles;    // 128 x TH tiles of the lattice
     double* acc;            // running FP64 sums (sampling)
     DevError* err;
@@ -56,6 +57,7 @@ struct HArgs {
     __half* dst;            // buffer receiving h*(t)
     Geometry geo;
     uint32_t step;
+    uint32_t node0;         // noise counter of node (0, 0) (slabs: Lx y0)
     int tiles_x, ntiles;
     double* acc;            // running FP64 sums of f - ref (sampling)
     DevError* err;

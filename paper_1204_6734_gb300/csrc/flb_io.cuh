@@ -30,10 +30,7 @@ __global__ void gather_state_kernel(const T* buf, Geometry geo, double* out) {
     const long long N = (long long)geo.Lx * geo.Ly;
     for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < (int)N; n += gridDim.x * blockDim.x) {
         const int y = n / geo.Lx, x = n - y * geo.Lx;
-        for (int i = 0; i < 9; ++i) {
-            const int xs = wrap(x - cvx(i), geo.Lx), ys = wrap(y - cvy(i), geo.Ly);
-            out[i * N + n] = (double)buf[at(geo, i, xs, ys)];
-        }
+        for (int i = 0; i < 9; ++i) out[i * N + n] = (double)buf[pull_at(geo, i, x, y)];
     }
 }
 
@@ -71,10 +68,7 @@ static __global__ void gather_dev_kernel(const __half* buf, Geometry geo, DevCod
     const long long N = (long long)geo.Lx * geo.Ly;
     for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < (int)N; n += gridDim.x * blockDim.x) {
         const int y = n / geo.Lx, x = n - y * geo.Lx;
-        for (int i = 0; i < 9; ++i) {
-            const int xs = wrap(x - cvx(i), geo.Lx), ys = wrap(y - cvy(i), geo.Ly);
-            out[i * N + n] = dev_decode(c, i, buf[at(geo, i, xs, ys)]);
-        }
+        for (int i = 0; i < 9; ++i) out[i * N + n] = dev_decode(c, i, buf[pull_at(geo, i, x, y)]);
     }
 }
 

@@ -37,6 +37,7 @@ struct StepArgs {
     T* dst;
     Geometry geo;
     uint32_t step;
+    uint32_t node0;     // noise counter of node (0, 0): Lx y0 for a slab starting at row y0
     double* partials;   // [gridDim.x][kSums] when sampling
     DevError* err;
     const T* lut;       // velocity table (look-up-table f-norm only)
@@ -109,13 +110,13 @@ step_kernel(StepArgs<T> a, CollideConst<T> cc) {
         }
         T f[9];
         const uint32_t st = collide_basis<T, BASIS>(
-            g, NodeNoise{cc.key, (uint32_t)n, a.step},
+            g, NodeNoise{cc.key, a.node0 + (uint32_t)n, a.step},
             [&](T* gg) {
 #pragma unroll
                 for (int i = 0; i < 9; ++i) gg[i] = g[i];
             },
             a.lut, cc, f);
-        if (st != kStatusOk) record_error(a.err, (int)(st & 0xFF), n, a.step);
+        if (st != kStatusOk) record_error(a.err, (int)(st & 0xFF), (long long)a.node0 + n, a.step);
         store_node(a.dst, a.geo, x, y, f);
     }
     if (SAMPLE) block_reduce_sums<A>(s, a.partials + (long long)blockIdx.x * kSums);

@@ -41,6 +41,15 @@ __host__ __device__ __forceinline__ long long at(const Geometry& g, int i, int x
     return (long long)i * g.plane + (long long)(y + 1) * g.pitch + (x + kXO);
 }
 
+// The cell the pull of f_i at interior node (x, y) reads: x - v_i, a ghost cell
+// at the edge of the lattice. Every writer keeps these cells current (the step
+// kernels and the state scatter write the ghost copies; a slab's ghost rows
+// are written by the halo exchange), so readers of the pre-collision state use
+// this cell rather than its periodic image.
+__host__ __device__ __forceinline__ long long pull_at(const Geometry& g, int i, int x, int y) {
+    return at(g, i, x - cvx(i), y - cvy(i));
+}
+
 __host__ __device__ __forceinline__ int wrap(int a, int L) {
     return a < 0 ? a + L : (a >= L ? a - L : a);
 }

@@ -219,7 +219,7 @@ step_fp16_kernel(const __grid_constant__ CUtensorMap map, const HArgs a,
         const int x0 = (t % a.tiles_x) * kTW, y = (t / a.tiles_x) * TH + ty;
         const int xA = x0 + r, xB = xA + 64;
         const bool inA = xA < Lx && y < Ly, inB = xB < Lx && y < Ly;
-        const uint32_t nodeA = (uint32_t)xA + (uint32_t)Lx * (uint32_t)y;
+        const uint32_t nodeA = a.node0 + (uint32_t)xA + (uint32_t)Lx * (uint32_t)y;
         f2 f[9];
         const uint32_t stt = collide_basis<f2, BASIS>(
             g, PairNoise{cc.key, nodeA, nodeA + 64u, a.step}, load, a.lut, cc, f);

@@ -300,7 +300,7 @@ step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
         for (int q = 0; q < 8; ++q) gc[q] = 0.f;
     }
     int gtiles = 0;
-    const uint32_t gblk = smem_u32(gram + warp * kGramWarpHalves);
+    const GramLane gblk(smem_u32(gram + warp * kGramWarpHalves));
     int k = 0;
     TileWalk w(blockIdx.x, gridDim.x, a.tiles_x);
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++k, w.next()) {
@@ -351,7 +351,7 @@ step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
             if (kTensor && BASIS != 2) stage(gg);
         };
         if (kTensor && BASIS == 2) stage(g);
-        const uint32_t nodeA = (uint32_t)xA + (uint32_t)Lx * (uint32_t)y;
+        const uint32_t nodeA = a.node0 + (uint32_t)xA + (uint32_t)Lx * (uint32_t)y;
         f2 f[9];
         const uint32_t stt = collide_basis<f2, BASIS>(
             g, PairNoise{cc.key, nodeA, nodeA + 64u, a.step}, refetch, a.lut,

@@ -77,10 +77,7 @@ __device__ __forceinline__ void node_fields(const T* buf, const Geometry& geo, c
                                             const Ref9<R>& c, int x, int y, R& r, R& jx, R& jy) {
     R d[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const int xs = wrap(x - cvx(i), geo.Lx), ys = wrap(y - cvy(i), geo.Ly);
-        d[i] = pop_dev(buf, at(geo, i, xs, ys), i, codec, c);
-    }
+    for (int i = 0; i < 9; ++i) d[i] = pop_dev(buf, pull_at(geo, i, x, y), i, codec, c);
     r = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
     jx = (d[1] - d[3]) + ((d[5] - d[6]) + (d[8] - d[7]));
     jy = (d[2] - d[4]) + ((d[5] + d[6]) - (d[7] + d[8]));

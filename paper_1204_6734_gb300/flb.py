@@ -26,8 +26,8 @@ BASIS = {"standard": 0, "local": 1, "lut": 2}
 OPT_KERNEL, OPT_PIPELINE_WARPS, OPT_PIPELINE_SAMPLING = 0, 1, 2
 KERNEL = {"auto": 0, "generic": 1, "pipelined": 2}
 PRECISION = {"fp64": 0, "fp32": 1, "fp16dev": 2}
-TILE = {"128x4": 0, "64x8": 1, "128x2": 2}   # tile shapes of the batched kernel
-TILE_COUNT = 3
+TILE = {"128x4": 0, "64x8": 1, "128x2": 2, "128x6": 3, "64x12": 4}   # tile shapes of the batched kernel
+TILE_COUNT = 5
 
 
 class FlbError(RuntimeError):
@@ -112,6 +112,10 @@ def load(build_if_missing: bool = True):
                                       C.c_int32, _u32p, _dp]),
         "flb_collide_nodes": (C.c_int, [P, _dp, _u32p, C.c_uint32, C.c_int32, _dp, _i32p]),
         "flb_set_option": (C.c_int, [h, C.c_int32, C.c_int32]),
+        "flb_set_slab": (C.c_int, [h, C.c_int32, C.c_int32]),
+        "flb_halo_bytes": (C.c_size_t, [h]),
+        "flb_halo_pack": (C.c_int, [h, C.c_void_p, C.c_void_p]),
+        "flb_halo_unpack": (C.c_int, [h, C.c_void_p, C.c_void_p]),
         "flb_step_noalloc": (C.c_int, [P, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, _dp, _dp,
                                        C.c_void_p]),
         "flb_batch_open": (C.c_int, [C.c_int32, C.c_int32, C.c_size_t, C.c_void_p, C.POINTER(h)]),
@@ -162,6 +166,7 @@ def exported_symbols():
             "flb_reset_error", "flb_correlations", "flb_raw_sums", "flb_conservation",
             "flb_get_populations", "flb_set_populations", "flb_run_host", "flb_noise_draws",
             "flb_collide_nodes", "flb_set_option", "flb_step_noalloc", "flb_error_string",
+            "flb_set_slab", "flb_halo_bytes", "flb_halo_pack", "flb_halo_unpack",
             "flb_version", "flb_state_difference", "flb_batch_open", "flb_batch_replica_bytes", "flb_batch_add",
             "flb_batch_remove", "flb_batch_create", "flb_batch_workspace_bytes",
             "flb_batch_destroy", "flb_batch_set_sampling", "flb_batch_step",
@@ -397,6 +402,27 @@ def flb_step_noalloc(p, dev_f, dev_work, t0, nsteps, stream=None):
     _check(load().flb_step_noalloc(C.byref(s), f, w, int(t0), int(nsteps), _ptr(S1), _ptr(S2),
                                    _stream_handle(stream)), "flb_step_noalloc")
     return S1, S2
+
+
+def flb_set_slab(h, Ly_total: int, y0: int):
+    _check(load().flb_set_slab(h, int(Ly_total), int(y0)), "flb_set_slab")
+
+
+def flb_halo_bytes(h) -> int:
+    return int(load().flb_halo_bytes(h))
+
+
+def _dev_ptr(x):
+    return x if isinstance(x, int) else int(x.data_ptr())
+
+
+def flb_halo_pack(h, lo, hi):
+    """lo, hi: device buffers (CUDA tensors or raw pointers) of flb_halo_bytes(h)."""
+    _check(load().flb_halo_pack(h, _dev_ptr(lo), _dev_ptr(hi)), "flb_halo_pack")
+
+
+def flb_halo_unpack(h, lo, hi):
+    _check(load().flb_halo_unpack(h, _dev_ptr(lo), _dev_ptr(hi)), "flb_halo_unpack")
 
 
 def _param_array(ps):

@@ -20,12 +20,11 @@ import os
 import numpy as np
 import pytest
 
+import sweeps
 from paper_1204_6734_gb300 import drift, inputs
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden", "paper_q_coefficients.json")
-KT = 1e-4
-OMEGA = inputs.omega_groups(1.0, 0.8, 1.0)
-US = np.array([0.05, 0.1, 0.15, 0.2, 0.25])
+KT, OMEGA, US = sweeps.KT, sweeps.OMEGA, sweeps.US
 
 
 def test_closed_forms_equal_the_mirrored_least_squares_fit():
@@ -72,19 +71,8 @@ def test_parities_of_the_hermite_rows(oracle):
 
 @pytest.fixture(scope="module")
 def oracle_sweep(oracle):
-    """Normalised moment correlators of oracle runs on the paper's 21 x 21
-    lattice (kT = 1e-4, shear 1.0, bulk 0.8, ghost 1.0), 6000 sampled steps at
-    each u_x0 in US, both norms, each measured in its own basis at u0."""
-    out = {}
-    for basis in ("standard", "local"):
-        D = []
-        for k, u in enumerate(US):
-            p = inputs.LatticeParams(21, 21, 1.0, u, 0.0, KT, OMEGA, basis, "fp64", seed=40 + k)
-            run = oracle.Run(p, warmup=500, every=1).step(6500)
-            C, _ = run.covariance()
-            D.append(drift.normalised(oracle.moment_covariance(C, basis, u, 0.0), KT, 1.0))
-        out[basis] = np.array(D)
-    return out
+    """Normalised moment correlators of the oracle's 21 x 21 sweep (tests/sweeps.py)."""
+    return {basis: sweeps.oracle_sweep(oracle, basis) for basis in ("standard", "local")}
 
 
 def test_mirror_map(oracle, oracle_sweep):

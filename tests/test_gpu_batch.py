@@ -104,8 +104,8 @@ def test_batch_against_oracle_with_sampling(basis, tile):
         f, (S1, S2, n) = res[k]
         assert np.abs(f - run.f).max() < 2e-6
         assert n == run.nsamp
-        np.testing.assert_allclose(S2, run.S2, rtol=2e-4, atol=1e-9 * n)
-        np.testing.assert_allclose(S1, run.S1, rtol=2e-4, atol=1e-7 * n)
+        # the 12-warp shapes take their sums on the tensor cores (FP16-staged deviations)
+        assert_sums_close(S1, S2, run.S1, run.S2, n, 2e-4, 1e-7 * n, 1e-9 * n)
 
 
 @pytest.mark.parametrize("basis", ALL_BASES)

@@ -85,6 +85,28 @@ def test_collide_nodes(basis, precision):
         assert np.abs(out - ref).max() < 2e-6 * g.sum(1).max()
 
 
+def test_fp32_noise_at_the_smallest_radius():
+    """Box-Muller at u1 = 1 (the 21-bit field 2^21 - 1): the radius, and the two
+    normals of the pair, are exactly 0; the FP32 collision forms the radius from
+    log2(u1), exact there, so the node collides as the FP64 oracle's does to
+    FP32 rounding even with a large noise amplitude."""
+    import philox_np
+    om = inputs.omega_groups(1.3, 0.7, 1.6)
+    for basis in BASES:
+        p = inputs.LatticeParams(1, 1, 1.0, 0.0, 0.0, 1e-2, om, basis, "fp32", seed=99)
+        cand = np.arange(1 << 23, dtype=np.uint64)
+        k = philox_np.fields(p.seed, 0, cand, 42)
+        hit = cand[np.any(k[:, 0::2] == (1 << 21) - 1, axis=1)][:8].astype(np.uint32)
+        assert len(hit) >= 4
+        for n in hit:
+            assert (1 << 21) - 1 in oracle.draw_fields(p.seed, 0, int(n), 42)[0::2]
+        g = _states(len(hit), seed=11)
+        out, st = flb.flb_collide_nodes(p, g, hit, 42)
+        assert np.all(st == 0)
+        ref = np.array([oracle.collide_node(p, g[j], int(hit[j]), 42) for j in range(len(hit))])
+        assert np.abs(out - ref).max() < 2e-6 * g.sum(1).max()
+
+
 def test_collide_nodes_invalid_velocity_status():
     p = inputs.LatticeParams(1, 1, kT=0.0, basis=inputs.LOCAL, precision="fp64")
     g = np.array([[0.1, 0.9, 0.1, 0.0, 0.1, 0.3, 0.0, 0.0, 0.3],

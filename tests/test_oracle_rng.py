@@ -90,3 +90,14 @@ def test_box_muller_pairs(oracle):
             if r2 > 1e-20:
                 ang = np.arctan2(z[2 * p + 1], z[2 * p]) % (2 * np.pi)
                 assert ang == pytest.approx(2 * np.pi * k[2 * p + 1] / 2 ** 21, abs=1e-9)
+
+
+def test_numpy_philox_helper_matches_the_oracle(oracle):
+    """tests/philox_np.py (used to search for draws with given fields) gives the
+    oracle's fields."""
+    import philox_np
+    nodes = np.concatenate([np.arange(40), np.array([2 ** 32 - 1, 123456789, 2 ** 31])])
+    for seed, rep, step in [(1, 0, 0), (0xDEADBEEFCAFEF00D, 7, 123456), (99, 3, 42)]:
+        got = philox_np.fields(seed, rep, nodes, step)
+        ref = np.array([oracle.draw_fields(seed, rep, int(n), step) for n in nodes])
+        np.testing.assert_array_equal(got, ref)
