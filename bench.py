@@ -29,17 +29,19 @@ METRIC = "MLUPS & % of HBM roofline (FP32 vs FP64); batched replica-steps/s, p50
 UNIT = "MLUPS"
 BYTES_PER_NODE = {"fp32": 72, "fp64": 144}
 # DRAM bytes (read + write) per launch of the FP32 step kernel at 4096^2,
-# f-norm basis, sampling every step: ncu dram__bytes_read.sum +
-# dram__bytes_write.sum of the full-size launch (616.7 + 559.0 MB, averaged
-# over 23 launches). Valid only for the kernel version it was taken on.
-DRAM_TRAFFIC = {("fp32", "local", 4096): 616.7e6 + 559.0e6}
+# f-norm basis, sampling every step (tensor-core sums, 12 colliding warps):
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of one 2048^2 launch of
+# the same kernel (156.3 + 101.5 MB) times the 4x nodes; a full-size capture
+# may take only the launch list. Valid only for the kernel version it was
+# taken on.
+DRAM_TRAFFIC = {("fp32", "local", 4096): 4 * (156.3e6 + 101.5e6)}
+TRAFFIC_SOURCE = "ncu dram bytes of a 2048^2 launch of the same kernel, x 4 (the nodes)"
 # FP64 operations per node-step of the FP64 step kernel (f-norm, sampling
 # every step): 2 DFMA + DADD + DMUL thread instructions counted by ncu on a
-# 2048^2 launch (1669.3 M DFMA, 487.2 M DADD, 629.1 M DMUL over 4.19 M nodes;
-# the FP64 pipe 87.5 % busy). The FP64 kernel is bound by GB300's FP64 rate,
-# not by HBM: its roofline is reported against the nominal FP64 peak (there
-# is no measured FP64 peak).
-FP64_FLOPS_PER_NODE = {"local": 1062.2}
+# 2048^2 launch (388 + 118 + 176 per node; the FP64 pipe 87 % busy). The
+# FP64 kernel is bound by GB300's FP64 rate, not by HBM: its roofline is
+# reported against the nominal FP64 peak (there is no measured FP64 peak).
+FP64_FLOPS_PER_NODE = {"local": 1070.0}
 FP64_NOMINAL_TFLOPS = 1.25
 
 
@@ -245,8 +247,9 @@ def bench_structure(args, p, stream, peak, peak_kind):
     rcorrelator) on the bench lattice: steps with S_k sampled every step minus
     steps without, per step. Algorithmic bytes of the power-of-two path per
     node (FP32 transform): populations read (36) + half-spectrum write (12) in
-    the row kernel, half-spectrum read (12) + FP64 sums read and written (32)
-    in the column kernel."""
+    the row kernel; half-spectrum read (12) + the FP32 partial sums read and
+    written (16) in the column kernel; the flush of the partials into the FP64
+    sums every 16 samples (2.5 amortised): 78.5 B."""
     import torch
 
     from paper_1204_6734_gb300 import flb
@@ -277,7 +280,7 @@ def bench_structure(args, p, stream, peak, peak_kind):
     out = {"ms_per_sample": per, "ms_per_step": base, "ms_per_step_sampled": with_sk,
            "samples": ns, "path": "power-of-two (2 launches)" if pow2 else "general"}
     if pow2 and p.precision == "fp32":
-        b = 92 * nodes
+        b = 78.5 * nodes
         ach = b / (per * 1e-3) / 1e9
         out["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
                            "frac": ach / peak, "peak_kind": peak_kind, "algorithmic_bytes": b,
@@ -897,7 +900,7 @@ def main():
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                 "kernel": kname, "algorithmic_bytes": algo_bytes,
-                "traffic_source": "ncu dram bytes of the full-size launch" if traffic else None}
+                "traffic_source": TRAFFIC_SOURCE if traffic else None}
     if args.precision == "fp64" and args.basis in FP64_FLOPS_PER_NODE:
         tf = FP64_FLOPS_PER_NODE[args.basis] * nodes / (step_ms * 1e-3) / 1e12
         roofline = {"bound": "alu", "achieved": tf, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",

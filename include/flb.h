@@ -169,12 +169,16 @@ int flb_raw_sums(flb_lattice h, double* S1, double* S2, int64_t* n_samples);
 int flb_conservation(flb_lattice h, double sums[3]);
 
 /* Copy the current pre-collision state f_i(x, t) to host memory
- * (9*Lx*Ly doubles, layout above). Synchronises. */
+ * (9*Lx*Ly doubles, layout above). Page-locked host memory (cudaHostAlloc,
+ * cudaHostRegister) is written by the device directly, in one pass; other
+ * host memory through a device staging buffer of the same size (FLB_ERR_OOM
+ * if it cannot be allocated). Synchronises. */
 int flb_get_populations(flb_lattice h, double* host_out);
 
 /* Replace the current pre-collision state f_i(x, t) by host data (9*Lx*Ly
- * doubles, layout above; converted to the handle's precision). Clears a
- * recorded device error. Synchronises. */
+ * doubles, layout above; converted to the handle's precision). Page-locked
+ * host memory is read by the device directly; other memory through a device
+ * staging buffer. Clears a recorded device error. Synchronises. */
 int flb_set_populations(flb_lattice h, const double* host_in);
 
 /* Difference of the current pre-collision states of two lattices of the same

@@ -940,11 +940,24 @@ int flb_state_difference(flb_lattice a, flb_lattice b, double out[3]) {
     return FLB_OK;
 }
 
+// The device address of page-locked host memory, or null for other memory:
+// the state I/O kernels then read or write the caller's host array themselves
+// (one pass over the host link, no device staging buffer).
+static double* pinned_view(const void* host) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? static_cast<double*>(a.devicePointer) : nullptr;
+}
+
 int flb_get_populations(flb_lattice h, double* host_out) {
     if (!h || !host_out) return FLB_ERR_ARG;
     const size_t n = (size_t)9 * h->p.Lx * h->p.Ly;
-    double* tmp = nullptr;
-    if (cudaMalloc(&tmp, n * sizeof(double)) != cudaSuccess) {
+    double* direct = pinned_view(host_out);
+    double* tmp = direct;
+    if (!direct && cudaMalloc(&tmp, n * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
         return FLB_ERR_OOM;
     }
@@ -959,10 +972,10 @@ int flb_get_populations(flb_lattice h, double* host_out) {
         gather_dev_kernel<<<grid, 256, 0, h->stream>>>((const __half*)h->buf[h->cur], h->geo,
                                                        dev_codec(h), tmp);
     cudaError_t ce = cudaGetLastError();
-    if (ce == cudaSuccess)
+    if (ce == cudaSuccess && !direct)
         ce = cudaMemcpyAsync(host_out, tmp, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
-    cudaFree(tmp);
+    if (!direct) cudaFree(tmp);
     if (ce != cudaSuccess) return FLB_ERR_CUDA;
     return check_device_error(h);
 }
@@ -970,13 +983,15 @@ int flb_get_populations(flb_lattice h, double* host_out) {
 int flb_set_populations(flb_lattice h, const double* host_in) {
     if (!h || !host_in) return FLB_ERR_ARG;
     const size_t n = (size_t)9 * h->p.Lx * h->p.Ly;
-    double* tmp = nullptr;
-    if (cudaMalloc(&tmp, n * sizeof(double)) != cudaSuccess) {
+    double* direct = pinned_view(host_in);
+    double* tmp = direct;
+    if (!direct && cudaMalloc(&tmp, n * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
         return FLB_ERR_OOM;
     }
-    cudaError_t ce = cudaMemcpyAsync(tmp, host_in, n * sizeof(double), cudaMemcpyHostToDevice,
-                                     h->stream);
+    cudaError_t ce = direct ? cudaSuccess
+                            : cudaMemcpyAsync(tmp, host_in, n * sizeof(double),
+                                              cudaMemcpyHostToDevice, h->stream);
     const int grid = grid_for((long long)h->p.Lx * h->p.Ly);
     if (ce == cudaSuccess) {
         if (h->p.precision == FLB_FP64)
@@ -992,7 +1007,7 @@ int flb_set_populations(flb_lattice h, const double* host_in) {
     }
     if (ce == cudaSuccess) ce = cudaMemsetAsync(h->err, 0, sizeof(DevError), h->stream);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
-    cudaFree(tmp);
+    if (!direct) cudaFree(tmp);
     h->sticky = 0;
     return cuda_rc(ce);
 }

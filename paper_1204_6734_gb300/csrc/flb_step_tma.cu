@@ -473,6 +473,7 @@ const void* kernel_for(int nw, int basis, int mode) {
     switch (nw) {
         case 8: return kernel_ptr<8>(basis, mode);
         case 12: return kernel_ptr<12>(basis, mode);
+        case 14: return kernel_ptr<14>(basis, mode);
         case 16: return kernel_ptr<16>(basis, mode);
         default: return nullptr;
     }
@@ -489,6 +490,7 @@ size_t smem_for(int nw) {
     switch (nw) {
         case 8: return TileShape<8>::smem_bytes() + gram_smem_bytes<8>();
         case 12: return TileShape<12>::smem_bytes() + gram_smem_bytes<12>();
+        case 14: return TileShape<14>::smem_bytes() + gram_smem_bytes<14>();
         case 16: return TileShape<16>::smem_bytes() + gram_smem_bytes<16>();
         default: return 0;
     }

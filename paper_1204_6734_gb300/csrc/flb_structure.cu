@@ -299,14 +299,21 @@ __global__ void __launch_bounds__(kThreads, 2) rows_pair_kernel(const T* __restr
     }
 }
 
+// The sums a column kernel adds to: FP64 (A = double: the products formed in
+// FP64, for FP64 transforms), or FP32 partials of at most kPartialSamples
+// samples (A = float: the products of the FP32 transform formed in FP32) that
+// flush_partials_kernel adds to the FP64 sums; GB300's FP64 rate makes the
+// FP64 products the cost of the column kernel otherwise.
+constexpr int kPartialSamples = 16;
+
 // One CTA per block of C = 2^lc columns of the half spectrum H[f][m][y]: the
 // y-transform of each, then acc[q][m_x][m_y] += |drho|^2 (q = 0), |dj_x|^2
 // (1), Re and Im of dj_x conj(dj_y) (2, 3); acc[q] is Hx x Ly, m_y fastest.
-template <class R>
+template <class R, class A>
 __global__ void __launch_bounds__(kThreads, 2) cols_acc_kernel(const Cx<R>* __restrict__ H, int lgLy,
                                                             int Hx, int lc,
                                                             const Cx<R>* __restrict__ tw,
-                                                            double* __restrict__ acc) {
+                                                            A* __restrict__ acc) {
     extern __shared__ __align__(16) unsigned char raw[];
     Cx<R>* s = reinterpret_cast<Cx<R>*>(raw);
     const int Ly = 1 << lgLy, C = 1 << lc;
@@ -339,7 +346,7 @@ __global__ void __launch_bounds__(kThreads, 2) cols_acc_kernel(const Cx<R>* __re
     // is written back
     constexpr int kAcc = 2;
     for (int j0 = threadIdx.x; j0 < n; j0 += kAcc * blockDim.x) {
-        double old[kAcc][4];
+        A old[kAcc][4];
 #pragma unroll
         for (int u = 0; u < kAcc; ++u) {
             const int j = j0 + u * blockDim.x;
@@ -347,7 +354,7 @@ __global__ void __launch_bounds__(kThreads, 2) cols_acc_kernel(const Cx<R>* __re
             const size_t k = (size_t)col * Ly + (j & (Ly - 1));
             const bool ok = j < n && col < Hx;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) old[u][q] = ok ? acc[q * Q + k] : 0.0;
+            for (int q = 0; q < 4; ++q) old[u][q] = ok ? acc[q * Q + k] : A(0);
         }
 #pragma unroll
         for (int u = 0; u < kAcc; ++u) {
@@ -359,12 +366,21 @@ __global__ void __launch_bounds__(kThreads, 2) cols_acc_kernel(const Cx<R>* __re
             const Cx<R> b = s[(C + cc) * seq + spos<kEfast>(m)];
             const Cx<R> d = s[(2 * C + cc) * seq + spos<kEfast>(m)];
             const size_t k = (size_t)col * Ly + m;
-            const double ar = a.re, ai = a.im, br = b.re, bi = b.im, dr = d.re, di = d.im;
+            const A ar = a.re, ai = a.im, br = b.re, bi = b.im, dr = d.re, di = d.im;
             acc[k] = old[u][0] + (ar * ar + ai * ai);
             acc[Q + k] = old[u][1] + (br * br + bi * bi);
             acc[2 * Q + k] = old[u][2] + (br * dr + bi * di);
             acc[3 * Q + k] = old[u][3] + (bi * dr - br * di);
         }
+    }
+}
+
+// acc[k] += part[k] in FP64, part[k] = 0.
+__global__ void flush_partials_kernel(float* __restrict__ part, double* __restrict__ acc, size_t n) {
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (size_t)gridDim.x * blockDim.x) {
+        acc[k] += (double)part[k];
+        part[k] = 0.f;
     }
 }
 
@@ -478,6 +494,8 @@ struct StructSampler {
     void* fields = nullptr;           // general: 3 Lx Ly complex; fast: 3 Ly Hx complex
     double* acc = nullptr;            // general: 4 x [Ly][Lx]; fast: 4 x [Hx][Ly]
     size_t acc_count = 0;             // doubles in acc
+    float* part = nullptr;            // fast FP32 transforms: FP32 partials of acc
+    int pending = 0;                  // samples held in part
     void* twx = nullptr;              // twiddles along x and y
     void* twy = nullptr;
     int64_t nsamp = 0;
@@ -498,6 +516,14 @@ cudaError_t upload_twiddles(int L, void** out) {
     return ce;
 }
 
+cudaError_t flush_partials(StructSampler* s, cudaStream_t st) {
+    s->pending = 0;
+    if (!s->part) return cudaSuccess;
+    const int grid = (int)std::min<size_t>(4096, (s->acc_count + 255) / 256);
+    flush_partials_kernel<<<grid, 256, 0, st>>>(s->part, s->acc, s->acc_count);
+    return cudaGetLastError();
+}
+
 template <class T, class R>
 cudaError_t sample_fast(StructSampler* s, const T* buf, const Geometry& geo, const DevCodec& codec,
                         const Ref9<R>& c, cudaStream_t st) {
@@ -509,13 +535,24 @@ cudaError_t sample_fast(StructSampler* s, const T* buf, const Geometry& geo, con
         buf, geo, codec, c, log2i(s->Lx), (const Cx<R>*)s->twx, H, s->Hx);
     ce = cudaGetLastError();
     if (ce != cudaSuccess) return ce;
-    ce = cudaFuncSetAttribute(cols_acc_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)s->smem_cols);
-    if (ce != cudaSuccess) return ce;
     const int C = 1 << s->lc;
-    cols_acc_kernel<R><<<(s->Hx + C - 1) / C, kThreads, s->smem_cols, st>>>(
-        H, log2i(s->Ly), s->Hx, s->lc, (const Cx<R>*)s->twy, s->acc);
-    return cudaGetLastError();
+    if constexpr (sizeof(R) == 4) {
+        ce = cudaFuncSetAttribute(cols_acc_kernel<R, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)s->smem_cols);
+        if (ce != cudaSuccess) return ce;
+        cols_acc_kernel<R, float><<<(s->Hx + C - 1) / C, kThreads, s->smem_cols, st>>>(
+            H, log2i(s->Ly), s->Hx, s->lc, (const Cx<R>*)s->twy, s->part);
+        ce = cudaGetLastError();
+        if (ce == cudaSuccess && ++s->pending == kPartialSamples) ce = flush_partials(s, st);
+        return ce;
+    } else {
+        ce = cudaFuncSetAttribute(cols_acc_kernel<R, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)s->smem_cols);
+        if (ce != cudaSuccess) return ce;
+        cols_acc_kernel<R, double><<<(s->Hx + C - 1) / C, kThreads, s->smem_cols, st>>>(
+            H, log2i(s->Ly), s->Hx, s->lc, (const Cx<R>*)s->twy, s->acc);
+        return cudaGetLastError();
+    }
 }
 
 template <class R>
@@ -619,6 +656,10 @@ int structure_create(StructSampler** out, int Lx, int Ly, int rbytes) {
     cudaError_t ce = cudaMalloc(&s->fields, nfield * cb);
     if (ce == cudaSuccess) ce = cudaMalloc(&s->acc, s->acc_count * sizeof(double));
     if (ce == cudaSuccess) ce = cudaMemset(s->acc, 0, s->acc_count * sizeof(double));
+    if (ce == cudaSuccess && s->fast && rbytes == 4) {
+        ce = cudaMalloc(&s->part, s->acc_count * sizeof(float));
+        if (ce == cudaSuccess) ce = cudaMemset(s->part, 0, s->acc_count * sizeof(float));
+    }
     if (ce == cudaSuccess)
         ce = rbytes == 8 ? upload_twiddles<double>(Lx, &s->twx) : upload_twiddles<float>(Lx, &s->twx);
     if (ce == cudaSuccess)
@@ -636,6 +677,7 @@ void structure_destroy(StructSampler* s) {
     if (!s) return;
     cudaFree(s->fields);
     cudaFree(s->acc);
+    cudaFree(s->part);
     cudaFree(s->twx);
     cudaFree(s->twy);
     delete s;
@@ -643,7 +685,10 @@ void structure_destroy(StructSampler* s) {
 
 cudaError_t structure_reset(StructSampler* s, cudaStream_t st) {
     s->nsamp = 0;
-    return cudaMemsetAsync(s->acc, 0, s->acc_count * sizeof(double), st);
+    s->pending = 0;
+    cudaError_t ce = cudaMemsetAsync(s->acc, 0, s->acc_count * sizeof(double), st);
+    if (ce == cudaSuccess && s->part) ce = cudaMemsetAsync(s->part, 0, s->acc_count * sizeof(float), st);
+    return ce;
 }
 
 cudaError_t structure_sample(StructSampler* s, const void* buf, int precision, const Geometry& geo,
@@ -663,6 +708,10 @@ cudaError_t structure_sample(StructSampler* s, const void* buf, int precision, c
 
 int structure_read(StructSampler* s, double* const out[4], double scale, cudaStream_t st) {
     const size_t N = (size_t)s->Lx * s->Ly;
+    if (s->pending > 0 && flush_partials(s, st) != cudaSuccess) {
+        cudaGetLastError();
+        return FLB_ERR_CUDA;
+    }
     if (!s->fast) {
         cudaError_t ce = cudaSuccess;
         for (int q = 0; q < 4 && ce == cudaSuccess; ++q)
