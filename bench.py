@@ -43,6 +43,13 @@ TRAFFIC_SOURCE = "ncu dram bytes of a 2048^2 launch of the same kernel, x 4 (the
 # reported against the nominal FP64 peak (there is no measured FP64 peak).
 FP64_FLOPS_PER_NODE = {"local": 1070.0}
 FP64_NOMINAL_TFLOPS = 1.25
+# Warp instructions per node-step of the FP32 step kernel with sampling every
+# step (tensor-core sums, 12 colliding warps), from ncu smsp__inst_executed.sum
+# of a 2048^2 launch (53.4 M and 35.3 M over 4.19 M nodes): with the issue rate
+# of the GPU (4 schedulers per SM, one warp instruction per cycle each) they
+# give the issue ceiling the f-norm step is bound by.
+INSTR_PER_NODE = {("fp32", "local"): 12.73, ("fp32", "standard"): 8.42}
+SCHEDULERS_PER_SM = 4
 
 
 def parse():
@@ -901,6 +908,15 @@ def main():
                 "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                 "kernel": kname, "algorithmic_bytes": algo_bytes,
                 "traffic_source": TRAFFIC_SOURCE if traffic else None}
+    ipn = INSTR_PER_NODE.get((args.precision, args.basis))
+    if ipn and args.sample_every == 1 and not args.pipeline_warps and not args.pipeline_sampling:
+        props = torch.cuda.get_device_properties(dev)
+        mhz = clk.summary().get("sm_mhz") or 2070.0
+        peak_inst = props.multi_processor_count * SCHEDULERS_PER_SM * mhz * 1e6
+        got = ipn * nodes / (step_ms * 1e-3)
+        roofline["issue"] = {"instructions_per_node": ipn, "achieved": got / 1e9, "peak": peak_inst / 1e9,
+                             "unit": "G warp-instructions/s", "frac": got / peak_inst,
+                             "source": "ncu smsp__inst_executed.sum of a 2048^2 launch"}
     if args.precision == "fp64" and args.basis in FP64_FLOPS_PER_NODE:
         tf = FP64_FLOPS_PER_NODE[args.basis] * nodes / (step_ms * 1e-3) / 1e12
         roofline = {"bound": "alu", "achieved": tf, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
