@@ -375,8 +375,9 @@ cudaError_t launch_step_p(flb_lattice h, bool sample) {
 }
 
 // Pipelined FP32 kernel: also reduces the sampled sums into h->acc itself.
-cudaError_t launch_step_tma(flb_lattice h, bool sample) {
+cudaError_t launch_step_tma(flb_lattice h, bool sample, float* fields) {
     TmaArgs a;
+    a.fields = fields;
     a.dst = (float*)h->buf[h->cur ^ 1];
     a.geo = h->geo;
     a.step = (uint32_t)h->t;
@@ -428,10 +429,12 @@ cudaError_t launch_step_fp16(flb_lattice h, bool sample) {
     return fp16_step(h->tma, h->cur, a, collide_const<float>(&h->p), h->p.basis, sample, h->stream);
 }
 
-cudaError_t launch_step(flb_lattice h, bool sample) {
+// fields: where the pipelined FP32 kernel writes the structure-factor fields
+// of this step's pre-collision state (nullptr: not sampled by the step).
+cudaError_t launch_step(flb_lattice h, bool sample, float* fields = nullptr) {
     if (h->p.precision == FLB_FP64) return launch_step_p<double>(h, sample);
     if (h->p.precision == FLB_FP16_DEV) return launch_step_fp16(h, sample);
-    if (uses_tma(h)) return launch_step_tma(h, sample);
+    if (uses_tma(h)) return launch_step_tma(h, sample, fields);
     return launch_step_p<float>(h, sample);
 }
 
@@ -679,7 +682,7 @@ int flb_set_structure_sampling(flb_lattice h, int64_t warmup, int64_t every) {
     if (h->sticky) return h->sticky;
     if (every > 0 && !h->sk) {
         const int rc = structure_create(&h->sk, h->p.Lx, h->p.Ly,
-                                        h->p.precision == FLB_FP64 ? 8 : 4);
+                                        h->p.precision == FLB_FP64 ? 8 : 4, h->p.precision == FLB_FP32);
         if (rc) return rc;
     }
     h->sk_warmup = warmup;
@@ -706,10 +709,17 @@ int flb_step(flb_lattice h, int64_t n) {
         const bool sample =
             h->every > 0 && h->t >= h->warmup && ((h->t - h->warmup) % h->every) == 0;
         cudaError_t ce = cudaSuccess;
-        if (h->sk_every > 0 && h->t >= h->sk_warmup && ((h->t - h->sk_warmup) % h->sk_every) == 0)
+        // a structure-factor sample of the state this step starts from: the
+        // pipelined FP32 kernel forms its fields while it collides, else the
+        // sampler reads the populations before the step
+        const bool sk_due =
+            h->sk_every > 0 && h->t >= h->sk_warmup && ((h->t - h->sk_warmup) % h->sk_every) == 0;
+        float* fields = sk_due && uses_tma(h) ? structure_fields(h->sk) : nullptr;
+        if (sk_due && !fields)
             ce = structure_sample(h->sk, h->buf[h->cur], h->p.precision, h->geo, dev_codec(h), h->ref,
                                   h->stream);
-        if (ce == cudaSuccess) ce = launch_step(h, sample);
+        if (ce == cudaSuccess) ce = launch_step(h, sample, fields);
+        if (ce == cudaSuccess && fields) ce = structure_sample_fields(h->sk, h->stream);
         if (ce == cudaSuccess && sample && !reduces_in_kernel(h)) {
             accumulate_partials_kernel<<<kSums, 32, 0, h->stream>>>(h->partials, h->nblocks,
                                                                      h->acc);

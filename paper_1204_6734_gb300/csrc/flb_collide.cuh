@@ -68,7 +68,12 @@ __device__ __forceinline__ void node_normals(const NoiseKey& key, uint32_t nodeA
 // node (scalar lanes) or a node pair (packed lanes) take the same operations
 // per lane, so both give bit-identical increments. FP64 uses unit normals
 // (operator()).
+// The offsets ride in fused multiply-adds on the exact conversions of the
+// 21-bit fields k: fma(k, 2^-21, 2^-21) is (k + 1) 2^-21 exactly, and
+// fma(k, c, -2^20 c) is (k - 2^20) c rounded once, as the product of the
+// exact difference would be (2^20 c is exact).
 constexpr float kLn2x2 = 1.3862943611198906f;
+constexpr float kAngle = (float)(kTwoPi * 0x1p-21);   // 2 pi 2^-21, the angle of one step of k
 
 struct NodeNoise {
     const NoiseKey& key;
@@ -83,11 +88,11 @@ struct NodeNoise {
         const float nr = rho * -kLn2x2;
 #pragma unroll
         for (int p = 0; p < 3; ++p) {
-            const float u1 = (float)(k[2 * p] + 1u) * 0x1p-21f;
-            const float r = sqr(__log2f(u1) * nr);
-            const float t = (float)((int)k[2 * p + 1] - (1 << 20)) * (float)(kTwoPi * 0x1p-21);
+            const float u1 = mad((float)k[2 * p], 0x1p-21f, 0x1p-21f);
+            const float r = sqr(lg2_ftz(u1) * nr);
+            const float t = mad((float)k[2 * p + 1], kAngle, -0x1p20f * kAngle);
             float s, c;
-            __sincosf(t, &s, &c);
+            sincos_ftz(t, &s, &c);
             // cos(t + pi) = -cos t, sin(t + pi) = -sin t
             n[2 * p] = (r * -amp[2 * p]) * c;
             n[2 * p + 1] = (r * -amp[2 * p + 1]) * s;
@@ -105,13 +110,13 @@ struct PairNoise {
         const f2 nr = rho * f2(-kLn2x2);
 #pragma unroll
         for (int p = 0; p < 3; ++p) {
-            const f2 u1 = f2((float)(ka[2 * p] + 1u), (float)(kb[2 * p] + 1u)) * f2(0x1p-21f);
-            const f2 r = sqr(f2(__log2f(u1.v.x), __log2f(u1.v.y)) * nr);
-            const f2 t = f2((float)((int)ka[2 * p + 1] - (1 << 20)),
-                            (float)((int)kb[2 * p + 1] - (1 << 20))) * f2((float)(kTwoPi * 0x1p-21));
+            const f2 u1 = mad(f2((float)ka[2 * p], (float)kb[2 * p]), f2(0x1p-21f), f2(0x1p-21f));
+            const f2 r = sqr(f2(lg2_ftz(u1.v.x), lg2_ftz(u1.v.y)) * nr);
+            const f2 t = mad(f2((float)ka[2 * p + 1], (float)kb[2 * p + 1]), f2(kAngle),
+                             f2(-0x1p20f * kAngle));
             float sa, ca, sb, cb;
-            __sincosf(t.v.x, &sa, &ca);
-            __sincosf(t.v.y, &sb, &cb);
+            sincos_ftz(t.v.x, &sa, &ca);
+            sincos_ftz(t.v.y, &sb, &cb);
             n[2 * p] = (r * f2(-amp[2 * p])) * f2(ca, cb);
             n[2 * p + 1] = (r * f2(-amp[2 * p + 1])) * f2(sa, sb);
         }

@@ -97,12 +97,12 @@ __device__ __forceinline__ void box_muller(const uint32_t k[6], float n[6]) {
 #pragma unroll
     for (int p = 0; p < 3; ++p) {
         const float u1 = (float)(k[2 * p] + 1u) * 0x1p-21f;
-        const float r2 = -1.3862943611198906f * __log2f(u1);   // -2 ln u1
+        const float r2 = -1.3862943611198906f * lg2_ftz(u1);   // -2 ln u1
         float r;
         asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(r2));
         const float t = (float)((int)k[2 * p + 1] - (1 << 20)) * (float)(kTwoPi * 0x1p-21);
         float s, c;
-        __sincosf(t, &s, &c);
+        sincos_ftz(t, &s, &c);
         n[2 * p] = -r * c;
         n[2 * p + 1] = -r * s;
     }

@@ -24,6 +24,9 @@ struct TmaArgs {
     float sinv;             // 1 / s
     float snref[9];         // -ref / s
     double s;               // s (the sums are rescaled in FP64)
+    // structure-factor sampling of this step's pre-collision state: the fields
+    // drho, dj_x, dj_y of every node into fields[f Lx Ly + y Lx + x] (nullptr: none)
+    float* fields;
 };
 
 constexpr int kPlanTensorSampling = 3;   // TmaPlan::sample_mode of the tensor-core sums

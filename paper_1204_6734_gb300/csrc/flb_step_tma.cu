@@ -64,26 +64,21 @@ __device__ __forceinline__ void issue_tile(float* smem, const CUtensorMap* map, 
 }
 
 // Producer state of an elected thread that refills each stage once every warp
-// has released it. Stage s holds tiles s, s + STAGES, ... of this CTA. WALK:
-// tile coordinates by TileWalk rather than a division per tile (which of the
-// two schedules faster differs between the two bases' kernels, by measurement).
-template <int NW, bool WALK>
+// has released it. Stage s holds tiles s, s + STAGES, ... of this CTA; the
+// tile coordinates advance by TileWalk, without a division per tile.
+template <int NW>
 struct Producer {
     int issued = 0;
     bool ok = true;
-    TileWalk walk;   // the next tile to issue (WALK)
+    TileWalk walk;   // the next tile to issue
 
     __device__ __forceinline__ explicit Producer(const TmaArgs& a)
         : walk(blockIdx.x, gridDim.x, a.tiles_x) {}
 
     __device__ __forceinline__ void issue(float* smem, const CUtensorMap* map, const TmaArgs& a,
-                                          int t, int s, uint64_t* full) {
-        if (WALK) {
-            issue_tile<NW>(smem, map, a, walk.tx, walk.ty, s, full);
-            walk.next();
-        } else {
-            issue_tile<NW>(smem, map, a, t % a.tiles_x, t / a.tiles_x, s, full);
-        }
+                                          int s, uint64_t* full) {
+        issue_tile<NW>(smem, map, a, walk.tx, walk.ty, s, full);
+        walk.next();
     }
 
     __device__ __forceinline__ void prologue(float* smem, const CUtensorMap* map,
@@ -91,7 +86,7 @@ struct Producer {
         prefetch_tensormap(map);
         for (int t = blockIdx.x; t < a.ntiles && issued < TileShape<NW>::STAGES;
              t += gridDim.x, ++issued)
-            issue(smem, map, a, t, issued, full);
+            issue(smem, map, a, issued, full);
     }
     // after this CTA's k-th tile (stage s, use n) was released by the caller
     __device__ __forceinline__ void refill(float* smem, const CUtensorMap* map, const TmaArgs& a,
@@ -104,7 +99,7 @@ struct Producer {
             ok = false;
             return;
         }
-        issue(smem, map, a, tn, s, full);
+        issue(smem, map, a, s, full);
         ++issued;
     }
     // no copy may be in flight when the CTA exits: wait for tiles issued but not
@@ -172,7 +167,6 @@ step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
     constexpr int TH = TS::TH;
     constexpr int kStages = TS::STAGES;
     constexpr int NX = WarpCount<MODE>::template extra<NW>();
-    constexpr bool kWalk = BASIS == 0;   // see Producer
     extern __shared__ __align__(128) float smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * TS::STAGE);
     uint64_t* empty = full + kStages;
@@ -201,11 +195,16 @@ step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
     if ((MODE == kNoSampling || kTensor) && !kEmbed && warp == NW) {
         // ---------------- producer warp
         if (lane_id == 0) {
-            Producer<NW, kWalk> prod(a);
+            Producer<NW> prod(a);
             prod.prologue(smem, &map, a, full);
-            int k = 0;
-            for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++k)
-                prod.refill(smem, &map, a, full, empty, k % kStages, k / kStages);
+            int s = 0, n = 0;
+            for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+                prod.refill(smem, &map, a, full, empty, s, n);
+                if (++s == kStages) {
+                    s = 0;
+                    ++n;
+                }
+            }
             prod.drain(a, full, prod.issued);
         }
         return;
@@ -215,24 +214,23 @@ step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
         // ---------------- sampler warps
         const int sw = warp - NW;
         const bool producer = sw == 0 && lane_id == 0;
-        Producer<NW, kWalk> prod(a);
+        Producer<NW> prod(a);
         if (producer) prod.prologue(smem, &map, a, full);
         f2 s1[9], s2[45];
 #pragma unroll
         for (int q = 0; q < 9; ++q) s1[q] = f2(0.f);
 #pragma unroll
         for (int q = 0; q < 45; ++q) s2[q] = f2(0.f);
-        int k = 0;
+        int k = 0, s = 0, n = 0;
         TileWalk w(blockIdx.x, gridDim.x, a.tiles_x);
         for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++k, w.next()) {
-            const int s = k % kStages, n = k / kStages;
             if (!mbar_wait_sleep(&full[s], n & 1)) {
                 record_error(a.err, kStatusTimeout, -1, a.step);
                 break;
             }
-            const int x0 = (kWalk ? w.tx : t % a.tiles_x) * kTW;
+            const int x0 = w.tx * kTW;
             for (int row = sw; row < TH; row += NX) {
-                const int y = (kWalk ? w.ty : t / a.tiles_x) * TH + row;
+                const int y = w.ty * TH + row;
                 const float* st = smem + s * TS::STAGE + row * kBoxW + 4 + lane_id;
                 f2 d[2][9];
 #pragma unroll
@@ -242,10 +240,7 @@ step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
                         const float* q = st + i * TS::SPLANE - cvx(i) + 64 * p;
                         d[p][i] = f2(q[0], q[32]);
                     }
-                if (row + NX >= TH) {   // last row: release before the arithmetic
-                    __syncwarp();
-                    if (lane_id == 0) mbar_arrive(&empty[s]);
-                }
+                if (row + NX >= TH) warp_arrive(&empty[s], lane_id);   // last row: release first
 #pragma unroll
                 for (int p = 0; p < 2; ++p) {
                     const int xA = x0 + lane_id + 64 * p;
@@ -265,11 +260,12 @@ step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
                     }
                 }
             }
-            if (sw >= TH) {   // a sampler without a row in this tile
-                __syncwarp();
-                if (lane_id == 0) mbar_arrive(&empty[s]);
-            }
+            if (sw >= TH) warp_arrive(&empty[s], lane_id);   // a sampler without a row here
             if (producer) prod.refill(smem, &map, a, full, empty, s, n);
+            if (++s == kStages) {
+                s = 0;
+                ++n;
+            }
         }
         if (producer) prod.drain(a, full, k);
         float v[kSums];
@@ -287,7 +283,7 @@ step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
     const int ty = c >> 6, r = c & 63;
     constexpr bool kFused = MODE == kFusedSampling;
     const bool producer = (kFused || kEmbed) && c == 0;
-    Producer<NW, kWalk> prod(a);
+    Producer<NW> prod(a);
     if (producer) prod.prologue(smem, &map, a, full);
     float v[kFused ? kSums : 1];
     if (kFused) {
@@ -301,10 +297,9 @@ step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
     }
     int gtiles = 0;
     const GramLane gblk(smem_u32(gram + warp * kGramWarpHalves));
-    int k = 0;
+    int k = 0, s = 0, n = 0;   // tile count, its stage and the stage's use
     TileWalk w(blockIdx.x, gridDim.x, a.tiles_x);
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++k, w.next()) {
-        const int s = k % kStages, n = k / kStages;
         if (!mbar_wait(&full[s], n & 1)) {
             record_error(a.err, kStatusTimeout, -1, a.step);
             break;
@@ -320,16 +315,42 @@ step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
         f2 g[9];
         load(g);
 
-        const int x0 = (kWalk ? w.tx : t % a.tiles_x) * kTW;
-        const int y = (kWalk ? w.ty : t / a.tiles_x) * TH + ty;
+        // tile origin (the same for every thread, so the tests on it below
+        // are uniform branches) and this thread's nodes
+        const int x0 = w.tx * kTW, y0 = w.ty * TH;
+        const int y = y0 + ty;
         const int xA = x0 + r, xB = xA + 64;
         const bool inA = xA < Lx && y < Ly, inB = xB < Lx && y < Ly;
+        const bool whole = x0 + kTW <= Lx && y0 + TH <= Ly;   // every node of the tile
+        if (a.fields) {
+            // structure-factor sample of this state: drho, dj_x, dj_y of both
+            // nodes from the deviations f_i - ref_i, summed in the order the
+            // separate field kernel uses (the same FP32 values)
+            f2 d[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) d[i] = g[i] - f2(a.ref[i]);
+            const f2 fr = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
+            const f2 fx = (d[1] - d[3]) + ((d[5] - d[6]) + (d[8] - d[7]));
+            const f2 fy = (d[2] - d[4]) + ((d[5] + d[6]) - (d[7] + d[8]));
+            const size_t N = (size_t)Lx * Ly;
+            float* o = a.fields + (size_t)y * Lx + xA;
+            if (whole || inA) {
+                o[0] = fr.v.x;
+                o[N] = fx.v.x;
+                o[2 * N] = fy.v.x;
+            }
+            if (whole || inB) {
+                o[64] = fr.v.y;
+                o[N + 64] = fx.v.y;
+                o[2 * N + 64] = fy.v.y;
+            }
+        }
         if (kFused) {
             f2 d[9];
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 f2 e = g[i] - f2(a.ref[i]);
-                if (!(inA && inB)) e = f2(inA ? e.v.x : 0.f, inB ? e.v.y : 0.f);
+                if (!whole) e = f2(inA ? e.v.x : 0.f, inB ? e.v.y : 0.f);
                 d[i] = e;
             }
             add_sums(reinterpret_cast<float(&)[kSums]>(v), d);
@@ -340,7 +361,7 @@ step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
             f2 hs[9];
 #pragma unroll
             for (int i = 0; i < 9; ++i) hs[i] = mad(gs[i], f2(a.sinv), f2(a.snref[i]));
-            if (!(inA && inB)) {
+            if (!whole) {
 #pragma unroll
                 for (int i = 0; i < 9; ++i) hs[i] = f2(inA ? hs[i].v.x : 0.f, inB ? hs[i].v.y : 0.f);
             }
@@ -364,15 +385,13 @@ step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
             }
         }
         // the stage is held until g was read the second time
-        __syncwarp();
-        if (lane_id == 0) mbar_arrive(&empty[s]);
+        warp_arrive(&empty[s], lane_id);
         if (stt) {
             if (inA && (stt & 0xFF)) record_error(a.err, (int)(stt & 0xFF), nodeA, a.step);
             if (inB && (stt >> 8)) record_error(a.err, (int)(stt >> 8), nodeA + 64u, a.step);
         }
         // tiles away from the lattice edge store without per-node checks
-        const int x0t = xA - r, y0t = y - ty;
-        if (x0t > 0 && y0t > 0 && x0t + kTW < Lx && y0t + TH < Ly) {
+        if (x0 > 0 && y0 > 0 && x0 + kTW < Lx && y0 + TH < Ly) {
             float* pa = a.dst + at(a.geo, 0, xA, y);
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
@@ -388,6 +407,10 @@ step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
                 prod.refill(smem, &map, a, full, empty, s, n);
             else if (k > 0)
                 prod.refill(smem, &map, a, full, empty, (k - 1) % kStages, (k - 1) / kStages);
+        }
+        if (++s == kStages) {
+            s = 0;
+            ++n;
         }
     }
     if (kEmbed && producer) prod.drain(a, full, k);

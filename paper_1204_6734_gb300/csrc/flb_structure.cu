@@ -262,9 +262,33 @@ __device__ __forceinline__ void store_pair(Cx<double>* p, Cx<double> a, Cx<doubl
     reinterpret_cast<double2*>(p)[1] = make_double2(b.re, b.im);
 }
 
-// One CTA per row pair (y0, y0 + 1): H[f][m][y], m = 0..Lx/2 (Hx columns of
-// Ly values), the x-transform of field f (0: drho, 1: dj_x, 2: dj_y) of row y,
-// stored column-major so that the y-transforms read contiguous columns.
+// The x-transform of the three fields of the row pair (y0, y0 + 1), staged in
+// shared memory s as one complex sequence per field (row y0 in the real part,
+// row y0 + 1 in the imaginary part, element x at spos(x)), and the store of
+// the half spectrum: H[f][m][y], m = 0..Lx/2 (Hx columns of Ly values), the
+// x-transform of field f (0: drho, 1: dj_x, 2: dj_y) of row y, column-major so
+// that the y-transforms read contiguous columns.
+template <class R>
+__device__ __forceinline__ void rows_transform_store(Cx<R>* s, int seq, int lgLx, int Lx, int Ly,
+                                                     int y0, const Cx<R>* __restrict__ tw,
+                                                     Cx<R>* __restrict__ H, int Hx) {
+    __syncthreads();
+    fft_seqs<kEfast>(s, lgLx, 3, seq, tw);
+    // z = a + i b with a, b real: A(m) = (Z(m) + conj Z(-m)) / 2,
+    // B(m) = (Z(m) - conj Z(-m)) / (2i)
+    for (int f = 0; f < 3; ++f) {
+        const Cx<R>* z = s + f * seq;
+        Cx<R>* out = H + (size_t)f * Hx * Ly + y0;
+        for (int m = threadIdx.x; m < Hx; m += blockDim.x) {
+            const Cx<R> u = z[spos<kEfast>(m)], w = z[spos<kEfast>((Lx - m) & (Lx - 1))];
+            store_pair(out + (size_t)m * Ly, Cx<R>{R(0.5) * (u.re + w.re), R(0.5) * (u.im - w.im)},
+                       Cx<R>{R(0.5) * (u.im + w.im), R(0.5) * (w.re - u.re)});
+        }
+    }
+}
+
+// One CTA per row pair (y0, y0 + 1): the fields formed from the pulled
+// populations, then rows_transform_store.
 template <class T, class R>
 __global__ void __launch_bounds__(kThreads, 2) rows_pair_kernel(const T* __restrict__ buf, Geometry geo,
                                                              DevCodec codec, Ref9<R> c, int lgLx,
@@ -284,19 +308,46 @@ __global__ void __launch_bounds__(kThreads, 2) rows_pair_kernel(const T* __restr
         s[seq + p] = {a0, a1};
         s[2 * seq + p] = {b0, b1};
     }
-    __syncthreads();
-    fft_seqs<kEfast>(s, lgLx, 3, seq, tw);
-    // z = a + i b with a, b real: A(m) = (Z(m) + conj Z(-m)) / 2,
-    // B(m) = (Z(m) - conj Z(-m)) / (2i)
-    for (int f = 0; f < 3; ++f) {
-        const Cx<R>* z = s + f * seq;
-        Cx<R>* out = H + (size_t)f * Hx * Ly + y0;
-        for (int m = threadIdx.x; m < Hx; m += blockDim.x) {
-            const Cx<R> u = z[spos<kEfast>(m)], w = z[spos<kEfast>((Lx - m) & (Lx - 1))];
-            store_pair(out + (size_t)m * Ly, Cx<R>{R(0.5) * (u.re + w.re), R(0.5) * (u.im - w.im)},
-                       Cx<R>{R(0.5) * (u.im + w.im), R(0.5) * (w.re - u.re)});
+    rows_transform_store(s, seq, lgLx, Lx, Ly, y0, tw, H, Hx);
+}
+
+// One CTA per row pair (y0, y0 + 1) of the FP32 fields F[f][y][x] that the
+// step kernel wrote on this sampling step (bit-identical to the fields
+// node_fields forms from the same state), then rows_transform_store. Four
+// consecutive x per 16-byte load, all six loads of a step issued together.
+__global__ void __launch_bounds__(kThreads, 2) rows_fields_kernel(const float* __restrict__ F, int Lx,
+                                                               int Ly, int lgLx,
+                                                               const Cx<float>* __restrict__ tw,
+                                                               Cx<float>* __restrict__ H, int Hx) {
+    extern __shared__ __align__(16) unsigned char raw[];
+    Cx<float>* s = reinterpret_cast<Cx<float>*>(raw);
+    const int seq = padded_len<kEfast>(Lx);
+    const int y0 = 2 * blockIdx.x;
+    const size_t N = (size_t)Lx * Ly;
+    const float* r0 = F + (size_t)y0 * Lx;
+    if (Lx >= 4) {
+        for (int x = 4 * threadIdx.x; x < Lx; x += 4 * blockDim.x) {
+            float4 a[3], b[3];
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                a[f] = __ldg(reinterpret_cast<const float4*>(r0 + f * N + x));
+                b[f] = __ldg(reinterpret_cast<const float4*>(r0 + f * N + Lx + x));
+            }
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                Cx<float>* z = s + f * seq;
+                z[spos<kEfast>(x)] = {a[f].x, b[f].x};
+                z[spos<kEfast>(x + 1)] = {a[f].y, b[f].y};
+                z[spos<kEfast>(x + 2)] = {a[f].z, b[f].z};
+                z[spos<kEfast>(x + 3)] = {a[f].w, b[f].w};
+            }
         }
+    } else {
+        for (int x = threadIdx.x; x < Lx; x += blockDim.x)
+#pragma unroll
+            for (int f = 0; f < 3; ++f) s[f * seq + spos<kEfast>(x)] = {r0[f * N + x], r0[f * N + Lx + x]};
     }
+    rows_transform_store(s, seq, lgLx, Lx, Ly, y0, tw, H, Hx);
 }
 
 // The sums a column kernel adds to: FP64 (A = double: the products formed in
@@ -495,6 +546,7 @@ struct StructSampler {
     double* acc = nullptr;            // general: 4 x [Ly][Lx]; fast: 4 x [Hx][Ly]
     size_t acc_count = 0;             // doubles in acc
     float* part = nullptr;            // fast FP32 transforms: FP32 partials of acc
+    float* fin = nullptr;             // fast, fused: 3 Lx Ly FP32 fields from the step kernel
     int pending = 0;                  // samples held in part
     void* twx = nullptr;              // twiddles along x and y
     void* twy = nullptr;
@@ -524,18 +576,12 @@ cudaError_t flush_partials(StructSampler* s, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template <class T, class R>
-cudaError_t sample_fast(StructSampler* s, const T* buf, const Geometry& geo, const DevCodec& codec,
-                        const Ref9<R>& c, cudaStream_t st) {
-    Cx<R>* H = (Cx<R>*)s->fields;
-    cudaError_t ce = cudaFuncSetAttribute(rows_pair_kernel<T, R>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem_rows);
-    if (ce != cudaSuccess) return ce;
-    rows_pair_kernel<T, R><<<s->Ly / 2, kThreads, s->smem_rows, st>>>(
-        buf, geo, codec, c, log2i(s->Lx), (const Cx<R>*)s->twx, H, s->Hx);
-    ce = cudaGetLastError();
-    if (ce != cudaSuccess) return ce;
+// The column launch of the power-of-two path and the partial-sum flush.
+template <class R>
+cudaError_t cols_accumulate(StructSampler* s, cudaStream_t st) {
+    const Cx<R>* H = (const Cx<R>*)s->fields;
     const int C = 1 << s->lc;
+    cudaError_t ce;
     if constexpr (sizeof(R) == 4) {
         ce = cudaFuncSetAttribute(cols_acc_kernel<R, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)s->smem_cols);
@@ -553,6 +599,18 @@ cudaError_t sample_fast(StructSampler* s, const T* buf, const Geometry& geo, con
             H, log2i(s->Ly), s->Hx, s->lc, (const Cx<R>*)s->twy, s->acc);
         return cudaGetLastError();
     }
+}
+
+template <class T, class R>
+cudaError_t sample_fast(StructSampler* s, const T* buf, const Geometry& geo, const DevCodec& codec,
+                        const Ref9<R>& c, cudaStream_t st) {
+    cudaError_t ce = cudaFuncSetAttribute(rows_pair_kernel<T, R>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem_rows);
+    if (ce != cudaSuccess) return ce;
+    rows_pair_kernel<T, R><<<s->Ly / 2, kThreads, s->smem_rows, st>>>(
+        buf, geo, codec, c, log2i(s->Lx), (const Cx<R>*)s->twx, (Cx<R>*)s->fields, s->Hx);
+    ce = cudaGetLastError();
+    return ce == cudaSuccess ? cols_accumulate<R>(s, st) : ce;
 }
 
 template <class R>
@@ -616,7 +674,7 @@ cudaError_t sample_typed(StructSampler* s, const void* buf, const Geometry& geo,
 
 }  // namespace
 
-int structure_create(StructSampler** out, int Lx, int Ly, int rbytes) {
+int structure_create(StructSampler** out, int Lx, int Ly, int rbytes, bool fused) {
     *out = nullptr;
     if ((rbytes != 4 && rbytes != 8) || Lx < 1 || Ly < 1) return FLB_ERR_ARG;
     int dev = 0, optin = 0;
@@ -659,6 +717,7 @@ int structure_create(StructSampler** out, int Lx, int Ly, int rbytes) {
     if (ce == cudaSuccess && s->fast && rbytes == 4) {
         ce = cudaMalloc(&s->part, s->acc_count * sizeof(float));
         if (ce == cudaSuccess) ce = cudaMemset(s->part, 0, s->acc_count * sizeof(float));
+        if (ce == cudaSuccess && fused) ce = cudaMalloc(&s->fin, 3 * N * sizeof(float));
     }
     if (ce == cudaSuccess)
         ce = rbytes == 8 ? upload_twiddles<double>(Lx, &s->twx) : upload_twiddles<float>(Lx, &s->twx);
@@ -678,6 +737,7 @@ void structure_destroy(StructSampler* s) {
     cudaFree(s->fields);
     cudaFree(s->acc);
     cudaFree(s->part);
+    cudaFree(s->fin);
     cudaFree(s->twx);
     cudaFree(s->twy);
     delete s;
@@ -702,6 +762,21 @@ cudaError_t structure_sample(StructSampler* s, const void* buf, int precision, c
         ce = precision == FLB_FP64   ? sample_typed<double, float>(s, buf, geo, codec, ref, st)
              : precision == FLB_FP32 ? sample_typed<float, float>(s, buf, geo, codec, ref, st)
                                      : sample_typed<__half, float>(s, buf, geo, codec, ref, st);
+    if (ce == cudaSuccess) s->nsamp += 1;
+    return ce;
+}
+
+float* structure_fields(StructSampler* s) { return s ? s->fin : nullptr; }
+
+cudaError_t structure_sample_fields(StructSampler* s, cudaStream_t st) {
+    if (!s->fin) return cudaErrorInvalidValue;
+    cudaError_t ce = cudaFuncSetAttribute(rows_fields_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)s->smem_rows);
+    if (ce != cudaSuccess) return ce;
+    rows_fields_kernel<<<s->Ly / 2, kThreads, s->smem_rows, st>>>(
+        s->fin, s->Lx, s->Ly, log2i(s->Lx), (const Cx<float>*)s->twx, (Cx<float>*)s->fields, s->Hx);
+    ce = cudaGetLastError();
+    if (ce == cudaSuccess) ce = cols_accumulate<float>(s, st);
     if (ce == cudaSuccess) s->nsamp += 1;
     return ce;
 }

@@ -18,7 +18,9 @@ struct StructSampler;
 // FP32, 8: FP64); FLB_ERR_ARG when a row or column of complex values does not
 // fit one CTA's shared memory (sides above 20480 in FP32, 10240 in FP64);
 // FLB_ERR_OOM when an allocation fails.
-int structure_create(StructSampler** out, int Lx, int Ly, int rbytes);
+// fused: the FP32 step kernel will form the fields itself (structure_fields,
+// structure_sample_fields), which needs a 3 Lx Ly FP32 field buffer.
+int structure_create(StructSampler** out, int Lx, int Ly, int rbytes, bool fused);
 void structure_destroy(StructSampler* s);
 cudaError_t structure_reset(StructSampler* s, cudaStream_t st);
 // One sample of the pre-collision state the pull from `buf` gives:
@@ -26,6 +28,13 @@ cudaError_t structure_reset(StructSampler* s, cudaStream_t st);
 // f^0(rho0, u0), the fields being sums of f_i - ref_i.
 cudaError_t structure_sample(StructSampler* s, const void* buf, int precision, const Geometry& geo,
                              const DevCodec& codec, const double* ref, cudaStream_t st);
+// The field buffer ([f][y][x], f = drho, dj_x, dj_y, FP32) a step kernel fills
+// on a sampling step when the sampler was created fused and both sides are
+// powers of two; nullptr otherwise (structure_sample is used then).
+float* structure_fields(StructSampler* s);
+// One sample from the fields a step kernel has written to structure_fields(s)
+// (the same sums as structure_sample of that step's pre-collision state).
+cudaError_t structure_sample_fields(StructSampler* s, cudaStream_t st);
 // The four FP64 sums S_rho, S_jx, Re R, Im R, each Ly x Lx ([m_y][m_x]),
 // times `scale`, into the host arrays out[0..3] (a NULL entry is skipped);
 // synchronises the stream. FLB_OK, FLB_ERR_OOM or FLB_ERR_CUDA.

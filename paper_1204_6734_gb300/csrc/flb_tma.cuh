@@ -36,6 +36,18 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// A warp releases a stage: every lane has finished its reads (syncwarp), then
+// lane 0 arrives, predicated rather than branched around.
+__device__ __forceinline__ void warp_arrive(uint64_t* bar, int lane_id) {
+    __syncwarp();
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.eq.s32 p, %1, 0;\n\t"
+        "@p mbarrier.arrive.shared::cta.b64 _, [%0];\n\t}" ::"r"(smem_u32(bar)),
+        "r"(lane_id)
+        : "memory");
+}
+
 // try_wait with a suspend-time hint: a thread whose phase has not completed is
 // parked by the hardware (up to the hint, in ns) instead of spinning, so a
 // waiting warp takes no issue slots from the warps that compute.

@@ -40,6 +40,19 @@ __device__ __forceinline__ float sqr(float x) {
     return r;
 }
 
+// SFU base-2 logarithm, sine and cosine with denormals flushed: the noise
+// draws never pass a denormal (u1 >= 2^-21, |angle| = 0 or >= 2 pi 2^-21), so
+// these give the values of the non-flushing forms without their fix-ups.
+__device__ __forceinline__ float lg2_ftz(float x) {
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ void sincos_ftz(float x, float* s, float* c) {
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(*s) : "f"(x));
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(*c) : "f"(x));
+}
+
 // Two FP32 lanes (node A in .x, node B in .y).
 struct f2 {
     float2 v;
