@@ -252,11 +252,12 @@ def oracle_mlups(p, max_seconds=15.0, side=1024):
 def bench_structure(args, p, stream, peak, peak_kind):
     """Cost of one structure-factor sample (Eqs. sfactorr, sfactoru,
     rcorrelator) on the bench lattice: steps with S_k sampled every step minus
-    steps without, per step. Algorithmic bytes of the power-of-two path per
-    node (FP32 transform): populations read (36) + half-spectrum write (12) in
-    the row kernel; half-spectrum read (12) + the FP32 partial sums read and
-    written (16) in the column kernel; the flush of the partials into the FP64
-    sums every 16 samples (2.5 amortised): 78.5 B."""
+    steps without, per step. Algorithmic bytes of the power-of-two FP32 path
+    per node: the step kernel writes the sampled state's three fields (12); the
+    row kernel reads them (12) and writes the half spectrum (12); the column
+    kernel reads it (12) and reads and writes the FP32 partial sums (16); the
+    flush of the partials into the FP64 sums every 16 samples (2.5 amortised):
+    66.5 B."""
     import torch
 
     from paper_1204_6734_gb300 import flb
@@ -287,11 +288,13 @@ def bench_structure(args, p, stream, peak, peak_kind):
     out = {"ms_per_sample": per, "ms_per_step": base, "ms_per_step_sampled": with_sk,
            "samples": ns, "path": "power-of-two (2 launches)" if pow2 else "general"}
     if pow2 and p.precision == "fp32":
-        b = 78.5 * nodes
+        b = 66.5 * nodes
         ach = b / (per * 1e-3) / 1e9
         out["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
                            "frac": ach / peak, "peak_kind": peak_kind, "algorithmic_bytes": b,
-                           "kernels": "rows_pair_kernel + cols_acc_kernel"}
+                           "bytes_per_node": 66.5,
+                           "kernels": "field stores in step_tma_kernel + rows_fields_kernel + "
+                                      "cols_part_kernel + flush_part4_kernel"}
     return out
 
 

@@ -27,6 +27,7 @@
 #include <algorithm>
 #include <cmath>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "../../include/flb.h"
@@ -51,6 +52,24 @@ struct Ref9 {
 template <class R>
 __device__ __forceinline__ Cx<R> cmul(Cx<R> a, Cx<R> b) {
     return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+
+// Twiddle-table reads, in FP32 marked to stay in L1 (a pass touches at most a
+// few KB of the table, while the transformed data streams past).
+__device__ __forceinline__ Cx<float> ld_twiddle(const Cx<float>* p) {
+    float2 v;
+    asm("ld.global.nc.L1::evict_last.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+    return {v.x, v.y};
+}
+__device__ __forceinline__ Cx<double> ld_twiddle(const Cx<double>* p) { return *p; }
+
+// Reads of data used once (spectra, partial sums): not kept in L1.
+__device__ __forceinline__ float4 ld_stream(const float4* p) {
+    float4 v;
+    asm volatile("ld.global.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p));
+    return v;
 }
 
 // f_i - c_i of one stored value, in the transform precision R.
@@ -146,16 +165,26 @@ __device__ __forceinline__ void dft_reg(Cx<RT>* v) {
 }
 
 // Shared-memory position of element i of a sequence transformed with E
-// elements per thread and pass: one padding element every E, so that the
-// stride-R writes of the first pass spread over the banks.
+// elements per thread and pass. E = 8: a permutation within each aligned block
+// of 128 elements, bits 4-6 of i XORed into bits 0-2 and bit 6 into bit 3, so
+// that every access pattern of the radix-8 passes is free of bank conflicts
+// for 8-byte elements (the 16 lanes of a half warp reach 16 distinct bank
+// pairs): consecutive elements (the reads, the loads, the stores), stride 8
+// (the first pass's writes) and runs of 8 a stride 64 apart (the second
+// pass's writes); no padding. E = 16: one padding element every 16.
+__host__ __device__ constexpr int spos8(int i) { return i ^ ((i >> 4) & 7) ^ (((i >> 6) & 1) << 3); }
+
 template <int E>
 __device__ __forceinline__ int spos(int i) {
-    return i + (i >> (E == 16 ? 4 : 3));
+    if constexpr (E == 16)
+        return i + (i >> 4);
+    else
+        return spos8(i);
 }
 
 template <int E>
 __host__ __device__ constexpr int padded_len(int L) {
-    return L + (L >> (E == 16 ? 4 : 3)) + 1;
+    return E == 16 ? L + (L >> 4) + 1 : L;
 }
 
 // One Stockham pass of radix R (the autosort formulation of Govindaraju et
@@ -193,14 +222,18 @@ __device__ __forceinline__ void stockham_pass(Cx<RT>* s, int lgL, int lgNs, int 
 #pragma unroll
                 for (int r = 0; r < R; ++r) v[b][r] = x[spos<E>(j + r * nj)];
                 if (lgNs > 0) {
-                    // w_r = exp(-2 pi i r k / (Ns R)): loaded for r a power of
-                    // two, else the product w_hi w_(r - hi), hi the largest
-                    // power of two below r (at most three roundings deep)
+                    // w_r = exp(-2 pi i r k / (Ns R)) = w_1^r: w_1 read from the
+                    // table (consecutive lanes read consecutive entries), the
+                    // powers of two by squaring, the others as w_hi w_(r - hi),
+                    // hi the largest power of two below r (at most four
+                    // roundings deep)
                     Cx<RT> w[R];
+                    w[1] = ld_twiddle(T + (k << tsh));
+                    v[b][1] = cmul(v[b][1], w[1]);
 #pragma unroll
-                    for (int r = 1; r < R; ++r) {
-                        const int hi = r >= 8 ? 8 : r >= 4 ? 4 : r >= 2 ? 2 : 1;
-                        w[r] = hi == r ? T[(r * k) << tsh] : cmul(w[hi], w[r - hi]);
+                    for (int r = 2; r < R; ++r) {
+                        const int hi = r >= 8 ? 8 : r >= 4 ? 4 : 2;
+                        w[r] = hi == r ? cmul(w[r / 2], w[r / 2]) : cmul(w[hi], w[r - hi]);
                         v[b][r] = cmul(v[b][r], w[r]);
                     }
                 }
@@ -249,6 +282,80 @@ struct Elines {
 };
 
 constexpr int kThreads = 512;
+// Shared memory a column CTA may take so that two fit one SM (half of the
+// 227 KB a CTA can opt into on sm_100 / sm_103).
+constexpr int kColsSmemBudget = 232448 / 2;
+
+// ---- the same radix-8 passes with the length 2^LG known at compile time ----
+// (the FP32 kernels of the fused-field path): loop bounds, strides and the
+// twiddle scale are constants, and the positions of a butterfly's elements
+// come from one swizzled base per butterfly, spos8 being linear over XOR
+// (spos8(a ^ b) = spos8(a) ^ spos8(b)) and a + b = a ^ b for the disjoint bit
+// ranges of j and r nj (reads) and of d and r Ns (writes).
+template <int LG, int R, int LGNS>
+__device__ __forceinline__ void pass_c(Cx<float>* s, int count, int seq, const Cx<float>* __restrict__ T) {
+    constexpr int lgR = R == 2 ? 1 : R == 4 ? 2 : 3;
+    constexpr int L = 1 << LG;
+    constexpr int per = (L < kEfast ? L : kEfast) / R;   // butterflies per thread
+    constexpr int nj = L >> lgR;                         // butterflies per sequence
+    constexpr int tps = nj / per;                        // threads per sequence
+    constexpr int spr = kThreads / tps;                  // sequences per round
+    constexpr int Ns = 1 << LGNS;
+    constexpr int tsh = LG - LGNS - lgR;
+    const int t = (int)threadIdx.x % tps, qt = (int)threadIdx.x / tps;
+    for (int q0 = 0; q0 < count; q0 += spr) {
+        const int q = q0 + qt;
+        const bool active = q < count;
+        Cx<float>* x = s + q * seq;
+        Cx<float> v[per][R];
+        if (active) {
+#pragma unroll
+            for (int b = 0; b < per; ++b) {
+                const int j = t + b * tps;
+                const int pj = spos8(j);
+#pragma unroll
+                for (int r = 0; r < R; ++r) v[b][r] = x[pj ^ spos8(r * nj)];
+                if constexpr (LGNS > 0) {
+                    // w_r = w_1^r as in stockham_pass
+                    Cx<float> w[R];
+                    w[1] = ld_twiddle(T + ((j & (Ns - 1)) << tsh));
+                    v[b][1] = cmul(v[b][1], w[1]);
+#pragma unroll
+                    for (int r = 2; r < R; ++r) {
+                        const int hi = r >= 4 ? 4 : 2;
+                        w[r] = hi == r ? cmul(w[r / 2], w[r / 2]) : cmul(w[hi], w[r - hi]);
+                        v[b][r] = cmul(v[b][r], w[r]);
+                    }
+                }
+                dft_reg<R>(v[b]);
+            }
+        }
+        __syncthreads();
+        if (active) {
+#pragma unroll
+            for (int b = 0; b < per; ++b) {
+                const int j = t + b * tps;
+                const int pd = spos8(((j >> LGNS) << (LGNS + lgR)) + (j & (Ns - 1)));
+#pragma unroll
+                for (int r = 0; r < R; ++r) x[pd ^ spos8(r * Ns)] = v[b][r];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Forward transform of `count` sequences of length 2^LG (element i at spos8(i)).
+template <int LG, int LGNS = 0>
+__device__ __forceinline__ void fft_c(Cx<float>* s, int count, int seq, const Cx<float>* __restrict__ T) {
+    if constexpr (LGNS + 3 <= LG) {
+        pass_c<LG, 8, LGNS>(s, count, seq, T);
+        fft_c<LG, LGNS + 3>(s, count, seq, T);
+    } else if constexpr (LG - LGNS == 2) {
+        pass_c<LG, 4, LGNS>(s, count, seq, T);
+    } else if constexpr (LG - LGNS == 1) {
+        pass_c<LG, 2, LGNS>(s, count, seq, T);
+    }
+}
 
 // ---- fast path: both sides powers of two ----------------------------------
 
@@ -260,6 +367,16 @@ __device__ __forceinline__ void store_pair(Cx<float>* p, Cx<float> a, Cx<float> 
 __device__ __forceinline__ void store_pair(Cx<double>* p, Cx<double> a, Cx<double> b) {
     reinterpret_cast<double2*>(p)[0] = make_double2(a.re, a.im);
     reinterpret_cast<double2*>(p)[1] = make_double2(b.re, b.im);
+}
+
+// Layout of the half spectrum H[f]: columns m = 0..Lx/2 in pairs (2p, 2p + 1),
+// each pair stored y by y with its two values side by side, (m, y) at
+// (p Ly + y) 2 + (m & 1); a field holds hx2(Hx) pairs. A row-pair CTA then
+// writes whole 32-byte sectors ((2p, y), (2p + 1, y), (2p, y + 1), (2p + 1,
+// y + 1) in FP32), and a column's values are every other one of its pair's.
+__host__ __device__ constexpr int hx2(int Hx) { return (Hx + 1) / 2; }
+__device__ __forceinline__ size_t h_index(int m, int y, int Ly) {
+    return ((size_t)(m >> 1) * Ly + y) * 2 + (m & 1);
 }
 
 // The x-transform of the three fields of the row pair (y0, y0 + 1), staged in
@@ -276,13 +393,22 @@ __device__ __forceinline__ void rows_transform_store(Cx<R>* s, int seq, int lgLx
     fft_seqs<kEfast>(s, lgLx, 3, seq, tw);
     // z = a + i b with a, b real: A(m) = (Z(m) + conj Z(-m)) / 2,
     // B(m) = (Z(m) - conj Z(-m)) / (2i)
+    const int np = hx2(Hx);
     for (int f = 0; f < 3; ++f) {
         const Cx<R>* z = s + f * seq;
-        Cx<R>* out = H + (size_t)f * Hx * Ly + y0;
-        for (int m = threadIdx.x; m < Hx; m += blockDim.x) {
-            const Cx<R> u = z[spos<kEfast>(m)], w = z[spos<kEfast>((Lx - m) & (Lx - 1))];
-            store_pair(out + (size_t)m * Ly, Cx<R>{R(0.5) * (u.re + w.re), R(0.5) * (u.im - w.im)},
-                       Cx<R>{R(0.5) * (u.im + w.im), R(0.5) * (w.re - u.re)});
+        Cx<R>* out = H + (size_t)f * np * Ly * 2;
+        for (int p = threadIdx.x; p < np; p += blockDim.x) {
+            Cx<R> a[2], b[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int m = 2 * p + h;
+                const Cx<R> u = z[spos<kEfast>(m & (Lx - 1))], w = z[spos<kEfast>((Lx - m) & (Lx - 1))];
+                a[h] = {R(0.5) * (u.re + w.re), R(0.5) * (u.im - w.im)};
+                b[h] = {R(0.5) * (u.im + w.im), R(0.5) * (w.re - u.re)};
+            }
+            Cx<R>* o = out + ((size_t)p * Ly + y0) * 2;   // (2p, y0), (2p + 1, y0), then row y0 + 1
+            store_pair(o, a[0], a[1]);
+            store_pair(o + 2, b[0], b[1]);
         }
     }
 }
@@ -313,53 +439,73 @@ __global__ void __launch_bounds__(kThreads, 2) rows_pair_kernel(const T* __restr
 
 // One CTA per row pair (y0, y0 + 1) of the FP32 fields F[f][y][x] that the
 // step kernel wrote on this sampling step (bit-identical to the fields
-// node_fields forms from the same state), then rows_transform_store. Four
-// consecutive x per 16-byte load, all six loads of a step issued together.
-__global__ void __launch_bounds__(kThreads, 2) rows_fields_kernel(const float* __restrict__ F, int Lx,
-                                                               int Ly, int lgLx,
+// node_fields forms from the same state), Lx = 2^LG: the x-transform of the
+// three fields as in rows_transform_store, with the compile-time passes.
+template <int LG>
+__global__ void __launch_bounds__(kThreads, 2) rows_fields_kernel(const float* __restrict__ F, int Ly,
                                                                const Cx<float>* __restrict__ tw,
                                                                Cx<float>* __restrict__ H, int Hx) {
+    constexpr int Lx = 1 << LG;
     extern __shared__ __align__(16) unsigned char raw[];
     Cx<float>* s = reinterpret_cast<Cx<float>*>(raw);
-    const int seq = padded_len<kEfast>(Lx);
     const int y0 = 2 * blockIdx.x;
     const size_t N = (size_t)Lx * Ly;
     const float* r0 = F + (size_t)y0 * Lx;
-    if (Lx >= 4) {
-        for (int x = 4 * threadIdx.x; x < Lx; x += 4 * blockDim.x) {
-            float4 a[3], b[3];
+    // one x per lane and step (consecutive lanes store to consecutive
+    // swizzled positions: no bank conflicts), all loads of a thread issued
+    // together; x and x + 512 k share the swizzle of x (512 k has no bits below 7)
+    constexpr int U = Lx > kThreads ? Lx / kThreads : 1;
+    const int x0 = threadIdx.x;
+    if (x0 < Lx) {
+        float a[U][3], b[U][3];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
 #pragma unroll
             for (int f = 0; f < 3; ++f) {
-                a[f] = __ldg(reinterpret_cast<const float4*>(r0 + f * N + x));
-                b[f] = __ldg(reinterpret_cast<const float4*>(r0 + f * N + Lx + x));
+                a[u][f] = __ldcs(r0 + f * N + x0 + u * kThreads);
+                b[u][f] = __ldcs(r0 + f * N + Lx + x0 + u * kThreads);
             }
+        const int p0 = spos8(x0);
 #pragma unroll
-            for (int f = 0; f < 3; ++f) {
-                Cx<float>* z = s + f * seq;
-                z[spos<kEfast>(x)] = {a[f].x, b[f].x};
-                z[spos<kEfast>(x + 1)] = {a[f].y, b[f].y};
-                z[spos<kEfast>(x + 2)] = {a[f].z, b[f].z};
-                z[spos<kEfast>(x + 3)] = {a[f].w, b[f].w};
-            }
-        }
-    } else {
-        for (int x = threadIdx.x; x < Lx; x += blockDim.x)
+        for (int u = 0; u < U; ++u)
 #pragma unroll
-            for (int f = 0; f < 3; ++f) s[f * seq + spos<kEfast>(x)] = {r0[f * N + x], r0[f * N + Lx + x]};
+            for (int f = 0; f < 3; ++f) s[f * Lx + p0 + u * kThreads] = {a[u][f], b[u][f]};
     }
-    rows_transform_store(s, seq, lgLx, Lx, Ly, y0, tw, H, Hx);
+    __syncthreads();
+    fft_c<LG>(s, 3, Lx, tw);
+    // z = a + i b with a, b real: A(m) = (Z(m) + conj Z(-m)) / 2,
+    // B(m) = (Z(m) - conj Z(-m)) / (2i); H[f][m][y], column-major
+    constexpr int np = hx2(Lx / 2 + 1);
+    for (int f = 0; f < 3; ++f) {
+        const Cx<float>* z = s + f * Lx;
+        Cx<float>* out = H + (size_t)f * np * Ly * 2;
+        for (int p = threadIdx.x; p < np; p += kThreads) {
+            Cx<float> a[2], b[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int m = 2 * p + h;
+                const Cx<float> u = z[spos8(m & (Lx - 1))], w = z[spos8((Lx - m) & (Lx - 1))];
+                a[h] = {0.5f * (u.re + w.re), 0.5f * (u.im - w.im)};
+                b[h] = {0.5f * (u.im + w.im), 0.5f * (w.re - u.re)};
+            }
+            Cx<float>* o = out + ((size_t)p * Ly + y0) * 2;   // one 32-byte sector
+            store_pair(o, a[0], a[1]);
+            store_pair(o + 2, b[0], b[1]);
+        }
+    }
 }
 
-// The sums a column kernel adds to: FP64 (A = double: the products formed in
-// FP64, for FP64 transforms), or FP32 partials of at most kPartialSamples
-// samples (A = float: the products of the FP32 transform formed in FP32) that
-// flush_partials_kernel adds to the FP64 sums; GB300's FP64 rate makes the
-// FP64 products the cost of the column kernel otherwise.
+// The sums a column kernel adds to: FP64 for FP64 transforms (the products
+// formed in FP64, cols_acc_kernel), FP32 partials of at most kPartialSamples
+// samples for FP32 transforms (the products formed in FP32, cols_part_kernel)
+// that flush_part4_kernel adds to the FP64 sums; GB300's FP64 rate makes FP64
+// products the cost of the column kernel otherwise.
 constexpr int kPartialSamples = 16;
 
 // One CTA per block of C = 2^lc columns of the half spectrum H[f][m][y]: the
 // y-transform of each, then acc[q][m_x][m_y] += |drho|^2 (q = 0), |dj_x|^2
-// (1), Re and Im of dj_x conj(dj_y) (2, 3); acc[q] is Hx x Ly, m_y fastest.
+// (1), Re and Im of dj_x conj(dj_y) (2, 3); acc[q] is Hx x Ly, m_y fastest
+// (instantiated for FP64 transforms and sums).
 template <class R, class A>
 __global__ void __launch_bounds__(kThreads, 2) cols_acc_kernel(const Cx<R>* __restrict__ H, int lgLy,
                                                             int Hx, int lc,
@@ -373,6 +519,7 @@ __global__ void __launch_bounds__(kThreads, 2) cols_acc_kernel(const Cx<R>* __re
     const int n = Ly << lc;
     const int lgn = lgLy + lc;
     const size_t Q = (size_t)Hx * Ly;
+    const size_t QH = (size_t)hx2(Hx) * Ly * 2;   // values of H per field
     // kLoad independent loads in flight per thread before the stores
     constexpr int kLoad = 8;
     for (int j0 = threadIdx.x; j0 < 3 * n; j0 += kLoad * blockDim.x) {
@@ -381,7 +528,7 @@ __global__ void __launch_bounds__(kThreads, 2) cols_acc_kernel(const Cx<R>* __re
         for (int u = 0; u < kLoad; ++u) {
             const int j = j0 + u * blockDim.x;
             const int f = j >> lgn, cc = (j >> lgLy) & (C - 1), y = j & (Ly - 1);
-            v[u] = (j < 3 * n && c0 + cc < Hx) ? H[(size_t)f * Q + (size_t)(c0 + cc) * Ly + y]
+            v[u] = (j < 3 * n && c0 + cc < Hx) ? H[(size_t)f * QH + h_index(c0 + cc, y, Ly)]
                                                : Cx<R>{R(0), R(0)};
         }
 #pragma unroll
@@ -426,12 +573,113 @@ __global__ void __launch_bounds__(kThreads, 2) cols_acc_kernel(const Cx<R>* __re
     }
 }
 
-// acc[k] += part[k] in FP64, part[k] = 0.
-__global__ void flush_partials_kernel(float* __restrict__ part, double* __restrict__ acc, size_t n) {
-    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+// Columns per CTA of the column kernels: the most (up to 4) whose three
+// sequences of 2^LG FP32 values leave room for two CTAs per SM.
+__host__ __device__ constexpr int cols_lc(int lg) {
+    return (24 << lg) * 4 <= kColsSmemBudget ? 2 : (24 << lg) * 2 <= kColsSmemBudget ? 1 : 0;
+}
+
+// The FP32 column kernel of the fused-field path, Ly = 2^LG, C = 2^cols_lc(LG)
+// columns per CTA: the y-transforms with the compile-time passes, then the
+// four partial sums of each half-plane point side by side (part[k] =
+// (|drho|^2, |dj_x|^2, Re, Im of dj_x conj dj_y), k = m_x Ly + m_y), one
+// 16-byte read and one 16-byte write per point; spectra and partial sums are
+// streamed past L1, where the twiddles are kept. With Ly >= 128 the swizzle
+// of the CTA's value i (column i >> LG, element i mod Ly) is spos8(i).
+template <int LG>
+__global__ void __launch_bounds__(kThreads, 2) cols_part_kernel(const Cx<float>* __restrict__ H, int Hx,
+                                                             const Cx<float>* __restrict__ tw,
+                                                             float4* __restrict__ part) {
+    constexpr int Ly = 1 << LG, LC = cols_lc(LG), C = 1 << LC;
+    constexpr int n = Ly << LC;        // values per field in this CTA
+    extern __shared__ __align__(16) unsigned char raw[];
+    Cx<float>* s = reinterpret_cast<Cx<float>*>(raw);
+    const int c0 = blockIdx.x * C;
+    const size_t QH = (size_t)hx2(Hx) * Ly * 2;   // values of H per field
+    const int nvalid = min(C, Hx - c0) * Ly;     // values of columns that exist
+    auto pos = [](int i) { return Ly >= 128 ? spos8(i) : (i & ~(Ly - 1)) + spos8(i & (Ly - 1)); };
+    // all of a field's loads in flight. One column (Ly = 4096): a value per
+    // lane, every other 8 bytes of the column pair (the CTA of the other
+    // column reads the rest, mostly from L2). Column pairs: both columns' y
+    // values as one 16-byte load, lanes over consecutive y.
+    constexpr int U = n > kThreads ? n / kThreads : 1;
+    const int i0 = threadIdx.x;
+    if (i0 < n) {
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            const Cx<float>* Hf = H + (size_t)f * QH + (size_t)c0 * Ly;   // pair c0 / 2 (c0 even when C > 1)
+            if constexpr (C == 1) {
+                float2 v[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int y = i0 + u * kThreads;
+                    v[u] = __ldcs(reinterpret_cast<const float2*>(H + (size_t)f * QH + h_index(c0, y, Ly)));
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) s[f * n + pos(i0 + u * kThreads)] = {v[u].x, v[u].y};
+            } else {
+                // value pair q (i = 2 q): pair of columns q >> LG, element y = q mod Ly
+                constexpr int U2 = U / 2 > 0 ? U / 2 : 1;
+                float4 v[U2];
+#pragma unroll
+                for (int u = 0; u < U2; ++u) {
+                    const int q = i0 + u * kThreads;   // < n / 2
+                    v[u] = q < n / 2 && 2 * (q >> LG) < min(C, Hx - c0)
+                               ? __ldcs(reinterpret_cast<const float4*>(Hf + 2 * q))
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+#pragma unroll
+                for (int u = 0; u < U2; ++u) {
+                    const int q = i0 + u * kThreads;
+                    if (q < n / 2) {
+                        const int cp = q >> LG, y = q & (Ly - 1);   // columns 2 cp, 2 cp + 1 of the CTA
+                        s[f * n + pos(2 * cp * Ly + y)] = {v[u].x, v[u].y};
+                        s[f * n + pos((2 * cp + 1) * Ly + y)] = {v[u].z, v[u].w};
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    fft_c<LG>(s, 3 * C, Ly, tw);
+    float4* pc = part + (size_t)c0 * Ly;   // the CTA's columns, contiguous
+    constexpr int kAcc = U < 4 ? U : 4;
+    if (i0 < n) {
+#pragma unroll
+        for (int u0 = 0; u0 < U; u0 += kAcc) {
+            float4 old[kAcc];
+#pragma unroll
+            for (int u = 0; u < kAcc; ++u) {
+                const int i = i0 + (u0 + u) * kThreads;
+                old[u] = i < nvalid ? ld_stream(pc + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < kAcc; ++u) {
+                const int i = i0 + (u0 + u) * kThreads;
+                if (i >= nvalid) continue;
+                const int p = pos(i);
+                const Cx<float> a = s[p], b = s[n + p], d = s[2 * n + p];
+                float4 o = old[u];
+                o.x += a.re * a.re + a.im * a.im;
+                o.y += b.re * b.re + b.im * b.im;
+                o.z += b.re * d.re + b.im * d.im;
+                o.w += b.im * d.re - b.re * d.im;
+                pc[i] = o;
+            }
+        }
+    }
+}
+
+// acc[q Q + k] += part[k].q in FP64, part[k] = 0 (Q half-plane points).
+__global__ void flush_part4_kernel(float4* __restrict__ part, double* __restrict__ acc, size_t Q) {
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < Q;
          k += (size_t)gridDim.x * blockDim.x) {
-        acc[k] += (double)part[k];
-        part[k] = 0.f;
+        const float4 v = part[k];
+        acc[k] += (double)v.x;
+        acc[Q + k] += (double)v.y;
+        acc[2 * Q + k] += (double)v.z;
+        acc[3 * Q + k] += (double)v.w;
+        part[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
 }
 
@@ -571,10 +819,32 @@ cudaError_t upload_twiddles(int L, void** out) {
 cudaError_t flush_partials(StructSampler* s, cudaStream_t st) {
     s->pending = 0;
     if (!s->part) return cudaSuccess;
-    const int grid = (int)std::min<size_t>(4096, (s->acc_count + 255) / 256);
-    flush_partials_kernel<<<grid, 256, 0, st>>>(s->part, s->acc, s->acc_count);
+    const size_t Q = s->acc_count / 4;
+    const int grid = (int)std::min<size_t>(4096, (Q + 255) / 256);
+    flush_part4_kernel<<<grid, 256, 0, st>>>(reinterpret_cast<float4*>(s->part), s->acc, Q);
     return cudaGetLastError();
 }
+
+// The compile-time-length kernels by log2 of the length (1..12).
+using RowsFieldsFn = void (*)(const float*, int, const Cx<float>*, Cx<float>*, int);
+using ColsPartFn = void (*)(const Cx<float>*, int, const Cx<float>*, float4*);
+template <int LG>
+constexpr RowsFieldsFn rows_fields_at() { return rows_fields_kernel<LG>; }
+template <int LG>
+constexpr ColsPartFn cols_part_at() { return cols_part_kernel<LG>; }
+template <int... LG>
+RowsFieldsFn rows_fields_fn(int lg, std::integer_sequence<int, LG...>) {
+    const RowsFieldsFn t[] = {rows_fields_at<LG + 1>()...};
+    return lg >= 1 && lg <= (int)sizeof...(LG) ? t[lg - 1] : nullptr;
+}
+template <int... LG>
+ColsPartFn cols_part_fn(int lg, std::integer_sequence<int, LG...>) {
+    const ColsPartFn t[] = {cols_part_at<LG + 1>()...};
+    return lg >= 1 && lg <= (int)sizeof...(LG) ? t[lg - 1] : nullptr;
+}
+constexpr int kMaxFastLg = 12;   // sides up to 4096
+RowsFieldsFn rows_fields_for(int lg) { return rows_fields_fn(lg, std::make_integer_sequence<int, kMaxFastLg>{}); }
+ColsPartFn cols_part_for(int lg) { return cols_part_fn(lg, std::make_integer_sequence<int, kMaxFastLg>{}); }
 
 // The column launch of the power-of-two path and the partial-sum flush.
 template <class R>
@@ -583,11 +853,12 @@ cudaError_t cols_accumulate(StructSampler* s, cudaStream_t st) {
     const int C = 1 << s->lc;
     cudaError_t ce;
     if constexpr (sizeof(R) == 4) {
-        ce = cudaFuncSetAttribute(cols_acc_kernel<R, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        const ColsPartFn k = cols_part_for(log2i(s->Ly));
+        ce = cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)s->smem_cols);
         if (ce != cudaSuccess) return ce;
-        cols_acc_kernel<R, float><<<(s->Hx + C - 1) / C, kThreads, s->smem_cols, st>>>(
-            H, log2i(s->Ly), s->Hx, s->lc, (const Cx<R>*)s->twy, s->part);
+        k<<<(s->Hx + C - 1) / C, kThreads, s->smem_cols, st>>>(H, s->Hx, (const Cx<R>*)s->twy,
+                                                               reinterpret_cast<float4*>(s->part));
         ce = cudaGetLastError();
         if (ce == cudaSuccess && ++s->pending == kPartialSamples) ce = flush_partials(s, st);
         return ce;
@@ -693,7 +964,10 @@ int structure_create(StructSampler** out, int Lx, int Ly, int rbytes, bool fused
         // columns per CTA: the most that leave room for two CTAs per SM, else one
         const size_t col = 3 * cb * padded_len<kEfast>(Ly);
         s->lc = 0;
-        while (s->lc < 2 && col << (s->lc + 1) <= (size_t)optin / 2) ++s->lc;
+        if (rbytes == 4)   // the FP32 column kernel's fixed count (two CTAs per SM on sm_103)
+            s->lc = cols_lc(log2i(Ly));
+        else
+            while (s->lc < 2 && col << (s->lc + 1) <= (size_t)optin / 2) ++s->lc;
         s->smem_cols = col << s->lc;
         s->fast = s->smem_rows <= (size_t)optin && s->smem_cols <= (size_t)optin;
     }
@@ -709,7 +983,7 @@ int structure_create(StructSampler** out, int Lx, int Ly, int rbytes, bool fused
     }
     const size_t N = (size_t)Lx * Ly;
     s->Hx = Lx / 2 + 1;
-    const size_t nfield = s->fast ? 3 * (size_t)Ly * s->Hx : 3 * N;
+    const size_t nfield = s->fast ? 3 * (size_t)Ly * 2 * hx2(s->Hx) : 3 * N;
     s->acc_count = s->fast ? 4 * (size_t)Ly * s->Hx : 4 * N;
     cudaError_t ce = cudaMalloc(&s->fields, nfield * cb);
     if (ce == cudaSuccess) ce = cudaMalloc(&s->acc, s->acc_count * sizeof(double));
@@ -770,11 +1044,12 @@ float* structure_fields(StructSampler* s) { return s ? s->fin : nullptr; }
 
 cudaError_t structure_sample_fields(StructSampler* s, cudaStream_t st) {
     if (!s->fin) return cudaErrorInvalidValue;
-    cudaError_t ce = cudaFuncSetAttribute(rows_fields_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const RowsFieldsFn k = rows_fields_for(log2i(s->Lx));
+    cudaError_t ce = cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)s->smem_rows);
     if (ce != cudaSuccess) return ce;
-    rows_fields_kernel<<<s->Ly / 2, kThreads, s->smem_rows, st>>>(
-        s->fin, s->Lx, s->Ly, log2i(s->Lx), (const Cx<float>*)s->twx, (Cx<float>*)s->fields, s->Hx);
+    k<<<s->Ly / 2, kThreads, s->smem_rows, st>>>(s->fin, s->Ly, (const Cx<float>*)s->twx,
+                                                  (Cx<float>*)s->fields, s->Hx);
     ce = cudaGetLastError();
     if (ce == cudaSuccess) ce = cols_accumulate<float>(s, st);
     if (ce == cudaSuccess) s->nsamp += 1;
