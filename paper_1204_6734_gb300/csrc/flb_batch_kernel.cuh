@@ -304,8 +304,7 @@ batch_step_kernel(const BatchArgs a) {
                         }
                         if (row + kSamplers >= TH && p == BS::PAIRS - 1) {
                             // last read of the stage: release before the arithmetic
-                            __syncwarp();
-                            if (lane_id == 0) mbar_arrive(&empty[s]);
+                            warp_arrive(&empty[s], lane_id);
                             released = true;
                         }
                         const int xA = info.x + lane_id + 64 * p;
@@ -326,10 +325,7 @@ batch_step_kernel(const BatchArgs a) {
                     }
                 }
             }
-            if (!released) {
-                __syncwarp();
-                if (lane_id == 0) mbar_arrive(&empty[s]);
-            }
+            if (!released) warp_arrive(&empty[s], lane_id);
             if (producer && issued < ntile) {
                 if (!mbar_wait_sleep(&empty[s], n & 1)) {
                     ok = false;
@@ -381,8 +377,7 @@ batch_step_kernel(const BatchArgs a) {
         const float* stg = smem + s * BS::STAGE;
         const int4 info = *reinterpret_cast<const int4*>(stg + 9 * BS::SPLANE + BS::HOT);
         if (!info.w) {
-            __syncwarp();
-            if (lane_id == 0) mbar_arrive(&empty[s]);
+            warp_arrive(&empty[s], lane_id);
             continue;
         }
         const ReplicaHot& hs = *reinterpret_cast<const ReplicaHot*>(stg + 9 * BS::SPLANE);
@@ -447,14 +442,15 @@ batch_step_kernel(const BatchArgs a) {
                 gram_mma(gl, reinterpret_cast<float(&)[8]>(gc));
                 if (++gtiles == kGramFlushTiles) gram_out();
             }
-            __syncwarp();
-            if (lane_id == 0) mbar_arrive(&empty[s]);
+            warp_arrive(&empty[s], lane_id);
             if (stt) {
                 if (inA && (stt & 0xFF)) record_error(err, (int)(stt & 0xFF), nodeA, tr);
                 if (inB && (stt >> 8)) record_error(err, (int)(stt >> 8), nodeA + TW / 2, tr);
             }
-            // tiles away from the lattice edge store without per-node checks
-            if (info.x > 0 && info.y > 0 && info.x + TW < geo.Lx && info.y + TH < geo.Ly) {
+            // node pairs away from the lattice edge (every pair of an inner
+            // tile, most of an edge tile's) store without ghost copies
+            const bool inner = info.x > 0 && info.y > 0 && info.x + TW < geo.Lx && info.y + TH < geo.Ly;
+            if (inner || (inA && inB && xA > 0 && xB < geo.Lx - 1 && y > 0 && y < geo.Ly - 1)) {
                 float* pa = dst + at(geo, 0, xA, y);
 #pragma unroll
                 for (int i = 0; i < 9; ++i) {
@@ -478,8 +474,7 @@ batch_step_kernel(const BatchArgs a) {
             float f[9];
             const uint32_t stt = collide_basis<float, BASIS>(
                 g, NodeNoise{hs.cc.key, node, tr}, load, a.lut, hs.cc, f);
-            __syncwarp();
-            if (lane_id == 0) mbar_arrive(&empty[s]);
+            warp_arrive(&empty[s], lane_id);
             if (in) {
                 if (stt & 0xFF) record_error(err, (int)(stt & 0xFF), node, tr);
                 store_node(dst, geo, x, y, f);

@@ -390,8 +390,10 @@ step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
             if (inA && (stt & 0xFF)) record_error(a.err, (int)(stt & 0xFF), nodeA, a.step);
             if (inB && (stt >> 8)) record_error(a.err, (int)(stt >> 8), nodeA + 64u, a.step);
         }
-        // tiles away from the lattice edge store without per-node checks
-        if (x0 > 0 && y0 > 0 && x0 + kTW < Lx && y0 + TH < Ly) {
+        // node pairs away from the lattice edge (every pair of an inner tile,
+        // most of an edge tile's) store without ghost copies
+        const bool inner = x0 > 0 && y0 > 0 && x0 + kTW < Lx && y0 + TH < Ly;
+        if (inner || (inA && inB && xA > 0 && xB < Lx - 1 && y > 0 && y < Ly - 1)) {
             float* pa = a.dst + at(a.geo, 0, xA, y);
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
