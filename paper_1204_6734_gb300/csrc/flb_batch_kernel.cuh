@@ -111,17 +111,13 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
         : "memory");
 }
 
-__device__ __forceinline__ bool sampled_at(const ReplicaHot& h, int t) {
-    return h.every > 0 && t >= h.warmup && ((t - h.warmup) % h.every) == 0;
-}
-
 // Fill stage s with global tile t (one thread). The tile record {x0, y0, t_r,
 // live} is written with a plain shared store before the arrival on the full
 // barrier, whose release makes it visible to the waiting warps.
 struct TileFetch {
     const ReplicaDesc* d;
     int x0, y0, tr, Ly;
-    bool live;
+    bool live, sampled;
 };
 
 // The global reads behind one tile (its code, then its replica's time and
@@ -138,6 +134,10 @@ __device__ __forceinline__ TileFetch batch_fetch(const BatchArgs& a, unsigned st
     const int tiles_x = __ldg(&f.d->hot.tiles_x);
     f.Ly = __ldg(&f.d->hot.Ly);
     f.live = f.tr < __ldg(&f.d->hot.tend);
+    // the sampling schedule, decided once per tile here rather than by every
+    // thread that reads the tile
+    const int every = __ldg(&f.d->hot.every), warmup = __ldg(&f.d->hot.warmup);
+    f.sampled = every > 0 && f.tr >= warmup && ((f.tr - warmup) % every) == 0;
     const int ty = local / tiles_x;
     f.x0 = (local - ty * tiles_x) * TW;
     f.y0 = ty * BS::TH;
@@ -148,7 +148,9 @@ template <int TW, int NPT, int NW>
 __device__ __forceinline__ void batch_issue(float* smem, const TileFetch& f, int s, uint64_t* full) {
     using BS = BatchShape<TW, NPT, NW>;
     float* st = smem + s * BS::STAGE;
-    *reinterpret_cast<int4*>(st + 9 * BS::SPLANE + BS::HOT) = make_int4(f.x0, f.y0, f.tr, f.live ? 1 : 0);
+    // record: origin, replica time, bit 0 live, bit 1 sampled at this time
+    *reinterpret_cast<int4*>(st + 9 * BS::SPLANE + BS::HOT) =
+        make_int4(f.x0, f.y0, f.tr, (f.live ? 1 : 0) | (f.live && f.sampled ? 2 : 0));
     if (!f.live) {
         mbar_arrive(&full[s]);
         return;
@@ -283,7 +285,7 @@ batch_step_kernel(const BatchArgs a) {
             const int4 info = *reinterpret_cast<const int4*>(stg + 9 * BS::SPLANE + BS::HOT);
             const ReplicaHot& h = *reinterpret_cast<const ReplicaHot*>(stg + 9 * BS::SPLANE);
             bool released = false;
-            if (info.w && sampled_at(h, info.z)) {
+            if (info.w & 2) {
                 double* acc = h.acc;
                 float ref[9];
 #pragma unroll
@@ -404,7 +406,7 @@ batch_step_kernel(const BatchArgs a) {
             const int xA = info.x + r, xB = xA + TW / 2;
             const bool inA = xA < geo.Lx && y < geo.Ly, inB = xB < geo.Lx && y < geo.Ly;
             const uint32_t nodeA = (uint32_t)xA + (uint32_t)geo.Lx * (uint32_t)y;
-            const bool smp = kTensor && sampled_at(hs, (int)tr);
+            const bool smp = kTensor && (info.w & 2);
             if (smp && hs.acc != run_key) {   // a new run of sampled tiles
                 gram_out();
                 ++run;
