@@ -451,25 +451,41 @@ __global__ void __launch_bounds__(kThreads, 2) rows_fields_kernel(const float* _
     const int y0 = 2 * blockIdx.x;
     const size_t N = (size_t)Lx * Ly;
     const float* r0 = F + (size_t)y0 * Lx;
-    // one x per lane and step (consecutive lanes store to consecutive
-    // swizzled positions: no bank conflicts), all loads of a thread issued
-    // together; x and x + 512 k share the swizzle of x (512 k has no bits below 7)
-    constexpr int U = Lx > kThreads ? Lx / kThreads : 1;
-    const int x0 = threadIdx.x;
-    if (x0 < Lx) {
-        float a[U][3], b[U][3];
+    if constexpr (Lx >= 4) {
+        // four consecutive x per lane and step (16-byte loads), all loads of a
+        // thread issued together; the four positions are spos8(x) ^ c (x a
+        // multiple of 4), and those of the 16 lanes of a half warp fall in
+        // distinct bank pairs for each c
+        constexpr int G = Lx / 4;                              // groups of four
+        constexpr int U = G > kThreads ? G / kThreads : 1;
+        const int g0 = threadIdx.x;
+        if (g0 < G) {
+            float4 a[U][3], b[U][3];
 #pragma unroll
-        for (int u = 0; u < U; ++u)
+            for (int u = 0; u < U; ++u)
 #pragma unroll
-            for (int f = 0; f < 3; ++f) {
-                a[u][f] = __ldcs(r0 + f * N + x0 + u * kThreads);
-                b[u][f] = __ldcs(r0 + f * N + Lx + x0 + u * kThreads);
+                for (int f = 0; f < 3; ++f) {
+                    const int x = 4 * (g0 + u * kThreads);
+                    a[u][f] = __ldcs(reinterpret_cast<const float4*>(r0 + f * N + x));
+                    b[u][f] = __ldcs(reinterpret_cast<const float4*>(r0 + f * N + Lx + x));
+                }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int p = spos8(4 * (g0 + u * kThreads));
+#pragma unroll
+                for (int f = 0; f < 3; ++f) {
+                    Cx<float>* z = s + f * Lx;
+                    z[p] = {a[u][f].x, b[u][f].x};
+                    z[p ^ 1] = {a[u][f].y, b[u][f].y};
+                    z[p ^ 2] = {a[u][f].z, b[u][f].z};
+                    z[p ^ 3] = {a[u][f].w, b[u][f].w};
+                }
             }
-        const int p0 = spos8(x0);
+        }
+    } else {
+        for (int x = threadIdx.x; x < Lx; x += kThreads)
 #pragma unroll
-        for (int u = 0; u < U; ++u)
-#pragma unroll
-            for (int f = 0; f < 3; ++f) s[f * Lx + p0 + u * kThreads] = {a[u][f], b[u][f]};
+            for (int f = 0; f < 3; ++f) s[f * Lx + spos8(x)] = {r0[f * N + x], r0[f * N + Lx + x]};
     }
     __syncthreads();
     fft_c<LG>(s, 3, Lx, tw);

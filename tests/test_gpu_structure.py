@@ -9,7 +9,9 @@ sfactoru, rcorrelator) sampled on the GPU, against the FP64 oracle.
 * FP32 and FP16-store lattices (FP32 transform): every step's sample against
   the oracle's transform of the lattice's own state (read back in FP64), so
   both sides see the same fields; 2e-5 of the largest mode (FP32 butterflies,
-  log2 L rounding steps on each axis).
+  log2 L rounding steps on each axis). The FP32 power-of-two sides take the
+  path whose fields the step kernel writes, down to sides of 2 and up to 4096
+  (the shortest and longest compile-time transforms).
 * the full 4096 x 4096 FP32 lattice: one sample at 24 wavevectors against the
   oracle's transform of those k one by one, plus Parseval over all k.
 """
@@ -60,7 +62,8 @@ def test_fp64_run_against_oracle(shape, basis):
 
 
 @pytest.mark.parametrize("precision,shape", [("fp32", (64, 32)), ("fp32", (512, 256)), ("fp32", (40, 24)),
-                                             ("fp16dev", (32, 48)), ("fp16dev", (128, 64))])
+                                             ("fp32", (2, 8)), ("fp32", (8, 2)), ("fp32", (4096, 2)),
+                                             ("fp32", (2, 4096)), ("fp16dev", (32, 48)), ("fp16dev", (128, 64))])
 def test_reduced_precision_samples_of_its_own_state(precision, shape):
     Lx, Ly = shape
     p = lattice_params(Lx, Ly, "local", precision, kT=1e-4, seed=3)
