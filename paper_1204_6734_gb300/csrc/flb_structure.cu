@@ -451,44 +451,37 @@ __global__ void __launch_bounds__(kThreads, 2) rows_fields_kernel(const float* _
     const int y0 = 2 * blockIdx.x;
     const size_t N = (size_t)Lx * Ly;
     const float* r0 = F + (size_t)y0 * Lx;
-    if constexpr (Lx >= 4) {
-        // four consecutive x per lane and step (16-byte loads), all loads of a
-        // thread issued together; the four positions are spos8(x) ^ c (x a
-        // multiple of 4), and those of the 16 lanes of a half warp fall in
-        // distinct bank pairs for each c
-        constexpr int G = Lx / 4;                              // groups of four
-        constexpr int U = G > kThreads ? G / kThreads : 1;
-        const int g0 = threadIdx.x;
-        if (g0 < G) {
-            float4 a[U][3], b[U][3];
+    if constexpr (LG >= 3) {
+        // the first radix-8 pass straight from the field rows: butterfly t of
+        // field q takes x = t + r Lx/8 (r = 0..7; consecutive lanes, coalesced
+        // loads), transforms in registers and writes its outputs 8 t + r to
+        // their swizzled positions spos8(8 t) ^ r, so the values do not pass
+        // through shared memory on their way in
+        constexpr int nj = Lx / 8, spr = kThreads / nj;
+        const int t = (int)threadIdx.x % nj, qt = (int)threadIdx.x / nj;
+        const int pd = spos8(8 * t);
+        for (int q0 = 0; q0 < 3; q0 += spr) {
+            const int q = q0 + qt;
+            if (q < 3) {
+                const float* rf = r0 + q * N + t;
+                Cx<float> v[8];
 #pragma unroll
-            for (int u = 0; u < U; ++u)
+                for (int r = 0; r < 8; ++r) v[r] = {__ldcs(rf + r * nj), __ldcs(rf + Lx + r * nj)};
+                dft_reg<8>(v);
+                Cx<float>* z = s + q * Lx;
 #pragma unroll
-                for (int f = 0; f < 3; ++f) {
-                    const int x = 4 * (g0 + u * kThreads);
-                    a[u][f] = __ldcs(reinterpret_cast<const float4*>(r0 + f * N + x));
-                    b[u][f] = __ldcs(reinterpret_cast<const float4*>(r0 + f * N + Lx + x));
-                }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int p = spos8(4 * (g0 + u * kThreads));
-#pragma unroll
-                for (int f = 0; f < 3; ++f) {
-                    Cx<float>* z = s + f * Lx;
-                    z[p] = {a[u][f].x, b[u][f].x};
-                    z[p ^ 1] = {a[u][f].y, b[u][f].y};
-                    z[p ^ 2] = {a[u][f].z, b[u][f].z};
-                    z[p ^ 3] = {a[u][f].w, b[u][f].w};
-                }
+                for (int r = 0; r < 8; ++r) z[pd ^ r] = v[r];
             }
         }
+        __syncthreads();
+        fft_c<LG, 3>(s, 3, Lx, tw);
     } else {
         for (int x = threadIdx.x; x < Lx; x += kThreads)
 #pragma unroll
             for (int f = 0; f < 3; ++f) s[f * Lx + spos8(x)] = {r0[f * N + x], r0[f * N + Lx + x]};
+        __syncthreads();
+        fft_c<LG>(s, 3, Lx, tw);
     }
-    __syncthreads();
-    fft_c<LG>(s, 3, Lx, tw);
     // z = a + i b with a, b real: A(m) = (Z(m) + conj Z(-m)) / 2,
     // B(m) = (Z(m) - conj Z(-m)) / (2i); H[f][m][y], column-major
     constexpr int np = hx2(Lx / 2 + 1);
@@ -614,27 +607,47 @@ __global__ void __launch_bounds__(kThreads, 2) cols_part_kernel(const Cx<float>*
     const size_t QH = (size_t)hx2(Hx) * Ly * 2;   // values of H per field
     const int nvalid = min(C, Hx - c0) * Ly;     // values of columns that exist
     auto pos = [](int i) { return Ly >= 128 ? spos8(i) : (i & ~(Ly - 1)) + spos8(i & (Ly - 1)); };
-    // all of a field's loads in flight. One column (Ly = 4096): a value per
-    // lane, every other 8 bytes of the column pair (the CTA of the other
-    // column reads the rest, mostly from L2). Column pairs: both columns' y
-    // values as one 16-byte load, lanes over consecutive y.
     constexpr int U = n > kThreads ? n / kThreads : 1;
     const int i0 = threadIdx.x;
-    if (i0 < n) {
+    if constexpr (LG >= 3) {
+        // the first radix-8 pass straight from H: butterfly t of sequence q
+        // (field q / C, column c0 + q mod C) takes y = t + r Ly/8 (consecutive
+        // lanes read consecutive y of the column), transforms in registers and
+        // writes its outputs 8 t + r to spos8(8 t) ^ r of the sequence
+        constexpr int nj = Ly / 8, spr = kThreads / nj;
+        const int t = (int)threadIdx.x % nj, qt = (int)threadIdx.x / nj;
+        const int pd = spos8(8 * t);
+        for (int q0 = 0; q0 < 3 * C; q0 += spr) {
+            const int q = q0 + qt;
+            if (q < 3 * C) {
+                const int f = q >> LC, c = c0 + (q & (C - 1));
+                Cx<float> v[8];
+                if (c < Hx) {
+                    const Cx<float>* col = H + (size_t)f * QH;
 #pragma unroll
-        for (int f = 0; f < 3; ++f) {
-            const Cx<float>* Hf = H + (size_t)f * QH + (size_t)c0 * Ly;   // pair c0 / 2 (c0 even when C > 1)
-            if constexpr (C == 1) {
-                float2 v[U];
+                    for (int r = 0; r < 8; ++r) {
+                        const float2 w = __ldcs(reinterpret_cast<const float2*>(col + h_index(c, t + r * nj, Ly)));
+                        v[r] = {w.x, w.y};
+                    }
+                    dft_reg<8>(v);
+                } else {
 #pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int y = i0 + u * kThreads;
-                    v[u] = __ldcs(reinterpret_cast<const float2*>(H + (size_t)f * QH + h_index(c0, y, Ly)));
+                    for (int r = 0; r < 8; ++r) v[r] = {0.f, 0.f};
                 }
+                Cx<float>* z = s + q * Ly;
 #pragma unroll
-                for (int u = 0; u < U; ++u) s[f * n + pos(i0 + u * kThreads)] = {v[u].x, v[u].y};
-            } else {
-                // value pair q (i = 2 q): pair of columns q >> LG, element y = q mod Ly
+                for (int r = 0; r < 8; ++r) z[pd ^ r] = v[r];
+            }
+        }
+        __syncthreads();
+        fft_c<LG, 3>(s, 3 * C, Ly, tw);
+    } else {
+        // all of a field's loads in flight; the C columns of a field: column
+        // pairs, both columns' y values as one 16-byte load
+        if (i0 < n) {
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                const Cx<float>* Hf = H + (size_t)f * QH + (size_t)c0 * Ly;   // pair c0 / 2 (c0 even when C > 1)
                 constexpr int U2 = U / 2 > 0 ? U / 2 : 1;
                 float4 v[U2];
 #pragma unroll
@@ -655,9 +668,9 @@ __global__ void __launch_bounds__(kThreads, 2) cols_part_kernel(const Cx<float>*
                 }
             }
         }
+        __syncthreads();
+        fft_c<LG>(s, 3 * C, Ly, tw);
     }
-    __syncthreads();
-    fft_c<LG>(s, 3 * C, Ly, tw);
     float4* pc = part + (size_t)c0 * Ly;   // the CTA's columns, contiguous
     constexpr int kAcc = U < 4 ? U : 4;
     if (i0 < n) {
