@@ -199,10 +199,15 @@ int flb_state_difference(flb_lattice a, flb_lattice b, double out[3]);
  * passes in shared memory) for power-of-two sides, a direct O(L^2) transform
  * per row or column for other sides; when both sides are powers of two up to
  * 4096, two launches per sample and sums over half the k plane (the other
- * half follows from S(-k) = S(k), R(-k) = conj R(k)). The first call with
- * every > 0 allocates the library's own device buffers (at most 3 complex
- * and 4 double arrays of Lx*Ly values), freed by flb_destroy. Errors: FLB_ERR_ARG (negative arguments; a side above 20480 in
- * FP32 or 10240 in FP64), FLB_ERR_OOM, a recorded device error (sticky). */
+ * half follows from S(-k) = S(k), R(-k) = conj R(k)); an FP32 lattice on the
+ * pipelined kernel then has the step kernel itself write the three fields of
+ * the state it starts from (the same FP32 values), and the two launches
+ * transform them. The first call with every > 0 allocates the library's own
+ * device buffers (at most 3 complex and 4 double arrays of Lx*Ly values; FP32
+ * power-of-two lattices also 4 float arrays of partial sums and 3 float field
+ * arrays), freed by flb_destroy. Errors: FLB_ERR_ARG (negative arguments; a
+ * side above 20480 in FP32 or 10240 in FP64), FLB_ERR_OOM, a recorded device
+ * error (sticky). */
 int flb_set_structure_sampling(flb_lattice h, int64_t warmup, int64_t every);
 
 /* The sampled factors, each an Ly x Lx array indexed [m_y][m_x] (host memory,
