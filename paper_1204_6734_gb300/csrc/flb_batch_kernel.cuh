@@ -418,8 +418,7 @@ batch_step_kernel(const BatchArgs a) {
                     run_s[run] = run_scale;
                 }
             }
-            // stage the nodes when the collision reads them a second time (the
-            // table f-norm reads them once: stage now)
+            // stage the nodes when the collision reads them a second time
             auto stage = [&](const f2* gs) {
                 const float inv = hs.gram_inv;
                 f2 hv[9];
@@ -433,9 +432,8 @@ batch_step_kernel(const BatchArgs a) {
             };
             auto refetch = [&](f2* gg) {
                 load(gg);
-                if (kTensor && BASIS != 2 && smp) stage(gg);
+                if (kTensor && smp) stage(gg);
             };
-            if (kTensor && BASIS == 2 && smp) stage(g);
             f2 f[9];
             const uint32_t stt = collide_basis<f2, BASIS>(
                 g, PairNoise{hs.cc.key, nodeA, nodeA + TW / 2, tr}, refetch,

@@ -510,10 +510,9 @@ int lattice_create(const flb_params* p, void* dev_workspace, size_t workspace_by
     }
     if (ce == cudaSuccess && sync) ce = cudaStreamSynchronize(h->stream);
     // sampling steps: the correlation sums on the tensor cores, 12 colliding
-    // warps, where the parameters allow it; otherwise, and for the table
-    // f-norm (whose table rows take the registers 12 warps leave), the sampler
-    // warps beside 8 colliding warps
-    const bool tensor = tensor_sampling_ok(p) && p->basis != FLB_BASIS_LOCAL_LUT;
+    // warps, where the parameters allow it; otherwise the sampler warps beside
+    // 8 colliding warps
+    const bool tensor = tensor_sampling_ok(p);
     h->tma.sample_mode = tensor ? kPlanTensorSampling : 0;
     if (ce == cudaSuccess && p->basis == FLB_BASIS_LOCAL_LUT &&
         lut_tables(&h->lut32, &h->lut64) != FLB_OK)

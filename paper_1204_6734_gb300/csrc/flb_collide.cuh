@@ -235,6 +235,196 @@ __device__ __forceinline__ void hermite_back(V D0, V K1, V K2, const V Dn[6], V 
     h[6] = b - xmy;
 }
 
+// Density, velocity and the non-equilibrium Hermite moments M^a - rho e_a(u),
+// a = 3..8 (Eqs. d2q93a, d2q94), of the populations g, u = j / rho.
+template <class V>
+__device__ __forceinline__ void hermite_moments(const V g[9], V& rho, V& ux, V& uy, V (&M)[6]) {
+    using S = typename Elem<V>::type;
+    const V s13 = g[1] + g[3], s24 = g[2] + g[4];
+    const V d13 = g[1] - g[3], d24 = g[2] - g[4];
+    const V c58 = g[5] + g[8], c67 = g[6] + g[7];
+    const V c56 = g[5] + g[6], c78 = g[7] + g[8];
+    const V cx = c58 - c67, cy = c56 - c78;
+    const V c = c58 + c67;
+    const V s1234 = s13 + s24;
+    rho = (g[0] + s1234) + c;
+    const V jx = d13 + cx, jy = d24 + cy;
+    const V ir = rcp(rho);
+    ux = jx * ir;
+    uy = jy * ir;
+    const V uxx = ux * ux, uyy = uy * uy, uxy = ux * uy;
+    const V usq = uxx + uyy;
+    const V t3 = uxx - uyy;
+    // Hermite equilibrium moments at rho = 1 (Eq. d2q94), negated: ne_a = -e_a
+    const V ne3 = t3 * V(S(-1.5)), ne4 = uxy * V(S(-3)), ne5 = usq * V(S(-1.5));
+    M[0] = mad(rho, ne3, (s13 - s24) * V(S(1.5)));
+    M[1] = mad(rho, ne4, ((g[5] - g[6]) + (g[7] - g[8])) * V(S(3)));
+    M[2] = mad(rho, ne5, mad(s1234, V(S(0.5)), c * V(S(2))) - g[0]);
+    M[3] = mad(cx, V(S(kSqrt6)), d13 * V(S(-kSqrt3h)));
+    M[4] = mad(cy, V(S(kSqrt6)), d24 * V(S(-kSqrt3h)));
+    M[5] = mad(g[0], V(S(0.5)), c * V(S(2))) - s1234;
+}
+
+// The Cholesky factor of the f-norm Schur complement at a velocity u (the
+// basis velocity), stored negated: Ln = -L' below the diagonal and inv_j =
+// 1/L'_jj (infinite where a pivot is not positive: u outside the valid
+// region). Inputs: u, its products and ne5 = -3/2 |u|^2.
+//  * Sn = -S, S = G_NN - e e^T - k1 k1^T - k2 k2^T (upper triangle), in closed
+//    form: with X = ux^2, Y = uy^2, Z = ux uy, Q = X + Y, D = X - Y the entries
+//    are short polynomials (the rank-3 update cancels most terms of G_NN),
+//    e.g. S_00 = 1 - 9Q/4 + 27/4 D^2 (1 - Q), S_22 = 1 - 9Q/4 + 27/4 Q^2 (1 - Q),
+//    S_01 = 27/2 Z D (1 - Q), S_55 = 1 + 3Q/2.
+//  * the factorisation and both triangular solves are chains of
+//    fma(Ln, ., .) followed by one scaling with 1/L'_jj.
+template <class V>
+__device__ __forceinline__ void fnorm_factor(V ux, V uy, V uxx, V uyy, V uxy, V usq, V t3, V ne5,
+                                             V (&Ln)[6][6], V (&inv)[6]) {
+    using S = typename Elem<V>::type;
+    V Sn[6][6];
+    {
+        const V Z2 = uxy * uxy, D2 = t3 * t3, Q2 = usq * usq;
+        const V nv = mad(usq, V(S(6.75)), V(S(-6.75)));      // -27/4 (1 - Q)
+        const V nv2 = mad(usq, V(S(13.5)), V(S(-13.5)));     // -27/2 (1 - Q)
+        const V nc1 = mad(usq, V(S(2.25)), V(S(-1)));        // -(1 - 9Q/4)
+        const V nw = mad(usq, V(S(-27)), V(S(18)));
+        const V ax = ux * V(S(kSqrt6 / 4)), ay = uy * V(S(kSqrt6 / 4));
+        Sn[0][0] = mad(D2, nv, nc1);
+        Sn[2][2] = mad(Q2, nv, nc1);
+        Sn[0][1] = (uxy * t3) * nv2;
+        Sn[1][1] = mad(Z2 + Z2, nv2, V(S(-1)));
+        Sn[1][2] = (uxy * usq) * nv2;
+        Sn[0][2] = (t3 * V(S(2.25))) * mad(mad(usq, V(S(3)), V(S(-3))), usq, V(S(1)));
+        Sn[0][5] = t3 * V(S(1.5));
+        Sn[1][5] = uxy * V(S(-6));
+        Sn[2][5] = ne5;
+        Sn[3][5] = ux * V(S(-kSqrt6));
+        Sn[4][5] = uy * V(S(-kSqrt6));
+        Sn[5][5] = mad(usq, V(S(-1.5)), V(S(-1)));
+        Sn[3][4] = uxy * mad(usq, V(S(9)), V(S(-6)));
+        Sn[3][3] = mad(uyy, mad(uyy, V(S(4.5)), mad(uxx, V(S(18)), V(S(-1.5)))),
+                       mad(uxx, V(S(-3)), V(S(-1))));
+        Sn[4][4] = mad(uxx, mad(uxx, V(S(4.5)), mad(uyy, V(S(18)), V(S(-1.5)))),
+                       mad(uyy, V(S(-3)), V(S(-1))));
+        Sn[0][3] = ax * mad(uyy, mad(t3, V(S(-27)), V(S(-6))), V(S(2)));
+        Sn[0][4] = ay * mad(uxx, mad(t3, V(S(-27)), V(S(6))), V(S(-2)));
+        Sn[1][3] = ay * mad(Z2, V(S(-54)), mad(uxx, V(S(12)), mad(uyy, V(S(6)), V(S(-4)))));
+        Sn[1][4] = ax * mad(Z2, V(S(-54)), mad(uyy, V(S(12)), mad(uxx, V(S(6)), V(S(-4)))));
+        Sn[2][3] = ax * mad(uyy, nw, V(S(-2)));
+        Sn[2][4] = ay * mad(uxx, nw, V(S(-2)));
+    }
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        V dn = Sn[j][j];                       // -(pivot)
+#pragma unroll
+        for (int k = 0; k < j; ++k) dn = mad(Ln[j][k], Ln[j][k], dn);
+        inv[j] = rsq_neg(dn);
+#pragma unroll
+        for (int i = j + 1; i < 6; ++i) {
+            V s = Sn[j][i];
+#pragma unroll
+            for (int k = 0; k < j; ++k) s = mad(Ln[i][k], Ln[j][k], s);
+            Ln[i][j] = s * inv[j];
+        }
+    }
+}
+
+// The f-norm collision given the non-equilibrium Hermite moments M (of the
+// node's own velocity) and the factor (Ln, inv) of the basis velocity u =
+// (ux, uy), here the table velocity u_g of the look-up-table variant. The
+// fully local collision (collide) takes the same steps with the node's own
+// velocity written out in one body: split into this function it measured 3 %
+// slower at 4096^2 (a different schedule of the same operations).
+//  * M~_N = L'^{-1} M, relaxation towards M~^{a,0} = 0 (Eq. fnormmeq) plus
+//    noise, D_N = L'^{-T} of the increments;
+//  * the conserved increments from the rows of L below the conserved block at
+//    u: -e, k1, k2 (zero entries omitted; cheap to rebuild from u, so they are
+//    computed here rather than kept in registers across the factorisation);
+//  * f* = g + W (.) P^T D, W_i = f_i^0(1, u) (Eq. d2q9f0). refetch(gg)
+//    supplies g again. Returns the status (invsum infinite: no basis at u).
+template <class V, class Noise, class Refetch>
+__device__ __forceinline__ uint32_t fnorm_update(const V (&M)[6], const V (&Ln)[6][6], const V (&inv)[6],
+                                                 V rho, V ux, V uy, Noise& noise, Refetch& refetch,
+                                                 const CollideConst<typename Elem<V>::type>& cc,
+                                                 V invsum, V f[9]) {
+    using S = typename Elem<V>::type;
+    const V uxx = ux * ux, uyy = uy * uy, uxy = ux * uy;
+    const V usq = uxx + uyy;
+    const V t3 = uxx - uyy;
+    const V ne3 = t3 * V(S(-1.5)), ne4 = uxy * V(S(-3)), ne5 = usq * V(S(-1.5));
+    const V s3x = ux * V(S(kSqrt3)), s3y = uy * V(S(kSqrt3));
+    // M~_N = L'^{-1} (M_N - rho e_N)
+    V y[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        V s = M[j];
+#pragma unroll
+        for (int k = 0; k < j; ++k) s = mad(Ln[j][k], y[k], s);
+        y[j] = s * inv[j];
+    }
+    // increments: relaxation towards M~^{a,0} = 0 (Eq. fnormmeq) plus noise
+    V z[6];
+    noise_increments(noise, rho, cc, z);
+#pragma unroll
+    for (int a = 0; a < 6; ++a) z[a] = mad(V(cc.nomega[a]), y[a], z[a]);
+    // D_N = L'^{-T} z
+#pragma unroll
+    for (int j = 5; j >= 0; --j) {
+        V s = z[j];
+#pragma unroll
+        for (int k = j + 1; k < 6; ++k) s = mad(Ln[k][j], z[k], s);
+        z[j] = s * inv[j];
+    }
+    const V nE = mad(ne3, z[0], mad(ne4, z[1], ne5 * z[2]));
+    V k1[5], k2[5];
+    {
+        const V base = mad(usq, V(S(-1.5)), V(S(1)));   // 1 - e5
+        k1[0] = s3x * mad(t3, V(S(-1.5)), V(S(1)));
+        k1[1] = s3y * mad(uxx, V(S(-3)), V(S(1)));
+        k1[2] = s3x * base;
+        k1[3] = uyy * V(S(kSqrt2x3h));
+        k1[4] = uxy * V(S(kSqrt2x3));
+        k2[0] = s3y * mad(t3, V(S(-1.5)), V(S(-1)));
+        k2[1] = s3x * mad(uyy, V(S(-3)), V(S(1)));
+        k2[2] = s3y * base;
+        k2[3] = k1[4];
+        k2[4] = uxx * V(S(kSqrt2x3h));
+    }
+    const V K1 = mad(k1[0], z[0], mad(k1[1], z[1], mad(k1[2], z[2], mad(k1[3], z[3], k1[4] * z[4]))));
+    const V K2 = mad(k2[0], z[0], mad(k2[1], z[1], mad(k2[2], z[2], mad(k2[3], z[3], k2[4] * z[4]))));
+    const V D0 = mad(s3x, K1, mad(s3y, K2, nE));
+    V h[9];
+    hermite_back<V, true>(D0, K1, K2, z, h);
+    // W_i = f_i^0(1, u) (Eq. d2q9f0)
+    V W[9];
+    {
+        const V base = mad(usq, V(S(-1.5)), V(S(1)));
+        const V b45 = mad(usq, V(S(4.5)), base);
+        const V ax = mad(uxx, V(S(4.5)), base), ay = mad(uyy, V(S(4.5)), base);
+        const V dp = mad(uxy, V(S(9)), b45), dm = mad(uxy, V(S(-9)), b45);
+        const V spy = ux + uy, smy = ux - uy;
+        W[0] = base * V(S(4.0 / 9.0));
+        const V tx = ax * V(S(1.0 / 9.0)), ty = ay * V(S(1.0 / 9.0));
+        W[1] = mad(ux, V(S(1.0 / 3.0)), tx);
+        W[3] = mad(ux, V(S(-1.0 / 3.0)), tx);
+        W[2] = mad(uy, V(S(1.0 / 3.0)), ty);
+        W[4] = mad(uy, V(S(-1.0 / 3.0)), ty);
+        const V tp = dp * V(S(1.0 / 36.0)), tm = dm * V(S(1.0 / 36.0));
+        W[5] = mad(spy, V(S(1.0 / 12.0)), tp);
+        W[7] = mad(spy, V(S(-1.0 / 12.0)), tp);
+        W[8] = mad(smy, V(S(1.0 / 12.0)), tm);
+        W[6] = mad(smy, V(S(-1.0 / 12.0)), tm);
+    }
+
+    V gg[9];
+    refetch(gg);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i] = mad(W[i], h[i], gg[i]);
+    if (all_ok(rho, invsum)) return 0;
+    const uint32_t st = lane_status(rho, invsum, true);
+    keep_invalid(st, gg, f);
+    return st;
+}
+
 // One collision. g: pre-collision populations; noise(N) fills the normals
 // N^3..N^8 (called once, after the basis is built, to keep registers free);
 // f: output.
@@ -321,60 +511,8 @@ __device__ __forceinline__ uint32_t collide(const V g[9], Noise noise, Refetch r
         k2[4] = uxx * V(S(kSqrt2x3h));
     };
 
-    // Sn = -S, S = G_NN - e e^T - k1 k1^T - k2 k2^T (upper triangle), in
-    // closed form: with X = ux^2, Y = uy^2, Z = ux uy, Q = X + Y, D = X - Y the
-    // entries are short polynomials (the rank-3 update cancels most terms of
-    // G_NN), e.g. S_00 = 1 - 9Q/4 + 27/4 D^2 (1 - Q), S_22 = 1 - 9Q/4 + 27/4 Q^2 (1 - Q),
-    // S_01 = 27/2 Z D (1 - Q), S_55 = 1 + 3Q/2.
-    V Sn[6][6];
-    {
-        const V Z2 = uxy * uxy, D2 = t3 * t3, Q2 = usq * usq;
-        const V nv = mad(usq, V(S(6.75)), V(S(-6.75)));      // -27/4 (1 - Q)
-        const V nv2 = mad(usq, V(S(13.5)), V(S(-13.5)));     // -27/2 (1 - Q)
-        const V nc1 = mad(usq, V(S(2.25)), V(S(-1)));        // -(1 - 9Q/4)
-        const V nw = mad(usq, V(S(-27)), V(S(18)));
-        const V ax = ux * V(S(kSqrt6 / 4)), ay = uy * V(S(kSqrt6 / 4));
-        Sn[0][0] = mad(D2, nv, nc1);
-        Sn[2][2] = mad(Q2, nv, nc1);
-        Sn[0][1] = (uxy * t3) * nv2;
-        Sn[1][1] = mad(Z2 + Z2, nv2, V(S(-1)));
-        Sn[1][2] = (uxy * usq) * nv2;
-        Sn[0][2] = (t3 * V(S(2.25))) * mad(mad(usq, V(S(3)), V(S(-3))), usq, V(S(1)));
-        Sn[0][5] = t3 * V(S(1.5));
-        Sn[1][5] = uxy * V(S(-6));
-        Sn[2][5] = ne5;
-        Sn[3][5] = ux * V(S(-kSqrt6));
-        Sn[4][5] = uy * V(S(-kSqrt6));
-        Sn[5][5] = mad(usq, V(S(-1.5)), V(S(-1)));
-        Sn[3][4] = uxy * mad(usq, V(S(9)), V(S(-6)));
-        Sn[3][3] = mad(uyy, mad(uyy, V(S(4.5)), mad(uxx, V(S(18)), V(S(-1.5)))),
-                       mad(uxx, V(S(-3)), V(S(-1))));
-        Sn[4][4] = mad(uxx, mad(uxx, V(S(4.5)), mad(uyy, V(S(18)), V(S(-1.5)))),
-                       mad(uyy, V(S(-3)), V(S(-1))));
-        Sn[0][3] = ax * mad(uyy, mad(t3, V(S(-27)), V(S(-6))), V(S(2)));
-        Sn[0][4] = ay * mad(uxx, mad(t3, V(S(-27)), V(S(6))), V(S(-2)));
-        Sn[1][3] = ay * mad(Z2, V(S(-54)), mad(uxx, V(S(12)), mad(uyy, V(S(6)), V(S(-4)))));
-        Sn[1][4] = ax * mad(Z2, V(S(-54)), mad(uyy, V(S(12)), mad(uxx, V(S(6)), V(S(-4)))));
-        Sn[2][3] = ax * mad(uyy, nw, V(S(-2)));
-        Sn[2][4] = ay * mad(uxx, nw, V(S(-2)));
-    }
-
-    // Cholesky of S with the factor stored negated: Ln = -L'
     V Ln[6][6], inv[6];
-#pragma unroll
-    for (int j = 0; j < 6; ++j) {
-        V dn = Sn[j][j];                       // -(pivot)
-#pragma unroll
-        for (int k = 0; k < j; ++k) dn = mad(Ln[j][k], Ln[j][k], dn);
-        inv[j] = rsq_neg(dn);
-#pragma unroll
-        for (int i = j + 1; i < 6; ++i) {
-            V s = Sn[j][i];
-#pragma unroll
-            for (int k = 0; k < j; ++k) s = mad(Ln[i][k], Ln[j][k], s);
-            Ln[i][j] = s * inv[j];
-        }
-    }
+    fnorm_factor(ux, uy, uxx, uyy, uxy, usq, t3, ne5, Ln, inv);
     const V invsum = ((inv[0] + inv[1]) + (inv[2] + inv[3])) + (inv[4] + inv[5]);
 
     // M~_N = L'^{-1} (M_N - rho e_N)
@@ -441,19 +579,24 @@ __device__ __forceinline__ uint32_t collide(const V g[9], Noise noise, Refetch r
 // ---------------------------------------------------------------------------
 // Look-up-table f-norm (Section 4, the paper's practical variant): the basis at
 // the nearest velocity u_g of a 51 x 51 table, u_g = ((k_x - 25)/50,
-// (k_y - 25)/50), k = floor(50 u + 25.5) in 0..50. A table entry holds, each
-// padded to kLutRow values, the rows a = 3..8 of the f-norm basis at u_g, the
-// weights W(u_g) = f^0(1, u_g), and a validity flag (0 where some W_i <= 0).
-// The collision: Y^a = m~^a(u_g) . (g - f^0(rho, u)) is the non-equilibrium
-// moment in the table basis (the equilibrium moments are the projection of the
-// node's own f^0, taken exactly), D^a = -omega_a Y^a + xi^a N^a, and
-// f* = g + W(u_g) (.) sum_a m~^a D^a.
+// (k_y - 25)/50), k = floor(50 u + 25.5) in 0..50. The collision projects
+// g - f^0(rho, u) (the node's own equilibrium, taken exactly) on the f-norm
+// basis at u_g, Y^a = m~^a(u_g) . (g - f^0(rho, u)), relaxes and adds noise,
+// D^a = -omega_a Y^a + xi^a N^a, and returns f* = g + W(u_g) (.) sum_a m~^a D^a.
+// Since g - f^0(rho, u) carries no mass or momentum, Y_N = L'(u_g)^{-1} (M_N -
+// rho e_N(u)) with the Hermite moments of the node: the local f-norm update
+// (fnorm_update) with the factor of u_g in place of the node's. A table entry
+// therefore holds that factor: Ln (the 15 entries below the diagonal, row by
+// row), inv (6), u_g (2) and a validity flag (0 where some W_i(u_g) <= 0, with
+// inv infinite there), 24 values, built in FP64.
 // ---------------------------------------------------------------------------
 constexpr int kLutN = 51;
-constexpr int kLutRow = 12;
-constexpr int kLutStride = 8 * kLutRow;   // 6 rows, W, flag (+ padding)
-constexpr int kLutW = 6 * kLutRow;
-constexpr int kLutFlag = 7 * kLutRow;
+constexpr int kLutStride = 24;   // values per entry
+constexpr int kLutInv = 15;
+constexpr int kLutU = 21;
+constexpr int kLutFlag = 23;
+
+__host__ __device__ constexpr int lut_ln_index(int i, int j) { return i * (i - 1) / 2 + j; }   // i > j
 
 __device__ __forceinline__ double lut_coord(double u) {
     return floor(__dadd_rn(__dmul_rn(50.0, u), 25.5));
@@ -470,11 +613,11 @@ __device__ __forceinline__ int lut_cell(S ux, S uy) {
     return (int)ky * kLutN + (int)kx;
 }
 
-// Row of kLutRow table values (16-byte aligned) through the read-only path.
-__device__ __forceinline__ void lut_load_row(const float* p, float (&r)[kLutRow]) {
+// One table entry (16-byte aligned) through the read-only path.
+__device__ __forceinline__ void lut_load_entry(const float* p, float (&r)[kLutStride]) {
     const float4* q = reinterpret_cast<const float4*>(p);
 #pragma unroll
-    for (int k = 0; k < kLutRow / 4; ++k) {
+    for (int k = 0; k < kLutStride / 4; ++k) {
         const float4 v = __ldg(q + k);
         r[4 * k] = v.x;
         r[4 * k + 1] = v.y;
@@ -482,105 +625,56 @@ __device__ __forceinline__ void lut_load_row(const float* p, float (&r)[kLutRow]
         r[4 * k + 3] = v.w;
     }
 }
-__device__ __forceinline__ void lut_load_row(const double* p, double (&r)[kLutRow]) {
+__device__ __forceinline__ void lut_load_entry(const double* p, double (&r)[kLutStride]) {
     const double2* q = reinterpret_cast<const double2*>(p);
 #pragma unroll
-    for (int k = 0; k < kLutRow / 2; ++k) {
+    for (int k = 0; k < kLutStride / 2; ++k) {
         const double2 v = __ldg(q + k);
         r[2 * k] = v.x;
         r[2 * k + 1] = v.y;
     }
 }
 
-template <class V, class Noise>
-__device__ __forceinline__ uint32_t collide_lut(const V g[9], Noise noise,
+template <class V, class Noise, class Refetch>
+__device__ __forceinline__ uint32_t collide_lut(const V g[9], Noise noise, Refetch refetch,
                                                 const typename Elem<V>::type* lut,
                                                 const CollideConst<typename Elem<V>::type>& cc,
                                                 V f[9]) {
     using S = typename Elem<V>::type;
     constexpr int NL = Lanes<V>::n;
-    const V s13 = g[1] + g[3], s24 = g[2] + g[4];
-    const V d13 = g[1] - g[3], d24 = g[2] - g[4];
-    const V c58 = g[5] + g[8], c67 = g[6] + g[7];
-    const V c56 = g[5] + g[6], c78 = g[7] + g[8];
-    const V rho = (g[0] + (s13 + s24)) + (c58 + c67);
-    const V jx = d13 + (c58 - c67), jy = d24 + (c56 - c78);
-    const V ir = rcp(rho);
-    const V ux = jx * ir, uy = jy * ir;
-    // table entry per lane
-    const S* e[NL];
-    uint32_t st = 0;
+    V rho, ux, uy, M[6];
+    hermite_moments(g, rho, ux, uy, M);
+    // the factor of each lane's table velocity; off the table or at an
+    // invalid cell, inv is infinite (the status then keeps the lane's g)
+    S e[NL][kLutStride];
+    bool on[NL];
 #pragma unroll
     for (int k = 0; k < NL; ++k) {
-        const S r = lane(rho, k);
         const int cell = lut_cell(lane(ux, k), lane(uy, k));
-        e[k] = lut + (size_t)(cell < 0 ? 0 : cell) * kLutStride;
-        uint32_t s = kStatusOk;
-        if (!(r > S(0)) || !isfinite(r))
-            s = kStatusNonfinite;
-        else if (cell < 0 || __ldg(e[k] + kLutFlag) == S(0))
-            s = kStatusInvalidVelocity;
-        st |= s << (8 * k);
+        on[k] = cell >= 0;
+        lut_load_entry(lut + (size_t)(cell < 0 ? 0 : cell) * kLutStride, e[k]);
     }
-    // one table row (9 values of each lane's entry) with vector loads
-    auto row_of = [&](int off, V r[9]) {
-        S a[NL][kLutRow];
-#pragma unroll
-        for (int k = 0; k < NL; ++k) lut_load_row(e[k] + off, a[k]);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            if constexpr (NL == 1)
-                r[i] = V(a[0][i]);
-            else
-                r[i] = V(a[0][i], a[NL - 1][i]);
-        }
+    auto val = [&](int q) {
+        if constexpr (NL == 1)
+            return V(e[0][q]);
+        else
+            return V(e[0][q], e[NL - 1][q]);
     };
-    // g - f^0(rho, u) (Eq. d2q9f0)
-    V d[9];
-    {
-        const V uxx = ux * ux, uyy = uy * uy, uxy = ux * uy;
-        const V usq = uxx + uyy;
-        const V base = mad(usq, V(S(-1.5)), V(S(1)));
-        const V b45 = mad(usq, V(S(4.5)), base);
-        const V ax = mad(uxx, V(S(4.5)), base), ay = mad(uyy, V(S(4.5)), base);
-        const V dp = mad(uxy, V(S(9)), b45), dm = mad(uxy, V(S(-9)), b45);
-        const V spy = ux + uy, smy = ux - uy;
-        const V r9 = rho * V(S(1.0 / 9.0)), r36 = rho * V(S(1.0 / 36.0));
-        const V tx = ax * r9, ty = ay * r9, tp = dp * r36, tm = dm * r36;
-        const V rx = rho * ux * V(S(1.0 / 3.0)), ry = rho * uy * V(S(1.0 / 3.0));
-        const V rp = rho * spy * V(S(1.0 / 12.0)), rm = rho * smy * V(S(1.0 / 12.0));
-        d[0] = g[0] - (base * rho) * V(S(4.0 / 9.0));
-        d[1] = g[1] - (tx + rx);
-        d[3] = g[3] - (tx - rx);
-        d[2] = g[2] - (ty + ry);
-        d[4] = g[4] - (ty - ry);
-        d[5] = g[5] - (tp + rp);
-        d[7] = g[7] - (tp - rp);
-        d[8] = g[8] - (tm + rm);
-        d[6] = g[6] - (tm - rm);
+    V Ln[6][6], inv[6];
+#pragma unroll
+    for (int i = 1; i < 6; ++i)
+#pragma unroll
+        for (int j = 0; j < i; ++j) Ln[i][j] = val(lut_ln_index(i, j));
+#pragma unroll
+    for (int j = 0; j < 6; ++j) inv[j] = val(kLutInv + j);
+    V invsum = ((inv[0] + inv[1]) + (inv[2] + inv[3])) + (inv[4] + inv[5]);
+    if (!(on[0] && on[NL - 1])) {
+        if constexpr (NL == 1)
+            invsum = V(S(INFINITY));
+        else
+            invsum = V(on[0] ? lane(invsum, 0) : S(INFINITY), on[1] ? lane(invsum, 1) : S(INFINITY));
     }
-    V xi[6];
-    noise_increments(noise, rho, cc, xi);
-    V h[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) h[i] = V(S(0));
-#pragma unroll
-    for (int a = 0; a < 6; ++a) {
-        V row[9];
-        row_of(a * kLutRow, row);
-        V y = row[0] * d[0];
-#pragma unroll
-        for (int i = 1; i < 9; ++i) y = mad(row[i], d[i], y);
-        const V D = mad(V(cc.nomega[a]), y, xi[a]);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) h[i] = mad(row[i], D, h[i]);
-    }
-    V W[9];
-    row_of(kLutW, W);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) f[i] = mad(W[i], h[i], g[i]);
-    keep_invalid(st, g, f);
-    return st;
+    return fnorm_update<V>(M, Ln, inv, rho, val(kLutU), val(kLutU + 1), noise, refetch, cc, invsum, f);
 }
 
 // The collision of basis BASIS: 0 Hermite norm, 1 f-norm, 2 look-up-table
@@ -591,7 +685,7 @@ __device__ __forceinline__ uint32_t collide_basis(const V g[9], Noise noise, Ref
                                                   const CollideConst<typename Elem<V>::type>& cc,
                                                   V f[9]) {
     if constexpr (BASIS == 2)
-        return collide_lut<V>(g, noise, lut, cc, f);
+        return collide_lut<V>(g, noise, refetch, lut, cc, f);
     else
         return collide<V, BASIS>(g, noise, refetch, cc, f);
 }

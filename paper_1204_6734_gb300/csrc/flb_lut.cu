@@ -1,12 +1,15 @@
 // flb_lut.cu -- the velocity table of the look-up-table f-norm (Section 4):
 // for each of the 51 x 51 table velocities u_g = ((k_x - 25)/50, (k_y - 25)/50)
-// the rows a = 3..8 of the f-norm basis at u_g, the weights f^0(1, u_g) and a
-// validity flag, in FP64 and FP32 (layout: flb_collide.cuh, kLutStride per
-// entry). Built once per device, on first use, by one kernel that factors the
-// Gram matrix at every table velocity in FP64; kept in this file's device
-// memory (2.0 MB per device) for the life of the process.
+// the Cholesky factor of the f-norm Schur complement at u_g (the form the
+// collision applies it in: below-diagonal entries negated, reciprocal diagonal),
+// u_g itself and a validity flag, in FP64 and FP32 (layout: flb_collide.cuh,
+// kLutStride per entry). Built once per device, on first use, by one kernel
+// that factors at every table velocity in FP64 (the FP32 table holds the FP64
+// values rounded); kept in this file's device memory (0.7 MB per device) for
+// the life of the process.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <mutex>
 
 #include "../../include/flb.h"
@@ -26,17 +29,21 @@ __global__ void lut_build_kernel(float* t32, double* t64) {
     if (cell >= kLutCells) return;
     const int kx = cell % kLutN, ky = cell / kLutN;
     const double ux = (kx - 25.0) / 50.0, uy = (ky - 25.0) / 50.0;
-    double mt[81], W[9];
-    const bool ok = fnorm_basis_fp64(ux, uy, mt);
+    double W[9];
     feq_unit_fp64(ux, uy, W);
+    bool ok = true;
+    for (int i = 0; i < 9; ++i) ok = ok && W[i] > 0.0;
+    const double uxx = ux * ux, uyy = uy * uy, uxy = ux * uy, usq = uxx + uyy;
+    double Ln[6][6], inv[6];
+    fnorm_factor<double>(ux, uy, uxx, uyy, uxy, usq, uxx - uyy, usq * -1.5, Ln, inv);
+    for (int j = 0; j < 6; ++j) ok = ok && isfinite(inv[j]);
     double* e = t64 + (size_t)cell * kLutStride;
-    for (int k = 0; k < kLutStride; ++k) e[k] = 0.0;
-    if (ok) {
-        for (int a = 0; a < 6; ++a)
-            for (int i = 0; i < 9; ++i) e[a * kLutRow + i] = mt[(a + 3) * 9 + i];
-        for (int i = 0; i < 9; ++i) e[kLutW + i] = W[i];
-        e[kLutFlag] = 1.0;
-    }
+    for (int i = 1; i < 6; ++i)
+        for (int j = 0; j < i; ++j) e[lut_ln_index(i, j)] = ok ? Ln[i][j] : 0.0;
+    for (int j = 0; j < 6; ++j) e[kLutInv + j] = ok ? inv[j] : (double)INFINITY;
+    e[kLutU] = ux;
+    e[kLutU + 1] = uy;
+    e[kLutFlag] = ok ? 1.0 : 0.0;
     float* e32 = t32 + (size_t)cell * kLutStride;
     for (int k = 0; k < kLutStride; ++k) e32[k] = (float)e[k];
 }

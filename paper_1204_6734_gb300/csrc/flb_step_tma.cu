@@ -356,7 +356,7 @@ step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
             add_sums(reinterpret_cast<float(&)[kSums]>(v), d);
         }
         // tensor sampling: stage this tile's nodes when the collision reads
-        // them a second time (the table f-norm reads them once: stage now)
+        // them a second time
         auto stage = [&](const f2* gs) {
             f2 hs[9];
 #pragma unroll
@@ -369,9 +369,8 @@ step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
         };
         auto refetch = [&](f2* gg) {
             load(gg);
-            if (kTensor && BASIS != 2) stage(gg);
+            if (kTensor) stage(gg);
         };
-        if (kTensor && BASIS == 2) stage(g);
         const uint32_t nodeA = a.node0 + (uint32_t)xA + (uint32_t)Lx * (uint32_t)y;
         f2 f[9];
         const uint32_t stt = collide_basis<f2, BASIS>(
