@@ -284,14 +284,19 @@ typedef struct flb_batch_s* flb_batch;
  *   staged in FP16, as FLB_OPT_PIPELINE_SAMPLING 3 of a lattice): only when
  *   every replica has kT > 0 and sqrt(rho0 / kT) <= 4000 (FLB_ERR_ARG from
  *   flb_batch_set_tile otherwise, and from flb_batch_add of a replica that
- *   breaks it; flb_batch_autotune skips them and reports -1 for their time).
+ *   breaks it; flb_batch_autotune skips them and reports -1 for their time);
+ * mixed: as 128 x 6, with each replica cut into columns of three tile kinds of
+ *   768 nodes (128 x 6, 64 x 12, 32 x 24): 128-wide columns, then one 64- or
+ *   32-wide column, or one of each, for the rest of the width, so that no
+ *   column pads more than 31 nodes of a row (the tensor-core conditions above).
  * One CTA per SM. */
 #define FLB_TILE_128x4 0
 #define FLB_TILE_64x8 1
 #define FLB_TILE_128x2 2
 #define FLB_TILE_128x6 3
 #define FLB_TILE_64x12 4
-#define FLB_TILE_COUNT 5
+#define FLB_TILE_MIXED 5
+#define FLB_TILE_COUNT 6
 
 /* Open an empty batch for replicas in `basis` (flb_basis): at most
  * max_replicas (1 .. 16384) at a time, population buffers carved from one

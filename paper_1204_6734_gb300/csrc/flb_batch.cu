@@ -77,9 +77,38 @@ constexpr int kMaxSide = 8192;
 size_t buffer_bytes(const Geometry& g) { return Arena::round_up((size_t)9 * g.plane * sizeof(float)); }
 
 int tile_rows(int tile) { return kBatchVariants[tile].th(); }
-int tile_cols(int tile) { return kBatchVariants[tile].tw; }
+int tile_cols(int tile) { return kBatchVariants[tile].mixed() ? kind_tw(0) : kBatchVariants[tile].tw; }
+
+// Column bands of the mixed tiling: nc[k] columns of kind k, the 128-wide
+// ones first; the rest w of the width takes one column of the narrowest kind
+// that covers it, or a 64-wide and a 32-wide column when 64 < w <= 96.
+struct Bands {
+    int nc[kKinds];
+    int64_t tiles[kKinds];
+};
+
+Bands mixed_bands(int Lx, int Ly) {
+    Bands b{};
+    b.nc[0] = Lx / kind_tw(0);
+    const int w = Lx - b.nc[0] * kind_tw(0);
+    if (w > kind_tw(0) - kind_tw(2)) {
+        ++b.nc[0];
+    } else if (w > kind_tw(1)) {
+        b.nc[1] = b.nc[2] = 1;
+    } else if (w > kind_tw(2)) {
+        b.nc[1] = 1;
+    } else if (w > 0) {
+        b.nc[2] = 1;
+    }
+    for (int k = 0; k < kKinds; ++k) b.tiles[k] = (int64_t)b.nc[k] * ((Ly + kind_th(k) - 1) / kind_th(k));
+    return b;
+}
 
 int64_t replica_tiles(const flb_params& p, int tile) {
+    if (kBatchVariants[tile].mixed()) {
+        const Bands b = mixed_bands(p.Lx, p.Ly);
+        return b.tiles[0] + b.tiles[1] + b.tiles[2];
+    }
     return (int64_t)((p.Lx + tile_cols(tile) - 1) / tile_cols(tile)) *
            ((p.Ly + tile_rows(tile) - 1) / tile_rows(tile));
 }
@@ -129,6 +158,19 @@ void drop_graphs(flb_batch_s* b) {
 // Tensor maps of the replica's two buffers for boxes of the tile shape, and
 // the tile-grid width the producer decodes tile indices with.
 cudaError_t encode_maps(ReplicaDesc& d, const BatchSlot& s, int tile) {
+    if (kBatchVariants[tile].mixed()) {
+        const Bands bd = mixed_bands(s.p.Lx, s.p.Ly);
+        cudaError_t e = cudaSuccess;
+        for (int k = 0; k < kKinds && e == cudaSuccess; ++k)
+            for (int j = 0; j < 2 && e == cudaSuccess; ++j)
+                e = tma_encode_planes(&d.map[2 * k + j], s.buf[j], s.geo, kind_bw(k), kind_th(k));
+        d.hot.tiles_x = bd.nc[0];
+        d.hot.kt0 = (int)bd.tiles[0];
+        d.hot.kt01 = (int)(bd.tiles[0] + bd.tiles[1]);
+        d.hot.kx1 = bd.nc[0] * kind_tw(0);
+        d.hot.kx2 = d.hot.kx1 + bd.nc[1] * kind_tw(1);
+        return e;
+    }
     const int bw = tile_cols(tile) + 8, th = tile_rows(tile);
     cudaError_t e = tma_encode_planes(&d.map[0], s.buf[0], s.geo, bw, th);
     if (e == cudaSuccess) e = tma_encode_planes(&d.map[1], s.buf[1], s.geo, bw, th);
@@ -329,6 +371,15 @@ int flb_batch_add(flb_batch b, const flb_params* p, int64_t nsteps, int32_t* slo
     h.Ly = p->Ly;
     h.gram_s = tensor_sampling_ok(p) ? (float)gram_scale(p) : 0.f;
     h.gram_inv = h.gram_s > 0.f ? (float)(1.0 / gram_scale(p)) : 0.f;
+    for (int q = 0; q < 6; ++q) {
+        h.pc.nomega[q] = make_float2(h.cc.nomega[q], h.cc.nomega[q]);
+        h.pc.namp[q] = make_float2(-h.cc.amp[q], -h.cc.amp[q]);
+    }
+    h.sinv = make_float2(h.gram_inv, h.gram_inv);
+    for (int i = 0; i < 9; ++i) {
+        const float v = -h.ref[i] * h.gram_inv;   // the FP32 product the kernel formed before
+        h.snref[i] = make_float2(v, v);
+    }
     h.t0 = 0;
     h.join = (int)(unsigned)b->step;
     h.warmup = 0;

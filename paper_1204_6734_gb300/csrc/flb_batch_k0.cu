@@ -21,6 +21,9 @@ const void* batch_kernel_std(int variant, bool sample) {
         case 4:
             return sample ? (const void*)batch_step_kernel<0, true, 64, 2, kBatchNWTensor>
                           : (const void*)batch_step_kernel<0, false, 64, 2, kBatchNWTensor>;
+        case 5:
+            return sample ? (const void*)batch_step_kernel<0, true, kMixedTW, 2, kBatchNWTensor>
+                          : (const void*)batch_step_kernel<0, false, kMixedTW, 2, kBatchNWTensor>;
         default:
             return nullptr;
     }
@@ -37,6 +40,7 @@ size_t batch_smem_bytes(int variant) {
         case 2: return BatchShape<128, 1>::smem_bytes();
         case 3: return BatchShape<128, 2, kBatchNWTensor>::smem_bytes();
         case 4: return BatchShape<64, 2, kBatchNWTensor>::smem_bytes();
+        case 5: return BatchShape<kMixedTW, 2, kBatchNWTensor>::smem_bytes();
         default: return 0;
     }
 }

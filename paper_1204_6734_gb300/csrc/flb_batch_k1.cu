@@ -21,6 +21,9 @@ const void* batch_kernel_loc(int variant, bool sample) {
         case 4:
             return sample ? (const void*)batch_step_kernel<1, true, 64, 2, kBatchNWTensor>
                           : (const void*)batch_step_kernel<1, false, 64, 2, kBatchNWTensor>;
+        case 5:
+            return sample ? (const void*)batch_step_kernel<1, true, kMixedTW, 2, kBatchNWTensor>
+                          : (const void*)batch_step_kernel<1, false, kMixedTW, 2, kBatchNWTensor>;
         default:
             return nullptr;
     }

@@ -3,7 +3,7 @@
 //
 // Every replica has its own two population buffers (ghost-frame layout,
 // flb_layout.cuh) and a descriptor in device memory: the TMA tensor maps of
-// its two buffers and a 256-byte "hot" block (collision constants, reference
+// its two buffers and a 448-byte "hot" block (collision constants, reference
 // equilibrium, geometry, pointers, time and sampling schedule). The tiles of
 // all replicas form one table; CTA b walks the contiguous range
 // [b T / G, (b + 1) T / G) of it, so it meets each replica in one run.
@@ -32,6 +32,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <cstddef>
 #include <cstdint>
 
 #include "flb_gram.cuh"
@@ -52,11 +53,31 @@ struct __align__(16) ReplicaHot {
     DevError* err;
     int tend;                 // the replica stops before time tend
     float gram_s;             // s = sqrt(kT rho0): nodes are staged as (f - ref) / s
+    // packed pairs {c, c} of the constants the node-pair consumers use
+    CollidePairs pc;          // -omega_a, -amp_a
+    float2 sinv;              // 1 / s
+    float2 snref[9];          // -ref_i / s: staged value (f_i - ref_i) / s = f_i / s + snref_i
+    // mixed tiling: tiles of kind 0 (tiles_x columns), of kinds 0 and 1, and
+    // the x origins of the kind-1 and kind-2 columns
+    int kt0, kt01, kx1, kx2;
 };
-static_assert(sizeof(ReplicaHot) == 256, "the hot block is copied as 256 bytes");
+static_assert(sizeof(ReplicaHot) == 448, "the hot block is copied as 448 bytes");
+static_assert(offsetof(ReplicaHot, pc) == 256 && offsetof(ReplicaHot, snref) % 8 == 0,
+              "packed pairs start on 8-byte boundaries");
+
+// Mixed tiling (tile width kMixedTW): a replica is cut into column bands of
+// three tile kinds of 768 nodes each, kind k = (128 >> k) x (6 << k) nodes:
+// 128-wide columns, then at most one 64-wide and one 32-wide column for the
+// rest of the width, so that no band pads more than 31 columns. Every kind
+// keeps two nodes per thread and 12 consumer warps.
+constexpr int kMixedTW = 0;
+constexpr int kKinds = 3;
+__host__ __device__ constexpr int kind_tw(int k) { return 128 >> k; }
+__host__ __device__ constexpr int kind_th(int k) { return 6 << k; }
+__host__ __device__ constexpr int kind_bw(int k) { return (128 >> k) + 8; }
 
 struct __align__(128) ReplicaDesc {
-    CUtensorMap map[2];       // tensor maps of buffer 0 and buffer 1
+    CUtensorMap map[2 * kKinds];   // tensor map of (kind k, buffer b) at 2 k + b
     ReplicaHot hot;
 };
 
@@ -82,21 +103,29 @@ constexpr int kBatchNW = 8;       // consumer warps beside sampler warps
 constexpr int kBatchNWTensor = 12;  // consumer warps with the tensor-core sums
 constexpr int kRunSlots = 4;        // runs of one replica whose sums a CTA keeps in shared memory
 
-template <int TW, int NPT, int NW_ = kBatchNW>
+template <int TW_, int NPT, int NW_ = kBatchNW>
 struct BatchShape {
     static constexpr int NW = NW_;
+    static constexpr bool MIXED = TW_ == kMixedTW;
+    static_assert(!MIXED || (NPT == 2 && NW == kBatchNWTensor), "mixed tiling: 12 warps, node pairs");
     static constexpr bool TENSOR = NW > kBatchNW;
+    static constexpr int TW = MIXED ? kind_tw(0) : TW_;           // (mixed: of kind 0)
     static constexpr int TH = NW * 32 * NPT / TW;                // rows per tile
     static constexpr int BW = TW + 8;                            // box width: x0 - 4 .. x0 + TW + 3
     static constexpr int RW = TW / NPT;                          // consumer threads per row
     static constexpr int PAIRS = TW / 64;                        // node pairs per sampler lane and row
-    static constexpr int SPLANE = (TH * BW + 31) / 32 * 32;      // floats per plane box
-    static constexpr int HOT = 64;                               // ReplicaHot
+    // floats per plane box (mixed: room for the largest box, kind 2's)
+    static constexpr int SPLANE = MIXED ? kind_th(2) * kind_bw(2) : (TH * BW + 31) / 32 * 32;
+    static constexpr int HOT = sizeof(ReplicaHot) / 4;           // floats of the hot block
     static constexpr int INFO = 32;                              // tile record, padded to 128 B
-    static constexpr int STAGE = 9 * SPLANE + HOT + INFO;
-    static constexpr int FIT = 163840 / (4 * STAGE);             // about 160 KB of stages
+    // a multiple of 32 floats, so that every plane box of every stage starts
+    // on the 128-byte boundary a tensor copy into shared memory needs
+    static constexpr int STAGE = (9 * SPLANE + HOT + INFO + 31) / 32 * 32;
+    static_assert(SPLANE % 32 == 0 && STAGE % 32 == 0, "128-byte aligned boxes");
+    static constexpr int FIT = (MIXED ? 180000 : 163840) / (4 * STAGE);   // 160-176 KB of stages
     static constexpr int STAGES = FIT < 16 ? FIT : 16;
-    static constexpr size_t GRAM = TENSOR ? (size_t)NW * kGramWarpHalves * 2 + kRunSlots * 256 * 8 + kRunSlots * 16 : 0;
+    static constexpr size_t GRAM =
+        TENSOR ? (size_t)NW * kGramWarpHalves * 2 + kRunSlots * 256 * 8 + kRunSlots * 16 + NW * 16 : 0;
     static constexpr size_t smem_bytes() {
         return sizeof(float) * (size_t)STAGES * STAGE + 2 * STAGES * sizeof(uint64_t) + 16 + GRAM;
     }
@@ -116,7 +145,7 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
 // barrier, whose release makes it visible to the waiting warps.
 struct TileFetch {
     const ReplicaDesc* d;
-    int x0, y0, tr, Ly;
+    int x0, y0, tr, Ly, kind, rep;
     bool live, sampled;
 };
 
@@ -128,7 +157,8 @@ __device__ __forceinline__ TileFetch batch_fetch(const BatchArgs& a, unsigned st
     using BS = BatchShape<TW, NPT, NW>;
     TileFetch f;
     const uint32_t code = __ldg(&a.tiles[t]);
-    f.d = a.desc + (code >> kLocalBits);
+    f.rep = (int)(code >> kLocalBits);
+    f.d = a.desc + f.rep;
     const int local = (int)(code & kLocalMask);
     f.tr = __ldg(&f.d->hot.t0) + (int)(step - (unsigned)__ldg(&f.d->hot.join));
     const int tiles_x = __ldg(&f.d->hot.tiles_x);
@@ -138,8 +168,24 @@ __device__ __forceinline__ TileFetch batch_fetch(const BatchArgs& a, unsigned st
     // thread that reads the tile
     const int every = __ldg(&f.d->hot.every), warmup = __ldg(&f.d->hot.warmup);
     f.sampled = every > 0 && f.tr >= warmup && ((f.tr - warmup) % every) == 0;
+    f.kind = 0;
+    if (BS::MIXED) {
+        const int kt0 = __ldg(&f.d->hot.kt0), kt01 = __ldg(&f.d->hot.kt01);
+        if (local >= kt01) {
+            f.kind = 2;
+            f.x0 = __ldg(&f.d->hot.kx2);
+            f.y0 = (local - kt01) * kind_th(2);
+            return f;
+        }
+        if (local >= kt0) {
+            f.kind = 1;
+            f.x0 = __ldg(&f.d->hot.kx1);
+            f.y0 = (local - kt0) * kind_th(1);
+            return f;
+        }
+    }
     const int ty = local / tiles_x;
-    f.x0 = (local - ty * tiles_x) * TW;
+    f.x0 = (local - ty * tiles_x) * BS::TW;
     f.y0 = ty * BS::TH;
     return f;
 }
@@ -148,15 +194,17 @@ template <int TW, int NPT, int NW>
 __device__ __forceinline__ void batch_issue(float* smem, const TileFetch& f, int s, uint64_t* full) {
     using BS = BatchShape<TW, NPT, NW>;
     float* st = smem + s * BS::STAGE;
-    // record: origin, replica time, bit 0 live, bit 1 sampled at this time
+    // record: origin, replica time, and (0 for a tile not stepped) bit 0 set,
+    // bit 1 sampled at this time, bits 2-3 the tile kind, bits 4.. the replica
     *reinterpret_cast<int4*>(st + 9 * BS::SPLANE + BS::HOT) =
-        make_int4(f.x0, f.y0, f.tr, (f.live ? 1 : 0) | (f.live && f.sampled ? 2 : 0));
+        make_int4(f.x0, f.y0, f.tr, f.live ? 1 | (f.sampled ? 2 : 0) | (f.kind << 2) | (f.rep << 4) : 0);
     if (!f.live) {
         mbar_arrive(&full[s]);
         return;
     }
-    mbar_arrive_expect_tx(&full[s], 9u * BS::TH * BS::BW * sizeof(float) + sizeof(ReplicaHot));
-    const CUtensorMap* map = &f.d->map[f.tr & 1];
+    const uint32_t box = BS::MIXED ? (uint32_t)(kind_th(f.kind) * kind_bw(f.kind)) : (uint32_t)(BS::TH * BS::BW);
+    mbar_arrive_expect_tx(&full[s], 9u * box * sizeof(float) + sizeof(ReplicaHot));
+    const CUtensorMap* map = &f.d->map[2 * f.kind + (f.tr & 1)];
 #pragma unroll
     for (int i = 0; i < 9; ++i)
         tma_load_2d(st + i * BS::SPLANE, map, f.x0 + kXO - 4, i * (f.Ly + 2) + f.y0 + 1 - cvy(i),
@@ -201,7 +249,10 @@ batch_step_kernel(const BatchArgs a) {
     double* run_cm = reinterpret_cast<double*>(empty + S + 2);
     double** run_acc = reinterpret_cast<double**>(run_cm + kRunSlots * 256);
     double* run_s = reinterpret_cast<double*>(run_acc + kRunSlots);
-    __half* gram = reinterpret_cast<__half*>(run_s + kRunSlots);
+    // each consumer warp's current run: its replica's sums and scale
+    double** cur_acc = reinterpret_cast<double**>(run_s + kRunSlots);
+    double* cur_s = reinterpret_cast<double*>(cur_acc + NW);
+    __half* gram = reinterpret_cast<__half*>(cur_s + NW);
 
     const int warp = threadIdx.x >> 5, lane_id = threadIdx.x & 31;
     const unsigned step = __ldcg(&a.ctl->step);
@@ -357,17 +408,15 @@ batch_step_kernel(const BatchArgs a) {
 #pragma unroll
         for (int q = 0; q < 8; ++q) gc[q] = 0.f;
     }
-    int run = -1, gtiles = 0;
-    const double* run_key = nullptr;
-    double run_scale = 0.0;
-    double* run_glob = nullptr;
-    const GramLane gl(kTensor ? smem_u32(gram + (c >> 5) * kGramWarpHalves) : 0u);
+    int run = -1, gtiles = 0, run_rep = -1;
+    const int wc = c >> 5;
+    const GramLane gl(kTensor ? smem_u32(gram + wc * kGramWarpHalves) : 0u);
     auto gram_out = [&]() {
         if (run < 0) return;
         if (run < kRunSlots)
             gram_flush(reinterpret_cast<float(&)[8]>(gc), run_cm + run * 256);
         else
-            gram_flush_global(reinterpret_cast<float(&)[8]>(gc), run_glob, run_scale);
+            gram_flush_global(reinterpret_cast<float(&)[8]>(gc), cur_acc[wc], cur_s[wc]);
         gtiles = 0;
     };
     for (int k = 0; k < ntile; ++k) {
@@ -383,48 +432,66 @@ batch_step_kernel(const BatchArgs a) {
             continue;
         }
         const ReplicaHot& hs = *reinterpret_cast<const ReplicaHot*>(stg + 9 * BS::SPLANE);
-        Geometry geo;
-        geo.Lx = hs.Lx;
-        geo.Ly = hs.Ly;
-        geo.pitch = hs.pitch;
-        geo.plane = hs.plane;
         const uint32_t tr = (uint32_t)info.z;
-        float* dst = hs.buf[(tr + 1u) & 1u];
-        DevError* err = hs.err;
-        const int y = info.y + ty;
-        const float* st = stg + ty * BW + 4 + r;
+        const int rep = info.w >> 4;
         if (NPT == 2) {
+            const int Lx = hs.Lx, Ly = hs.Ly;
+            // this thread's node pair: A at (ax, ay) of the tile, B at
+            // (ax + dx, ay + dy); the tile is tw x th nodes in boxes bw wide
+            int tw = BS::TW, th = BS::TH, bw = BW, ax = r, ay = ty, dx = BS::TW / 2, dy = 0;
+            if constexpr (BS::MIXED) {
+                // kind 0: two warps a row, each 64 columns wide; kind 1: a
+                // warp a row; kind 2: a warp two rows. B lies 32 columns
+                // right of A (kinds 0 and 1) or under it (kind 2).
+                const int kind = (info.w >> 2) & 3, w = c >> 5;
+                const bool vert = kind == 2;
+                tw = kind_tw(kind);
+                th = kind_th(kind);
+                bw = tw + 8;
+                ay = (w << 1) >> (2 - kind);
+                ax = lane_id + (kind == 0 ? (w & 1) << 6 : 0);
+                dx = vert ? 0 : 32;
+                dy = vert ? 1 : 0;
+            }
+            const float* sa = stg + ay * bw + ax + 4;   // node A's cell in plane 0
+            const int sb = dy * bw + dx;                // node B's offset from A
             auto load = [&](f2* g) {
 #pragma unroll
                 for (int i = 0; i < 9; ++i) {
-                    const float* p = st + i * BS::SPLANE - cvx(i);
-                    g[i] = f2(p[0], p[TW / 2]);
+                    const float* p = sa + i * BS::SPLANE - cvx(i);
+                    g[i] = f2(p[0], p[sb]);
                 }
             };
             f2 g[9];
             load(g);
-            const int xA = info.x + r, xB = xA + TW / 2;
-            const bool inA = xA < geo.Lx && y < geo.Ly, inB = xB < geo.Lx && y < geo.Ly;
-            const uint32_t nodeA = (uint32_t)xA + (uint32_t)geo.Lx * (uint32_t)y;
+            const int xA = info.x + ax, yA = info.y + ay, xB = xA + dx, yB = yA + dy;
+            const bool inA = xA < Lx && yA < Ly, inB = xB < Lx && yB < Ly;
+            const uint32_t nodeA = (uint32_t)xA + (uint32_t)Lx * (uint32_t)yA;
+            const uint32_t nodeB = (uint32_t)xB + (uint32_t)Lx * (uint32_t)yB;
             const bool smp = kTensor && (info.w & 2);
-            if (smp && hs.acc != run_key) {   // a new run of sampled tiles
+            if (smp && rep != run_rep) {   // a new run of sampled tiles
                 gram_out();
                 ++run;
-                run_key = hs.acc;
-                run_glob = hs.acc;
-                run_scale = (double)hs.gram_s;
-                if (run < kRunSlots && lane_id == 0) {
-                    run_acc[run] = hs.acc;
-                    run_s[run] = run_scale;
+                run_rep = rep;
+                if (lane_id == 0) {
+                    const double sc = (double)hs.gram_s;
+                    cur_acc[wc] = hs.acc;
+                    cur_s[wc] = sc;
+                    if (run < kRunSlots) {
+                        run_acc[run] = hs.acc;
+                        run_s[run] = sc;
+                    }
                 }
+                __syncwarp();
             }
+            // every node of the tile lies in the replica (a uniform test)
+            const bool whole = info.x + tw <= Lx && info.y + th <= Ly;
             // stage the nodes when the collision reads them a second time
             auto stage = [&](const f2* gs) {
-                const float inv = hs.gram_inv;
                 f2 hv[9];
 #pragma unroll
-                for (int i = 0; i < 9; ++i) hv[i] = mad(gs[i], f2(inv), f2(-hs.ref[i] * inv));
-                if (!(inA && inB)) {
+                for (int i = 0; i < 9; ++i) hv[i] = mad(gs[i], f2(hs.sinv), f2(hs.snref[i]));
+                if (!whole) {
 #pragma unroll
                     for (int i = 0; i < 9; ++i) hv[i] = f2(inA ? hv[i].v.x : 0.f, inB ? hv[i].v.y : 0.f);
                 }
@@ -436,32 +503,50 @@ batch_step_kernel(const BatchArgs a) {
             };
             f2 f[9];
             const uint32_t stt = collide_basis<f2, BASIS>(
-                g, PairNoise{hs.cc.key, nodeA, nodeA + TW / 2, tr}, refetch,
-                a.lut, hs.cc, f);
+                g, PairNoise{hs.cc.key, nodeA, nodeB, tr}, refetch, a.lut, hs.pc, f);
             if (kTensor && smp) {
                 gram_mma(gl, reinterpret_cast<float(&)[8]>(gc));
                 if (++gtiles == kGramFlushTiles) gram_out();
             }
+            // what the stores need, read before the stage is released
+            Geometry geo;
+            geo.Lx = Lx;
+            geo.Ly = Ly;
+            geo.pitch = hs.pitch;
+            geo.plane = hs.plane;
+            float* dst = hs.buf[(tr + 1u) & 1u];
             warp_arrive(&empty[s], lane_id);
             if (stt) {
+                DevError* err = a.desc[rep].hot.err;
                 if (inA && (stt & 0xFF)) record_error(err, (int)(stt & 0xFF), nodeA, tr);
-                if (inB && (stt >> 8)) record_error(err, (int)(stt >> 8), nodeA + TW / 2, tr);
+                if (inB && (stt >> 8)) record_error(err, (int)(stt >> 8), nodeB, tr);
             }
             // node pairs away from the lattice edge (every pair of an inner
-            // tile, most of an edge tile's) store without ghost copies
-            const bool inner = info.x > 0 && info.y > 0 && info.x + TW < geo.Lx && info.y + TH < geo.Ly;
-            if (inner || (inA && inB && xA > 0 && xB < geo.Lx - 1 && y > 0 && y < geo.Ly - 1)) {
-                float* pa = dst + at(geo, 0, xA, y);
+            // tile, most of an edge tile's) store without ghost copies; A
+            // never lies right of or below B
+            const bool inner = info.x > 0 && info.y > 0 && info.x + tw < geo.Lx && info.y + th < geo.Ly;
+            float* pa = dst + at(geo, 0, xA, yA);
+            const long long gb = dy * geo.pitch + dx;   // B's offset from A
+            if (inner) {
 #pragma unroll
                 for (int i = 0; i < 9; ++i) {
                     pa[i * geo.plane] = f[i].v.x;
-                    pa[i * geo.plane + TW / 2] = f[i].v.y;
+                    pa[i * geo.plane + gb] = f[i].v.y;
                 }
             } else {
-                if (inA) store_lane(dst, geo, xA, y, f, 0);
-                if (inB) store_lane(dst, geo, xB, y, f, 1);
+                if (inA) store_lane_ghosts(pa, geo, xA, yA, f, 0);
+                if (inB) store_lane_ghosts(pa + gb, geo, xB, yB, f, 1);
             }
         } else {
+            Geometry geo;
+            geo.Lx = hs.Lx;
+            geo.Ly = hs.Ly;
+            geo.pitch = hs.pitch;
+            geo.plane = hs.plane;
+            float* dst = hs.buf[(tr + 1u) & 1u];
+            DevError* err = hs.err;
+            const int y = info.y + ty;
+            const float* st = stg + ty * BW + 4 + r;
             auto load = [&](float* g) {
 #pragma unroll
                 for (int i = 0; i < 9; ++i) g[i] = st[i * BS::SPLANE - cvx(i)];
@@ -503,13 +588,15 @@ batch_step_kernel(const BatchArgs a) {
 // Tile shapes the batch can run; index = FLB_TILE_* of flb.h. Shapes with 12
 // consumer warps take their correlation sums on the tensor cores.
 struct BatchVariant {
-    int tw, npt, nw;
-    __host__ __device__ constexpr int th() const { return nw * 32 * npt / tw; }
+    int tw, npt, nw;   // tw = kMixedTW: the mixed tiling
+    __host__ __device__ constexpr bool mixed() const { return tw == kMixedTW; }
+    __host__ __device__ constexpr int th() const { return mixed() ? kind_th(0) : nw * 32 * npt / tw; }
     __host__ __device__ constexpr bool tensor() const { return nw > kBatchNW; }
 };
-constexpr BatchVariant kBatchVariants[5] = {{128, 2, kBatchNW}, {64, 2, kBatchNW}, {128, 1, kBatchNW},
-                                            {128, 2, kBatchNWTensor}, {64, 2, kBatchNWTensor}};
-constexpr int kNumBatchVariants = 5;
+constexpr BatchVariant kBatchVariants[6] = {{128, 2, kBatchNW},       {64, 2, kBatchNW},
+                                            {128, 1, kBatchNW},       {128, 2, kBatchNWTensor},
+                                            {64, 2, kBatchNWTensor},  {kMixedTW, 2, kBatchNWTensor}};
+constexpr int kNumBatchVariants = 6;
 
 // Kernel of (variant, basis, sampling), instantiated in flb_batch_k<basis>.cu.
 const void* batch_kernel_std(int variant, bool sample);

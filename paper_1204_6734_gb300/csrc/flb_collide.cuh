@@ -75,6 +75,15 @@ __device__ __forceinline__ void node_normals(const NoiseKey& key, uint32_t nodeA
 constexpr float kLn2x2 = 1.3862943611198906f;
 constexpr float kAngle = (float)(kTwoPi * 0x1p-21);   // 2 pi 2^-21, the angle of one step of k
 
+// -omega_a and -amp_a as operands of type V, from the constants in either form
+// (CollideConst: scalars broadcast to the lanes; CollidePairs: packed pairs).
+template <class V, class T>
+__device__ __forceinline__ V nomega_of(const CollideConst<T>& cc, int a) { return V(cc.nomega[a]); }
+template <class V>
+__device__ __forceinline__ V nomega_of(const CollidePairs& cc, int a) { return V(cc.nomega[a]); }
+__device__ __forceinline__ f2 namp_of(const CollideConst<float>& cc, int a) { return f2(-cc.amp[a]); }
+__device__ __forceinline__ f2 namp_of(const CollidePairs& cc, int a) { return f2(cc.namp[a]); }
+
 struct NodeNoise {
     const NoiseKey& key;
     uint32_t node, step;
@@ -82,7 +91,7 @@ struct NodeNoise {
     __device__ __forceinline__ void operator()(T n[6]) const {
         node_normals(key, node, step, n);
     }
-    __device__ __forceinline__ void scaled(float rho, const float (&amp)[6], float n[6]) const {
+    __device__ __forceinline__ void scaled(float rho, const CollideConst<float>& cc, float n[6]) const {
         uint32_t k[6];
         node_fields(key, node, step, k);
         const float nr = rho * -kLn2x2;
@@ -94,8 +103,8 @@ struct NodeNoise {
             float s, c;
             sincos_ftz(t, &s, &c);
             // cos(t + pi) = -cos t, sin(t + pi) = -sin t
-            n[2 * p] = (r * -amp[2 * p]) * c;
-            n[2 * p + 1] = (r * -amp[2 * p + 1]) * s;
+            n[2 * p] = (r * -cc.amp[2 * p]) * c;
+            n[2 * p + 1] = (r * -cc.amp[2 * p + 1]) * s;
         }
     }
 };
@@ -103,7 +112,8 @@ struct NodeNoise {
 struct PairNoise {
     const NoiseKey& key;
     uint32_t nodeA, nodeB, step;
-    __device__ __forceinline__ void scaled(f2 rho, const float (&amp)[6], f2 n[6]) const {
+    template <class CC>
+    __device__ __forceinline__ void scaled(f2 rho, const CC& cc, f2 n[6]) const {
         uint32_t ka[6], kb[6];
         node_fields(key, nodeA, step, ka);
         node_fields(key, nodeB, step, kb);
@@ -117,20 +127,18 @@ struct PairNoise {
             float sa, ca, sb, cb;
             sincos_ftz(t.v.x, &sa, &ca);
             sincos_ftz(t.v.y, &sb, &cb);
-            n[2 * p] = (r * f2(-amp[2 * p])) * f2(ca, cb);
-            n[2 * p + 1] = (r * f2(-amp[2 * p + 1])) * f2(sa, sb);
+            n[2 * p] = (r * namp_of(cc, 2 * p)) * f2(ca, cb);
+            n[2 * p + 1] = (r * namp_of(cc, 2 * p + 1)) * f2(sa, sb);
         }
     }
 };
 
 // xi^a N^a, a = 3..8: FP32 folds the amplitudes into the draw (NodeNoise,
 // PairNoise); FP64 scales unit normals (the arithmetic of the oracle's order).
-template <class V, class Noise>
-__device__ __forceinline__ void noise_increments(Noise& noise, V rho,
-                                                 const CollideConst<typename Elem<V>::type>& cc,
-                                                 V xi[6]) {
+template <class V, class Noise, class CC>
+__device__ __forceinline__ void noise_increments(Noise& noise, V rho, const CC& cc, V xi[6]) {
     if constexpr (!std::is_same<V, double>::value) {
-        noise.scaled(rho, cc.amp, xi);
+        noise.scaled(rho, cc, xi);
     } else {
         V N[6];
         noise(N);
@@ -341,11 +349,10 @@ __device__ __forceinline__ void fnorm_factor(V ux, V uy, V uxx, V uyy, V uxy, V 
 //    computed here rather than kept in registers across the factorisation);
 //  * f* = g + W (.) P^T D, W_i = f_i^0(1, u) (Eq. d2q9f0). refetch(gg)
 //    supplies g again. Returns the status (invsum infinite: no basis at u).
-template <class V, class Noise, class Refetch>
+template <class V, class Noise, class Refetch, class CC>
 __device__ __forceinline__ uint32_t fnorm_update(const V (&M)[6], const V (&Ln)[6][6], const V (&inv)[6],
                                                  V rho, V ux, V uy, Noise& noise, Refetch& refetch,
-                                                 const CollideConst<typename Elem<V>::type>& cc,
-                                                 V invsum, V f[9]) {
+                                                 const CC& cc, V invsum, V f[9]) {
     using S = typename Elem<V>::type;
     const V uxx = ux * ux, uyy = uy * uy, uxy = ux * uy;
     const V usq = uxx + uyy;
@@ -365,7 +372,7 @@ __device__ __forceinline__ uint32_t fnorm_update(const V (&M)[6], const V (&Ln)[
     V z[6];
     noise_increments(noise, rho, cc, z);
 #pragma unroll
-    for (int a = 0; a < 6; ++a) z[a] = mad(V(cc.nomega[a]), y[a], z[a]);
+    for (int a = 0; a < 6; ++a) z[a] = mad(nomega_of<V>(cc, a), y[a], z[a]);
     // D_N = L'^{-T} z
 #pragma unroll
     for (int j = 5; j >= 0; --j) {
@@ -428,10 +435,8 @@ __device__ __forceinline__ uint32_t fnorm_update(const V (&M)[6], const V (&Ln)[
 // One collision. g: pre-collision populations; noise(N) fills the normals
 // N^3..N^8 (called once, after the basis is built, to keep registers free);
 // f: output.
-template <class V, int BASIS, class Noise>
-__device__ __forceinline__ uint32_t collide(const V g[9], Noise noise,
-                                            const CollideConst<typename Elem<V>::type>& cc,
-                                            V f[9]) {
+template <class V, int BASIS, class Noise, class CC>
+__device__ __forceinline__ uint32_t collide(const V g[9], Noise noise, const CC& cc, V f[9]) {
     return collide<V, BASIS>(g, noise, [&](V* gg) {
 #pragma unroll
         for (int i = 0; i < 9; ++i) gg[i] = g[i];
@@ -441,10 +446,9 @@ __device__ __forceinline__ uint32_t collide(const V g[9], Noise noise,
 // As above; refetch(gg) supplies g again for the final f = g + W h, so the
 // caller may drop g from registers in between (the pipelined kernel re-reads
 // it from shared memory).
-template <class V, int BASIS, class Noise, class Refetch>
+template <class V, int BASIS, class Noise, class Refetch, class CC>
 __device__ __forceinline__ uint32_t collide(const V g[9], Noise noise, Refetch refetch,
-                                            const CollideConst<typename Elem<V>::type>& cc,
-                                            V f[9]) {
+                                            const CC& cc, V f[9]) {
     using S = typename Elem<V>::type;
     // density, momentum, velocity
     const V s13 = g[1] + g[3], s24 = g[2] + g[4];
@@ -477,7 +481,7 @@ __device__ __forceinline__ uint32_t collide(const V g[9], Noise noise, Refetch r
         V Dn[6];
         noise_increments(noise, rho, cc, Dn);
 #pragma unroll
-        for (int a = 0; a < 6; ++a) Dn[a] = mad(V(cc.nomega[a]), M[a], Dn[a]);
+        for (int a = 0; a < 6; ++a) Dn[a] = mad(nomega_of<V>(cc, a), M[a], Dn[a]);
         V h[9];
         hermite_back<V, false>(V(S(0)), V(S(0)), V(S(0)), Dn, h);
         V gg[9];
@@ -528,7 +532,7 @@ __device__ __forceinline__ uint32_t collide(const V g[9], Noise noise, Refetch r
     V z[6];
     noise_increments(noise, rho, cc, z);
 #pragma unroll
-    for (int a = 0; a < 6; ++a) z[a] = mad(V(cc.nomega[a]), y[a], z[a]);
+    for (int a = 0; a < 6; ++a) z[a] = mad(nomega_of<V>(cc, a), y[a], z[a]);
     // D_N = L'^{-T} z
 #pragma unroll
     for (int j = 5; j >= 0; --j) {
@@ -635,10 +639,9 @@ __device__ __forceinline__ void lut_load_entry(const double* p, double (&r)[kLut
     }
 }
 
-template <class V, class Noise, class Refetch>
+template <class V, class Noise, class Refetch, class CC>
 __device__ __forceinline__ uint32_t collide_lut(const V g[9], Noise noise, Refetch refetch,
-                                                const typename Elem<V>::type* lut,
-                                                const CollideConst<typename Elem<V>::type>& cc,
+                                                const typename Elem<V>::type* lut, const CC& cc,
                                                 V f[9]) {
     using S = typename Elem<V>::type;
     constexpr int NL = Lanes<V>::n;
@@ -679,10 +682,9 @@ __device__ __forceinline__ uint32_t collide_lut(const V g[9], Noise noise, Refet
 
 // The collision of basis BASIS: 0 Hermite norm, 1 f-norm, 2 look-up-table
 // f-norm (lut: the velocity table, unused otherwise).
-template <class V, int BASIS, class Noise, class Refetch>
+template <class V, int BASIS, class Noise, class Refetch, class CC>
 __device__ __forceinline__ uint32_t collide_basis(const V g[9], Noise noise, Refetch refetch,
-                                                  const typename Elem<V>::type* lut,
-                                                  const CollideConst<typename Elem<V>::type>& cc,
+                                                  const typename Elem<V>::type* lut, const CC& cc,
                                                   V f[9]) {
     if constexpr (BASIS == 2)
         return collide_lut<V>(g, noise, refetch, lut, cc, f);

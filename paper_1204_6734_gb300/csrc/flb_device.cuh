@@ -125,6 +125,15 @@ struct CollideConst {
     NoiseKey key;
 };
 
+// The FP32 relaxation and noise constants as packed pairs {c, c}: a kernel that
+// reads its constants from shared memory then loads each FP32x2 operand with one
+// 64-bit load instead of a load and two moves. The Philox key stays in
+// CollideConst.
+struct CollidePairs {
+    float2 nomega[6];   // -omega_a
+    float2 namp[6];     // -sqrt(kT omega_a (2 - omega_a))
+};
+
 __host__ __device__ inline NoiseKey make_noise_key(uint64_t seed, uint32_t replica) {
     NoiseKey k;
     uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);

@@ -26,8 +26,8 @@ BASIS = {"standard": 0, "local": 1, "lut": 2}
 OPT_KERNEL, OPT_PIPELINE_WARPS, OPT_PIPELINE_SAMPLING = 0, 1, 2
 KERNEL = {"auto": 0, "generic": 1, "pipelined": 2}
 PRECISION = {"fp64": 0, "fp32": 1, "fp16dev": 2}
-TILE = {"128x4": 0, "64x8": 1, "128x2": 2, "128x6": 3, "64x12": 4}   # tile shapes of the batched kernel
-TILE_COUNT = 5
+TILE = {"128x4": 0, "64x8": 1, "128x2": 2, "128x6": 3, "64x12": 4, "mixed": 5}   # tile shapes of the batched kernel
+TILE_COUNT = 6
 
 
 class FlbError(RuntimeError):

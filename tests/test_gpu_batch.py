@@ -37,10 +37,12 @@ def _lib():
     flb.load()
 
 
-def uneven(basis, n=7, seed=11):
+def uneven(basis, n=8, seed=11):
     """Small replicas of ragged sizes (partial tiles in x and y, one-node
-    lattices, more than one tile column) with their own u0, kT, rates, seeds."""
-    shapes = [(37, 29), (64, 64), (130, 17), (1, 1), (200, 131), (5, 3), (129, 9)][:n]
+    lattices, more than one tile column; for the mixed tiling, every kind of
+    column band: 32, 64, 64 + 32 and a 128-wide last column) with their own u0,
+    kT, rates, seeds."""
+    shapes = [(37, 29), (64, 64), (130, 17), (1, 1), (200, 131), (5, 3), (129, 9), (110, 7)][:n]
     g = np.random.Generator(np.random.PCG64(seed))
     out = []
     for r, (Lx, Ly) in enumerate(shapes):
