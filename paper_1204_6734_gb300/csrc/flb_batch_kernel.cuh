@@ -521,9 +521,8 @@ batch_step_kernel(const BatchArgs a) {
                 if (inA && (stt & 0xFF)) record_error(err, (int)(stt & 0xFF), nodeA, tr);
                 if (inB && (stt >> 8)) record_error(err, (int)(stt >> 8), nodeB, tr);
             }
-            // node pairs away from the lattice edge (every pair of an inner
-            // tile, most of an edge tile's) store without ghost copies; A
-            // never lies right of or below B
+            // an inner tile stores without edge tests; on an edge tile each lane
+            // tests its node and adds the ghost copies it needs
             const bool inner = info.x > 0 && info.y > 0 && info.x + tw < geo.Lx && info.y + th < geo.Ly;
             float* pa = dst + at(geo, 0, xA, yA);
             const long long gb = dy * geo.pitch + dx;   // B's offset from A

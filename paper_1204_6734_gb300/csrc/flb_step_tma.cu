@@ -389,19 +389,19 @@ step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
             if (inA && (stt & 0xFF)) record_error(a.err, (int)(stt & 0xFF), nodeA, a.step);
             if (inB && (stt >> 8)) record_error(a.err, (int)(stt >> 8), nodeA + 64u, a.step);
         }
-        // node pairs away from the lattice edge (every pair of an inner tile,
-        // most of an edge tile's) store without ghost copies
+        // an inner tile stores without edge tests; on an edge tile each lane
+        // tests its node and adds the ghost copies it needs
         const bool inner = x0 > 0 && y0 > 0 && x0 + kTW < Lx && y0 + TH < Ly;
-        if (inner || (inA && inB && xA > 0 && xB < Lx - 1 && y > 0 && y < Ly - 1)) {
-            float* pa = a.dst + at(a.geo, 0, xA, y);
+        float* pa = a.dst + at(a.geo, 0, xA, y);
+        if (inner) {
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 pa[i * a.geo.plane] = f[i].v.x;
                 pa[i * a.geo.plane + 64] = f[i].v.y;
             }
         } else {
-            if (inA) store_lane(a.dst, a.geo, xA, y, f, 0);
-            if (inB) store_lane(a.dst, a.geo, xB, y, f, 1);
+            if (inA) store_lane_ghosts(pa, a.geo, xA, y, f, 0);
+            if (inB) store_lane_ghosts(pa + 64, a.geo, xB, y, f, 1);
         }
         if (producer) {
             if (!kEmbed)
