@@ -66,15 +66,36 @@ __host__ __device__ __forceinline__ void store_pop(T* dst, const Geometry& g, in
     }
 }
 
+// Store the populations v[i] of interior node (x, y) at p[i plane] (p: the
+// node's cell in plane 0) with the ghost copies of store_pop: population i
+// that leaves through the left (right) edge is also pulled by its periodic
+// image from column x + Lx (x - Lx), one that leaves through the bottom (top)
+// edge from row y + Ly (y - Ly), both at a corner. The edge tests are per
+// thread and the copies predicated, so nodes away from the edge pay only the
+// tests.
 template <class T>
-__host__ __device__ __forceinline__ void store_node(T* dst, const Geometry& g, int x, int y, const T f[9]) {
-    if (x > 0 && y > 0 && x < g.Lx - 1 && y < g.Ly - 1) {
+__device__ __forceinline__ void store_node_ghosts(T* p, const Geometry& g, int x, int y, const T v[9]) {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) dst[at(g, i, x, y)] = f[i];
-    } else {
+    for (int i = 0; i < 9; ++i) p[i * g.plane] = v[i];
+    const bool eL = x == 0, eR = x == g.Lx - 1, eB = y == 0, eT = y == g.Ly - 1;
+    if (!(eL || eR || eB || eT)) return;
+    const long long sx = g.Lx, sy = (long long)g.Ly * g.pitch;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) store_pop(dst, g, i, x, y, f[i]);
+    for (int i = 1; i < 9; ++i) {
+        const bool lx = cvx(i) < 0 ? eL : (cvx(i) > 0 ? eR : false);
+        const bool ly = cvy(i) < 0 ? eB : (cvy(i) > 0 ? eT : false);
+        if (lx || ly) {
+            long long o = i * g.plane;
+            if (lx) o += cvx(i) < 0 ? sx : -sx;
+            if (ly) o += cvy(i) < 0 ? sy : -sy;
+            p[o] = v[i];
+        }
     }
+}
+
+template <class T>
+__device__ __forceinline__ void store_node(T* dst, const Geometry& g, int x, int y, const T f[9]) {
+    store_node_ghosts(dst + at(g, 0, x, y), g, x, y, f);
 }
 
 }  // namespace flb

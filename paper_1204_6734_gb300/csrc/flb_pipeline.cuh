@@ -36,38 +36,14 @@ struct TileShape {
     }
 };
 
-__device__ __forceinline__ void store_lane(float* dst, const Geometry& geo, int x, int y,
-                                           const f2 f[9], int k) {
+// Store lane k of a node pair, interior node (x, y) whose cell in plane 0 is
+// pa, with the ghost copies it needs (store_node_ghosts).
+__device__ __forceinline__ void store_lane_ghosts(float* pa, const Geometry& geo, int x, int y,
+                                                  const f2 f[9], int k) {
     float v[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) v[i] = lane(f[i], k);
-    store_node(dst, geo, x, y, v);
-}
-
-// Store lane k of a node pair at interior node (x, y), whose population i
-// goes to pa[i plane], with the ghost copies of store_pop: population i that
-// leaves through the left (right) edge is also pulled by its periodic image
-// from column x + Lx (x - Lx), one that leaves through the bottom (top) edge
-// from row y + Ly (y - Ly), both for a corner. The edge tests are per lane and
-// the copies predicated, so lanes away from the edge only pay the tests.
-__device__ __forceinline__ void store_lane_ghosts(float* pa, const Geometry& geo, int x, int y,
-                                                  const f2 f[9], int k) {
-#pragma unroll
-    for (int i = 0; i < 9; ++i) pa[i * geo.plane] = lane(f[i], k);
-    const bool eL = x == 0, eR = x == geo.Lx - 1, eB = y == 0, eT = y == geo.Ly - 1;
-    if (!(eL || eR || eB || eT)) return;
-    const long long sx = geo.Lx, sy = (long long)geo.Ly * geo.pitch;
-#pragma unroll
-    for (int i = 1; i < 9; ++i) {
-        const bool lx = cvx(i) < 0 ? eL : (cvx(i) > 0 ? eR : false);
-        const bool ly = cvy(i) < 0 ? eB : (cvy(i) > 0 ? eT : false);
-        if (lx || ly) {
-            long long o = i * geo.plane;
-            if (lx) o += cvx(i) < 0 ? sx : -sx;
-            if (ly) o += cvy(i) < 0 ? sy : -sy;
-            pa[o] = lane(f[i], k);
-        }
-    }
+    store_node_ghosts(pa, geo, x, y, v);
 }
 
 // CTA reduction of per-thread correlation sums held by `group` threads (warps

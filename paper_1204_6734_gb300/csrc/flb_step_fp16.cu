@@ -237,16 +237,16 @@ step_fp16_kernel(const __grid_constant__ CUtensorMap map, const HArgs a,
             hA[i] = __float2half_rn(h.v.x);
             hB[i] = __float2half_rn(h.v.y);
         }
+        __half* pa = a.dst + at(a.geo, 0, xA, y);
         if (x0 > 0 && y - ty > 0 && x0 + kTW < Lx && y - ty + TH < Ly) {
-            __half* pa = a.dst + at(a.geo, 0, xA, y);
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 pa[i * a.geo.plane] = hA[i];
                 pa[i * a.geo.plane + 64] = hB[i];
             }
         } else {
-            if (inA) store_node(a.dst, a.geo, xA, y, hA);
-            if (inB) store_node(a.dst, a.geo, xB, y, hB);
+            if (inA) store_node_ghosts(pa, a.geo, xA, y, hA);
+            if (inB) store_node_ghosts(pa + 64, a.geo, xB, y, hB);
         }
     }
 }
