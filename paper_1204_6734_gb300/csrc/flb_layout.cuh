@@ -74,7 +74,7 @@ __host__ __device__ __forceinline__ void store_pop(T* dst, const Geometry& g, in
 // thread and the copies predicated, so nodes away from the edge pay only the
 // tests.
 template <class T>
-__device__ __forceinline__ void store_node_ghosts(T* p, const Geometry& g, int x, int y, const T v[9]) {
+__host__ __device__ __forceinline__ void store_node_ghosts(T* p, const Geometry& g, int x, int y, const T v[9]) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) p[i * g.plane] = v[i];
     const bool eL = x == 0, eR = x == g.Lx - 1, eB = y == 0, eT = y == g.Ly - 1;
@@ -94,7 +94,7 @@ __device__ __forceinline__ void store_node_ghosts(T* p, const Geometry& g, int x
 }
 
 template <class T>
-__device__ __forceinline__ void store_node(T* dst, const Geometry& g, int x, int y, const T f[9]) {
+__host__ __device__ __forceinline__ void store_node(T* dst, const Geometry& g, int x, int y, const T f[9]) {
     store_node_ghosts(dst + at(g, 0, x, y), g, x, y, f);
 }
 
