@@ -509,12 +509,16 @@ int lattice_create(const flb_params* p, void* dev_workspace, size_t workspace_by
         ce = cudaGetLastError();
     }
     if (ce == cudaSuccess && sync) ce = cudaStreamSynchronize(h->stream);
-    // sampling steps: the correlation sums on the tensor cores, 12 colliding
-    // warps (16 for the table f-norm: 51.6 against 50.3 GLUPS at 4096^2), where
-    // the parameters allow it; otherwise the sampler warps beside 8 colliding
-    // warps
+    // sampling steps: the correlation sums on the tensor cores, where the
+    // parameters allow it, with 16 colliding warps in the f-norm bases (4096^2:
+    // f-norm 54.8 against 54.6 GLUPS with 12, table f-norm 55.5 against 50.4)
+    // and 12 in the Hermite norm (77.9 against 71.4 with 16); otherwise the
+    // sampler warps beside 8 colliding warps. 16 warps make 128 x 8 tiles: a
+    // lattice with fewer than 8 of them per SM keeps 12 (more CTAs busy).
     const bool tensor = tensor_sampling_ok(p);
-    const int tensor_nw = p->basis == FLB_BASIS_LOCAL_LUT ? 16 : kTensorNW;
+    const bool tall = (long long)((p->Lx + 127) / 128) * ((p->Ly + 7) / 8) >= 8LL * (sms > 0 ? sms : 1);
+    const int fnorm_nw = tall ? 16 : kTensorNW;
+    const int tensor_nw = p->basis == FLB_BASIS_STANDARD ? kTensorNW : fnorm_nw;
     h->tma.sample_mode = tensor ? kPlanTensorSampling : 0;
     if (ce == cudaSuccess && p->basis == FLB_BASIS_LOCAL_LUT &&
         lut_tables(&h->lut32, &h->lut64) != FLB_OK)
@@ -522,10 +526,11 @@ int lattice_create(const flb_params* p, void* dev_workspace, size_t workspace_by
     h->tma_quiet.ready = false;
     if (ce == cudaSuccess && p->precision == FLB_FP32) {
         ce = tma_plan(&h->tma, h->buf[0], h->buf[1], h->geo, tensor ? tensor_nw : 0);
-        // steps without sampling: 12 colliding warps in the f-norm bases
-        // (measured 56.7 against 53.5 GLUPS at 4096^2 with 8), 8 in the
-        // Hermite norm (73-79 GLUPS)
-        const int quiet_nw = p->basis == FLB_BASIS_STANDARD ? 8 : 12;
+        // steps without sampling: 16 colliding warps in the f-norm bases
+        // (4096^2: f-norm 64.6 against 60.6 GLUPS with 12, table f-norm 63.8
+        // against 61.8; 12 on small lattices), 8 in the Hermite norm (85.0
+        // against 74.4 with 12)
+        const int quiet_nw = p->basis == FLB_BASIS_STANDARD ? 8 : fnorm_nw;
         if (ce == cudaSuccess && quiet_nw != h->tma.nw &&
             tma_plan(&h->tma_quiet, h->buf[0], h->buf[1], h->geo, quiet_nw) != cudaSuccess) {
             cudaGetLastError();
@@ -749,7 +754,13 @@ int flb_set_option(flb_lattice h, int32_t option, int32_t value) {
         if (value == kPlanTensorSampling && !tensor_sampling_ok(&h->p)) return FLB_ERR_ARG;
         TmaPlan plan = h->tma;
         plan.sample_mode = value;
-        const cudaError_t ce = tma_plan(&plan, h->buf[0], h->buf[1], h->geo, h->tma.nw);
+        cudaError_t ce = tma_plan(&plan, h->buf[0], h->buf[1], h->geo, h->tma.nw);
+        if (ce == cudaSuccess && plan.sample_mode != value && h->tma.nw > kTensorNW) {
+            // 16 colliding warps take only the tensor-core sums: the other
+            // modes run with 12
+            plan.sample_mode = value;
+            ce = tma_plan(&plan, h->buf[0], h->buf[1], h->geo, kTensorNW);
+        }
         if (ce != cudaSuccess || plan.sample_mode != value) {
             cudaGetLastError();
             return FLB_ERR_ARG;

@@ -128,10 +128,11 @@ __device__ __forceinline__ void add_sums(float (&v)[kSums], const f2 (&d)[9]) {
 // Sampling modes of the pipelined step.
 enum : int { kNoSampling = 0, kSamplerWarps = 1, kFusedSampling = 2, kTensorSampling = 3 };
 
-// With 16 colliding warps the producer is thread 0 of the first colliding warp
-// (a 17th warp would cap every thread at 96 registers: one sub-partition would
-// hold five warps); it refills the stage of the tile before the one it has just
-// finished, which every warp has normally released by then.
+// With 16 colliding warps there is no producer warp (a 17th warp would cap
+// every thread at 96 registers: one sub-partition would hold five warps):
+// thread 0 issues the first STAGES tiles, and after that the last warp to
+// release a stage refills it (a counter per stage in place of the empty
+// barrier), so no thread waits for the others.
 template <int NW, int MODE>
 constexpr bool embedded_producer() {
     return NW >= 16 && (MODE == kNoSampling || MODE == kTensorSampling);
@@ -176,10 +177,17 @@ step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
     __half* gram = reinterpret_cast<__half*>(red + TS::RED * kSums);
 
     const int warp = threadIdx.x >> 5, lane_id = threadIdx.x & 31;
+    constexpr bool kEmbed = embedded_producer<NW, MODE>();
+    static_assert(!kEmbed || (NW & (NW - 1)) == 0, "release counts wrap at 2^32");
+    // kEmbed: the empty barriers' words count the releases of each stage
+    uint32_t* released = reinterpret_cast<uint32_t*>(empty);
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], NW + (MODE == kSamplerWarps ? NX : 0));
+            if (kEmbed)
+                released[s] = 0u;
+            else
+                mbar_init(&empty[s], NW + (MODE == kSamplerWarps ? NX : 0));
         }
         fence_mbar_init();
     }
@@ -191,7 +199,6 @@ step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
 
     const int Lx = a.geo.Lx, Ly = a.geo.Ly;
 
-    constexpr bool kEmbed = embedded_producer<NW, MODE>();
     if ((MODE == kNoSampling || kTensor) && !kEmbed && warp == NW) {
         // ---------------- producer warp
         if (lane_id == 0) {
@@ -298,10 +305,12 @@ step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
     int gtiles = 0;
     const GramLane gblk(smem_u32(gram + warp * kGramWarpHalves));
     int k = 0, s = 0, n = 0;   // tile count, its stage and the stage's use
+    bool timed_out = false;
     TileWalk w(blockIdx.x, gridDim.x, a.tiles_x);
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++k, w.next()) {
         if (!mbar_wait(&full[s], n & 1)) {
             record_error(a.err, kStatusTimeout, -1, a.step);
+            timed_out = true;
             break;
         }
         const float* st = smem + s * TS::STAGE + ty * kBoxW + 4 + r;
@@ -384,7 +393,22 @@ step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
             }
         }
         // the stage is held until g was read the second time
-        warp_arrive(&empty[s], lane_id);
+        if constexpr (kEmbed) {
+            // the NW-th release of this use of the stage refills it with the
+            // CTA's tile kStages later (the counter is never reset: NW divides
+            // 2^32)
+            __syncwarp();
+            if (lane_id == 0 && ((atomicAdd(&released[s], 1u) + 1u) & (NW - 1)) == 0) {
+                const int tn = t + kStages * gridDim.x;
+                if (tn < a.ntiles) {
+                    fence_proxy_async_smem();
+                    const int nty = tn / a.tiles_x;
+                    issue_tile<NW>(smem, &map, a, tn - nty * a.tiles_x, nty, s, full);
+                }
+            }
+        } else {
+            warp_arrive(&empty[s], lane_id);
+        }
         if (stt) {
             if (inA && (stt & 0xFF)) record_error(a.err, (int)(stt & 0xFF), nodeA, a.step);
             if (inB && (stt >> 8)) record_error(a.err, (int)(stt >> 8), nodeA + 64u, a.step);
@@ -403,18 +427,18 @@ step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
             if (inA) store_lane_ghosts(pa, a.geo, xA, y, f, 0);
             if (inB) store_lane_ghosts(pa + 64, a.geo, xB, y, f, 1);
         }
-        if (producer) {
-            if (!kEmbed)
-                prod.refill(smem, &map, a, full, empty, s, n);
-            else if (k > 0)
-                prod.refill(smem, &map, a, full, empty, (k - 1) % kStages, (k - 1) / kStages);
-        }
+        if (producer && !kEmbed) prod.refill(smem, &map, a, full, empty, s, n);
         if (++s == kStages) {
             s = 0;
             ++n;
         }
     }
-    if (kEmbed && producer) prod.drain(a, full, k);
+    if (kEmbed && timed_out && lane_id == 0) {
+        // copies this warp did not consume may still be in flight: wait (with
+        // the bound of every wait) for the next kStages tiles
+        for (int j = k; j < k + kStages && blockIdx.x + j * gridDim.x < a.ntiles; ++j)
+            if (!mbar_wait(&full[j % kStages], (j / kStages) & 1)) break;
+    }
     if (kFused) {
         if (producer) prod.drain(a, full, k);
         publish_sums(reinterpret_cast<float(&)[kSums]>(v), 0, NW * 32, red, a);

@@ -221,16 +221,19 @@ def test_fp32_parity_lattice_full_run(parity_run, kernel):
 
 
 KERNELS = ["generic", "pipelined", "pipelined-samplers", "pipelined-fused", "pipelined16",
-           "pipelined8"]
+           "pipelined12", "pipelined8"]
 
 
 def lattice(p, kernel):
     """A lattice with the given FP32 step kernel: the generic one, or the
-    pipelined one -- by default the sums on the tensor cores and 12 colliding
-    warps; sampler warps with 8 colliding warps; sums fused into the colliding
-    warps; 16 or 8 colliding warps with the tensor-core sums."""
+    pipelined one -- by default the sums on the tensor cores, 16 colliding
+    warps in the f-norm bases and 12 in the Hermite norm; sampler warps with 8
+    colliding warps; sums fused into the colliding warps; 16, 12 or 8 colliding
+    warps with the tensor-core sums."""
     if kernel == "pipelined16":
         return flb.Lattice(p, kernel="pipelined", pipeline_warps=16)
+    if kernel == "pipelined12":
+        return flb.Lattice(p, kernel="pipelined", pipeline_warps=12)
     if kernel == "pipelined8":
         return flb.Lattice(p, kernel="pipelined", pipeline_warps=8)
     if kernel == "pipelined-samplers":
@@ -247,7 +250,7 @@ def test_warp_counts_give_identical_states(basis):
     p = inputs.LatticeParams(300, 37, 1.0, 0.15, 0.05, 1e-3, inputs.omega_groups(1.2, 0.8, 1.3), basis,
                              "fp32", seed=8)
     out = []
-    for kernel in ("pipelined", "pipelined8", "pipelined16", "pipelined-samplers"):
+    for kernel in ("pipelined", "pipelined8", "pipelined12", "pipelined16", "pipelined-samplers"):
         with lattice(p, kernel) as lat:
             lat.set_sampling(10, 3)
             lat.step(40)
