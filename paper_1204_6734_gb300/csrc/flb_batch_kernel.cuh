@@ -125,7 +125,8 @@ struct BatchShape {
     static constexpr int FIT = (MIXED ? 180000 : 163840) / (4 * STAGE);   // 160-176 KB of stages
     static constexpr int STAGES = FIT < 16 ? FIT : 16;
     static constexpr size_t GRAM =
-        TENSOR ? (size_t)NW * kGramWarpHalves * 2 + kRunSlots * 256 * 8 + kRunSlots * 16 + NW * 16 : 0;
+        TENSOR ? ((size_t)NW * kGramWarpHalves + kGramPadHalves) * 2 + kRunSlots * 256 * 8 + kRunSlots * 16 + NW * 16
+               : 0;
     static constexpr size_t smem_bytes() {
         return sizeof(float) * (size_t)STAGES * STAGE + 2 * STAGES * sizeof(uint64_t) + 16 + GRAM;
     }

@@ -4,13 +4,16 @@
 // The sums S1_i = sum_x d_i(x) and S2_ij = sum_x d_i(x) d_j(x) of the centred
 // pre-collision populations d = f - f^0(rho0, u0) (Eqs. dfdef, efif0) are one
 // Gram matrix: with H the 16 x K matrix whose rows 0..8 hold d_i / s over K
-// nodes, row 9 holds ones and rows 10..15 zeros, C = H H^T has
-// C_ij = S2_ij / s^2 and C_i9 = S1_i / s. A warp stages its 64 nodes (two per
-// thread) as FP16 (round to nearest) in a 16 x 64 shared-memory block
-// (gram_stage), loads the block back in the fragment layout of mma.m16n8k16
-// with ldmatrix and accumulates C in FP32 registers, 8 per thread (gram_mma);
-// every kGramFlushTiles tiles the FP32 partials are added to an FP64 16 x 16
-// matrix in shared memory (gram_flush).
+// nodes and row 9 holds ones, C = H H^T has C_ij = S2_ij / s^2 and
+// C_i9 = S1_i / s. A warp stages its 64 nodes (two per thread) as FP16 (round
+// to nearest) in rows 0..9 of a shared-memory block (gram_stage), loads 16
+// rows back in the fragment layout of mma.m16n8k16 with ldmatrix and
+// accumulates C in FP32 registers, 8 per thread (gram_mma); every
+// kGramFlushTiles tiles the FP32 partials of rows and columns 0..9 are added
+// to an FP64 16 x 16 matrix in shared memory (gram_flush). Rows 10..15 of H
+// only reach rows and columns 10..15 of C, which nothing reads: they are not
+// allocated, and ldmatrix reads whatever follows the block there (the next
+// warp's block, or the pad after the last one).
 //
 // The scale s (sqrt(kT rho0)) makes the thermal fluctuations of order one in
 // FP16, whose rounding (relative 2^-12, unbiased) enters the sums as noise
@@ -29,15 +32,15 @@
 namespace flb {
 
 constexpr int kGramRowHalves = 72;                       // 64 nodes + 8 halves: 144-byte rows
-constexpr int kGramWarpHalves = 16 * kGramRowHalves;     // one warp's block: 2304 bytes
+constexpr int kGramRows = 10;                            // rows of H a warp stages
+constexpr int kGramWarpHalves = kGramRows * kGramRowHalves;   // one warp's block: 1440 bytes
+constexpr int kGramPadHalves = (16 - kGramRows) * kGramRowHalves;   // read past the last block
 constexpr int kGramFlushTiles = 16;                      // FP32 partials of <= 1024 products
 
-// Constant rows of a warp's block: row 9 ones, rows 10..15 zeros.
+// The constant row of a warp's block: row 9, ones.
 __device__ __forceinline__ void gram_init(__half* blk) {
     const int lane = threadIdx.x & 31;
-    uint32_t* w = reinterpret_cast<uint32_t*>(blk);
-#pragma unroll
-    for (int r = 9; r < 16; ++r) w[r * (kGramRowHalves / 2) + lane] = r == 9 ? 0x3C003C00u : 0u;
+    reinterpret_cast<uint32_t*>(blk)[9 * (kGramRowHalves / 2) + lane] = 0x3C003C00u;
 }
 
 __device__ __forceinline__ void mma16816(float (&c)[8], int o, uint32_t a0, uint32_t a1,

@@ -28,7 +28,7 @@ struct TileShape {
     static constexpr int TH = NW / 2;                                  // rows per tile
     static constexpr int SPLANE = (TH * kBoxW + 31) / 32 * 32;         // floats per plane box
     static constexpr int STAGE = 9 * SPLANE;                           // floats per stage
-    static constexpr int STAGES = NW <= 8 ? 8 : (NW <= 12 ? 6 : (NW <= 14 ? 5 : 4));   // 157 / 176 / 173 / 157 KB
+    static constexpr int STAGES = NW <= 8 ? 8 : (NW <= 12 ? 6 : 5);   // 157 / 176 / 173 / 196 KB
     static constexpr int RED = NW > kSamplers ? NW : kSamplers;        // warps reducing
     static constexpr size_t smem_bytes() {
         return sizeof(float) * (size_t)STAGES * STAGE + 2 * STAGES * sizeof(uint64_t) +

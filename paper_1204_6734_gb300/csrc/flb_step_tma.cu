@@ -148,9 +148,11 @@ struct WarpCount {
 };
 
 // Shared memory of the tensor-sampling mode beyond the ring and the reduction
-// buffer: one Gram block per colliding warp.
+// buffer: one Gram block per colliding warp, and the pad the last one reads past.
 template <int NW>
-constexpr size_t gram_smem_bytes() { return (size_t)NW * kGramWarpHalves * sizeof(__half); }
+constexpr size_t gram_smem_bytes() {
+    return ((size_t)NW * kGramWarpHalves + kGramPadHalves) * sizeof(__half);
+}
 
 // Warp roles. kNoSampling: NW consumer warps + one producer warp.
 // kSamplerWarps: NW consumers + kSamplers sampler warps (sampler w reads rows
