@@ -33,6 +33,14 @@ const void* batch_kernel_std(int variant, bool sample) {
 
 namespace flb {
 
+// Every tile shape fits the 227 KB of shared memory a CTA may take.
+static_assert(BatchShape<128, 2>::smem_bytes() <= 227 * 1024 && BatchShape<64, 2>::smem_bytes() <= 227 * 1024 &&
+                  BatchShape<128, 1>::smem_bytes() <= 227 * 1024 &&
+                  BatchShape<128, 2, kBatchNWTensor>::smem_bytes() <= 227 * 1024 &&
+                  BatchShape<64, 2, kBatchNWTensor>::smem_bytes() <= 227 * 1024 &&
+                  BatchShape<kMixedTW, 2, kBatchNWTensor>::smem_bytes() <= 227 * 1024,
+              "batch shapes");
+
 size_t batch_smem_bytes(int variant) {
     switch (variant) {
         case 0: return BatchShape<128, 2>::smem_bytes();

@@ -154,6 +154,13 @@ constexpr size_t gram_smem_bytes() {
     return ((size_t)NW * kGramWarpHalves + kGramPadHalves) * sizeof(__half);
 }
 
+// Every shape fits the 227 KB of shared memory a CTA may take.
+constexpr size_t kMaxSmem = 227 * 1024;
+static_assert(TileShape<8>::smem_bytes() + gram_smem_bytes<8>() <= kMaxSmem, "8 warps");
+static_assert(TileShape<12>::smem_bytes() + gram_smem_bytes<12>() <= kMaxSmem, "12 warps");
+static_assert(TileShape<14>::smem_bytes() + gram_smem_bytes<14>() <= kMaxSmem, "14 warps");
+static_assert(TileShape<16>::smem_bytes() + gram_smem_bytes<16>() <= kMaxSmem, "16 warps");
+
 // Warp roles. kNoSampling: NW consumer warps + one producer warp.
 // kSamplerWarps: NW consumers + kSamplers sampler warps (sampler w reads rows
 // w, w + kSamplers, ... of each tile from the same stage and accumulates the
