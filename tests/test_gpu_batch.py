@@ -86,6 +86,40 @@ def test_batch_equals_lattices_alone(basis, tile):
         check_pop(tile, got[k], ref)
 
 
+@pytest.mark.parametrize("basis", BASES)
+def test_mixed_tiling_band_boundaries(basis):
+    """The mixed tiling at every width where its column bands change (the
+    remainder w of the width past the 128-wide columns: 0, 1-32 one 32-wide
+    band, 33-64 one 64-wide, 65-96 one of each, 97-127 one more 128-wide
+    column), with heights around the band kinds' 6, 12 and 24 rows, sampled
+    every step: populations bit-identical to the lattices stepped alone, sums
+    within the FP32 tolerances."""
+    widths = [1, 31, 32, 33, 63, 64, 65, 95, 96, 97, 127, 128, 129, 160, 193, 255, 256, 289]
+    heights = [5, 6, 7, 12, 13, 24, 25, 49]
+    g = np.random.Generator(np.random.PCG64(21))
+    ps = []
+    for r, Lx in enumerate(widths):
+        Ly = heights[r % len(heights)]
+        ps.append(inputs.LatticeParams(
+            Lx, Ly, 1.0, float(g.uniform(0, 0.2)), float(g.uniform(-0.05, 0.05)), 1e-4,
+            inputs.omega_groups(float(g.uniform(0.7, 1.6)), 0.9, 1.1), basis, "fp32",
+            seed=3000 + 7 * r, replica=r))
+    nsteps = 9
+    with flb.Batch(ps, tile="mixed") as b:
+        b.set_sampling(0, 1)
+        b.step(nsteps)
+        b.sync()
+        got = [b.populations(k) for k in range(len(ps))]
+        sums = [b.raw_sums(k) for k in range(len(ps))]
+    for k, p in enumerate(ps):
+        ref, ref_sums = alone(p, nsteps, warmup=0, every=1)
+        np.testing.assert_array_equal(got[k], ref)
+        n = sums[k][2]
+        assert n == ref_sums[2]
+        assert_sums_close(sums[k][0], sums[k][1], ref_sums[0], ref_sums[1], n, 1e-4,
+                          3e-6 * n * np.sqrt(p.kT), 1e-6 * n * p.kT)
+
+
 @pytest.mark.parametrize("tile", TILES)
 @pytest.mark.parametrize("basis", BASES)
 def test_batch_against_oracle_with_sampling(basis, tile):
