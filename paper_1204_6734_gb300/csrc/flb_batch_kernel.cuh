@@ -125,8 +125,7 @@ struct BatchShape {
     static constexpr int FIT = (MIXED ? 180000 : 163840) / (4 * STAGE);   // 160-176 KB of stages
     static constexpr int STAGES = FIT < 16 ? FIT : 16;
     static constexpr size_t GRAM =
-        TENSOR ? ((size_t)NW * kGramWarpHalves + kGramPadHalves) * 2 + kRunSlots * 256 * 8 + kRunSlots * 16 + NW * 16
-               : 0;
+        TENSOR ? (size_t)NW * kGramFullHalves * 2 + kRunSlots * 256 * 8 + kRunSlots * 16 + NW * 16 : 0;
     static constexpr size_t smem_bytes() {
         return sizeof(float) * (size_t)STAGES * STAGE + 2 * STAGES * sizeof(uint64_t) + 16 + GRAM;
     }
@@ -267,7 +266,7 @@ batch_step_kernel(const BatchArgs a) {
     }
     if (kTensor) {
         for (int k = threadIdx.x; k < kRunSlots * 256; k += blockDim.x) run_cm[k] = 0.0;
-        if (warp < NW) gram_init(gram + warp * kGramWarpHalves);
+        if (warp < NW) gram_init_full(gram + warp * kGramFullHalves);
     }
     __syncthreads();
 
@@ -411,7 +410,7 @@ batch_step_kernel(const BatchArgs a) {
     }
     int run = -1, gtiles = 0, run_rep = -1;
     const int wc = c >> 5;
-    const GramLane gl(kTensor ? smem_u32(gram + wc * kGramWarpHalves) : 0u);
+    const GramLane gl(kTensor ? smem_u32(gram + wc * kGramFullHalves) : 0u);
     auto gram_out = [&]() {
         if (run < 0) return;
         if (run < kRunSlots)
