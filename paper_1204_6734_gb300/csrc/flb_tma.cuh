@@ -55,19 +55,18 @@ __device__ __forceinline__ void warp_arrive(uint64_t* bar, int lane_id) {
         : "memory");
 }
 
-// try_wait with a suspend-time hint: a thread whose phase has not completed is
-// parked by the hardware (up to the hint, in ns) instead of spinning, so a
-// waiting warp takes no issue slots from the warps that compute.
-constexpr uint32_t kSuspendHintNs = 1000000;
-
+// try_wait: a thread whose phase has not completed is parked by the hardware
+// for up to its own time limit before the call returns false, so a waiting
+// warp takes few issue slots from the warps that compute. (A 1 ms suspend-time
+// hint measured 0.3-0.5 % slower in the pipelined steps.)
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendHintNs)
+        : "r"(smem_u32(bar)), "r"(parity)
         : "memory");
     return ok != 0;
 }
