@@ -473,6 +473,7 @@ batch_step_kernel(const BatchArgs a) {
                 gram_out();
                 ++run;
                 run_rep = rep;
+                __syncwarp();   // every lane has flushed with the previous run's record
                 if (lane_id == 0) {
                     const double sc = (double)hs.gram_s;
                     cur_acc[wc] = hs.acc;

@@ -285,6 +285,35 @@ def test_full_ensemble_sampled_replicas():
                           1e-6 * n * ps[k].kT)
 
 
+@pytest.mark.parametrize("tile", ["64x12", "mixed"])
+def test_many_runs_per_cta(tile):
+    """1216 one-tile replicas (8 per SM): every CTA meets eight runs of sampled
+    tiles, more than the four it keeps in shared memory, so the later runs add
+    their sums straight to the replicas' FP64 sums. Every replica has its
+    sample count, and the replicas checked have their populations and sums
+    as the lattices stepped alone."""
+    nrep = 1216
+    ps = [inputs.LatticeParams(16 + r % 5, 9 + r % 3, 1.0, 0.05 * (r % 4), 0.0, 1e-4,
+                               inputs.omega_groups(1.0 + 0.1 * (r % 3), 0.8, 1.0), inputs.LOCAL,
+                               "fp32", seed=5000 + r, replica=r) for r in range(nrep)]
+    nsteps = 4
+    with flb.Batch(ps, tile=tile) as b:
+        b.set_sampling(0, 1)
+        b.step(nsteps)
+        b.sync()
+        counts = [b.raw_sums(k)[2] for k in range(nrep)]
+        pick = list(range(0, nrep, 97)) + [nrep - 1]
+        got = {k: (b.populations(k), b.raw_sums(k)) for k in pick}
+    assert counts == [nsteps * p.nodes for p in ps]
+    for k in pick:
+        f, (S1, S2, n) = got[k]
+        ref, (R1, R2, rn) = alone(ps[k], nsteps, warmup=0, every=1)
+        np.testing.assert_array_equal(f, ref)
+        assert n == rn
+        assert_sums_close(S1, S2, R1, R2, n, 1e-4, 3e-6 * n * np.sqrt(ps[k].kT),
+                          1e-6 * n * ps[k].kT)
+
+
 @pytest.mark.parametrize("basis", ALL_BASES)
 def test_pooled_correlations(basis):
     """flb_batch_correlations over copies with one rho0, u0 (different seeds
