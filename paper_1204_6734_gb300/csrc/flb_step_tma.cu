@@ -407,7 +407,7 @@ step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
             // CTA's tile kStages later (the counter is never reset: NW divides
             // 2^32)
             __syncwarp();
-            if (lane_id == 0 && ((atomicAdd(&released[s], 1u) + 1u) & (NW - 1)) == 0) {
+            if (lane_id == 0 && ((release_count(&released[s]) + 1u) & (NW - 1)) == 0) {
                 const int tn = t + kStages * gridDim.x;
                 if (tn < a.ntiles) {
                     fence_proxy_async_smem();

@@ -26,6 +26,18 @@ __device__ __forceinline__ void fence_mbar_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
+// Count one release of a stage (acquire-release at CTA scope: the thread that
+// makes the last release also observes every earlier releaser's reads of the
+// stage as complete). Returns the count before this release.
+__device__ __forceinline__ uint32_t release_count(uint32_t* cnt) {
+    uint32_t old;
+    asm volatile("atom.acq_rel.cta.shared::cta.add.u32 %0, [%1], 1;"
+                 : "=r"(old)
+                 : "r"(smem_u32(cnt))
+                 : "memory");
+    return old;
+}
+
 // Orders this thread's view of shared memory before its later asynchronous-proxy
 // (tensor copy) accesses: used before a copy into a stage released through a
 // counter rather than an mbarrier.
