@@ -464,14 +464,16 @@ int flb_server_set_tile(flb_server s, int32_t tile);
  *    FLB_KERNEL_GENERIC (one node per thread, plain loads) or
  *    FLB_KERNEL_PIPELINED (FP32 only). All give the same results up to rounding.
  *  FLB_OPT_PIPELINE_WARPS: colliding warps per CTA of the pipelined kernel
- *    (8, 12 or 16; the tile is 128 x value/2 nodes) for every step. By
- *    default sampling steps use 12 (8 with sampler warps) and steps without
- *    sampling 12 in the f-norm bases, 8 in the Hermite norm. 16 exists with
- *    the tensor-core sums and without sampling only. FP32 only.
+ *    (8, 12, 14 or 16; the tile is 128 x value/2 nodes) for every step. By
+ *    default the f-norm bases use 16 on lattices of at least 8 such tiles
+ *    per SM and 12 below that, the Hermite norm 12 on sampling steps and 8
+ *    without sampling; with sampler warps, 8. 16 (no producer warp: the last
+ *    warp to release a stage refills it) exists with the tensor-core sums
+ *    and without sampling only; choosing sampling mode 1 or 2 then falls back
+ *    to 12. FP32 only.
  *  FLB_OPT_PIPELINE_SAMPLING: how the pipelined kernel accumulates the
  *    correlation sums on sampling steps -- 1: dedicated sampler warps read the
- *    staged tile (FP32 products; the default for the look-up-table f-norm and
- *    where 3 is not allowed); 2: the colliding warps accumulate their own nodes
+ *    staged tile (FP32 products; the default where 3 is not allowed); 2: the colliding warps accumulate their own nodes
  *    (FP32 products); 3 (default): the colliding warps stage their nodes'
  *    deviations (f - f^0(rho0, u0)) / sqrt(kT rho0) in FP16 and add them to a
  *    Gram matrix on the tensor cores, FP32 partials of at most 1024 products
