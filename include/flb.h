@@ -467,10 +467,10 @@ int flb_server_set_tile(flb_server s, int32_t tile);
  *    (8, 12, 14 or 16; the tile is 128 x value/2 nodes) for every step. By
  *    default the f-norm bases use 16 on lattices of at least 8 such tiles
  *    per SM and 12 below that, the Hermite norm 12 on sampling steps and 8
- *    without sampling; with sampler warps, 8. 16 (no producer warp: the last
- *    warp to release a stage refills it) exists with the tensor-core sums
- *    and without sampling only; choosing sampling mode 1 or 2 then falls back
- *    to 12. FP32 only.
+ *    without sampling; with sampler warps, 8. 14 and 16 exist with the
+ *    tensor-core sums and without sampling only (16 without a producer warp:
+ *    the last warp to release a stage refills it); choosing sampling mode 1
+ *    or 2 then falls back to 12. FP32 only.
  *  FLB_OPT_PIPELINE_SAMPLING: how the pipelined kernel accumulates the
  *    correlation sums on sampling steps -- 1: dedicated sampler warps read the
  *    staged tile (FP32 products; the default where 3 is not allowed); 2: the colliding warps accumulate their own nodes
