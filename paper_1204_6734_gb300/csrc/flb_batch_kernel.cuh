@@ -410,7 +410,7 @@ batch_step_kernel(const BatchArgs a) {
     }
     int run = -1, gtiles = 0, run_rep = -1;
     const int wc = c >> 5;
-    const GramLane gl(kTensor ? smem_u32(gram + wc * kGramFullHalves) : 0u);
+    const GramLane gl(kTensor ? smem_u32(gram + wc * kGramFullHalves) : 0u, 16);
     auto gram_out = [&]() {
         if (run < 0) return;
         if (run < kRunSlots)

@@ -12,8 +12,9 @@
 // kGramFlushTiles tiles the FP32 partials of rows and columns 0..9 are added
 // to an FP64 16 x 16 matrix in shared memory (gram_flush). Rows 10..15 of H
 // only reach rows and columns 10..15 of C, which nothing reads: they are not
-// allocated, and ldmatrix reads whatever follows the block there (the next
-// warp's block, or the pad after the last one).
+// allocated, and the ldmatrix lanes of rows 10..15 read the warp's own rows
+// 2..7 (finite values the warp staged itself; rows 8, 9 and 2..7 fall in
+// distinct shared-memory banks).
 //
 // The scale s (sqrt(kT rho0)) makes the thermal fluctuations of order one in
 // FP16, whose rounding (relative 2^-12, unbiased) enters the sums as noise
@@ -34,7 +35,6 @@ namespace flb {
 constexpr int kGramRowHalves = 72;                       // 64 nodes + 8 halves: 144-byte rows
 constexpr int kGramRows = 10;                            // rows of H a warp stages
 constexpr int kGramWarpHalves = kGramRows * kGramRowHalves;   // one warp's block: 1440 bytes
-constexpr int kGramPadHalves = (16 - kGramRows) * kGramRowHalves;   // read past the last block
 constexpr int kGramFlushTiles = 16;                      // FP32 partials of <= 1024 products
 
 // The constant row of a warp's block: row 9, ones.
@@ -44,8 +44,7 @@ __device__ __forceinline__ void gram_init(__half* blk) {
 }
 // A block with all 16 rows (row 9 ones, rows 10..15 zeros), for the batched
 // kernel, which has shared memory to spare: measured 1 % faster there than
-// blocks whose rows 10..15 overlap the next warp's (the one-lattice kernel
-// needs the room for its fifth stage).
+// ten-row blocks (the one-lattice kernel needs the room for its fifth stage).
 constexpr int kGramFullHalves = 16 * kGramRowHalves;
 __device__ __forceinline__ void gram_init_full(__half* blk) {
     const int lane = threadIdx.x & 31;
@@ -72,10 +71,12 @@ __device__ __forceinline__ void mma16816(float (&c)[8], int o, uint32_t a0, uint
 // matrices (0, 2) and (1, 3)).
 struct GramLane {
     uint32_t st, ld;
-    __device__ __forceinline__ explicit GramLane(uint32_t blk) {
+    // rows: the rows the block holds (kGramRows, or 16 for a full block)
+    __device__ __forceinline__ GramLane(uint32_t blk, int rows) {
         const int lane = threadIdx.x & 31, m = lane >> 3, r = lane & 7;
+        const int row = (m & 1) * 8 + r;
         st = blk + 4u * lane;
-        ld = blk + 2u * (((m & 1) * 8 + r) * kGramRowHalves + (m >> 1) * 8);
+        ld = blk + 2u * ((row < rows ? row : row - 8) * kGramRowHalves + (m >> 1) * 8);
     }
 };
 

@@ -148,10 +148,10 @@ struct WarpCount {
 };
 
 // Shared memory of the tensor-sampling mode beyond the ring and the reduction
-// buffer: one Gram block per colliding warp, and the pad the last one reads past.
+// buffer: one Gram block per colliding warp.
 template <int NW>
 constexpr size_t gram_smem_bytes() {
-    return ((size_t)NW * kGramWarpHalves + kGramPadHalves) * sizeof(__half);
+    return (size_t)NW * kGramWarpHalves * sizeof(__half);
 }
 
 // Every shape fits the 227 KB of shared memory a CTA may take.
@@ -312,7 +312,7 @@ step_tma_kernel(const __grid_constant__ CUtensorMap map, const TmaArgs a,
         for (int q = 0; q < 8; ++q) gc[q] = 0.f;
     }
     int gtiles = 0;
-    const GramLane gblk(smem_u32(gram + warp * kGramWarpHalves));
+    const GramLane gblk(smem_u32(gram + warp * kGramWarpHalves), kGramRows);
     int k = 0, s = 0, n = 0;   // tile count, its stage and the stage's use
     bool timed_out = false;
     TileWalk w(blockIdx.x, gridDim.x, a.tiles_x);
