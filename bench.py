@@ -34,8 +34,8 @@ BYTES_PER_NODE = {"fp32": 72, "fp64": 144}
 # the same kernel (156.3 + 101.4 MB) times the 4x nodes; a full-size capture
 # may take only the launch list. Valid only for the kernel version it was
 # taken on.
-DRAM_TRAFFIC = {("fp32", "local", 4096): 4 * (156.00e6 + 101.36e6),
-                ("fp32", "lut", 4096): 4 * (156.00e6 + 102.24e6)}
+DRAM_TRAFFIC = {("fp32", "local", 4096): 4 * (156.00e6 + 101.18e6),
+                ("fp32", "lut", 4096): 4 * (156.00e6 + 102.08e6)}
 TRAFFIC_SOURCE = "ncu dram bytes of a 2048^2 launch of the same kernel, x 4 (the nodes)"
 # FP64 operations per node-step of the FP64 step kernel (f-norm, sampling
 # every step): 2 DFMA + DADD + DMUL thread instructions counted by ncu on a
@@ -46,10 +46,10 @@ FP64_FLOPS_PER_NODE = {"local": 1070.0}
 FP64_NOMINAL_TFLOPS = 1.25
 # Warp instructions per node-step of the FP32 step kernel with sampling every
 # step (tensor-core sums, 16 colliding warps), from ncu smsp__inst_executed.sum
-# of a 2048^2 launch (51.8 M and 53.5 M over 4.19 M nodes): with the issue rate
+# of a 2048^2 launch (51.9 M and 53.7 M over 4.19 M nodes): with the issue rate
 # of the GPU (4 schedulers per SM, one warp instruction per cycle each) they
 # give the issue ceiling the f-norm step is bound by.
-INSTR_PER_NODE = {("fp32", "local"): 12.34, ("fp32", "lut"): 12.77}
+INSTR_PER_NODE = {("fp32", "local"): 12.37, ("fp32", "lut"): 12.80}
 SCHEDULERS_PER_SM = 4
 
 
