@@ -1,21 +1,26 @@
 // flb_step_tma.cu -- the pipelined FP32 fused step for sm_103a.
 //
 // Persistent CTAs walk the lattice in tiles of 128 x TH nodes (TH = NW / 2).
-// One producer warp streams, for every tile and every plane i, the box of
-// 136 x TH populations that the pull g_i(x) = f*_i(x - v_i) of the tile needs
-// (shifted by v_iy rows; 4 extra columns on each side cover v_ix = +-1) from
-// HBM into a ring of shared-memory stages with 2D TMA copies, signalling
-// mbarriers. NW consumer warps take two nodes per thread -- node A at tile
-// column r, node B at r + 64 -- read their nine shifted populations from shared
-// memory, release the stage, and collide both nodes at once in packed FP32x2
-// arithmetic (flb_collide.cuh with V = f2). Stores go straight to HBM, rows
-// coalesced, with the ghost copies of boundary nodes (flb_layout.cuh).
+// For every tile and every plane i, the box of 136 x TH populations that the
+// pull g_i(x) = f*_i(x - v_i) of the tile needs (shifted by v_iy rows; 4 extra
+// columns on each side cover v_ix = +-1) streams from HBM into a ring of
+// shared-memory stages with 2D TMA copies, signalling mbarriers. NW consumer
+// warps take two nodes per thread -- node A at tile column r, node B at
+// r + 64 -- read their nine shifted populations from shared memory, collide
+// both nodes at once in packed FP32x2 arithmetic (flb_collide.cuh with
+// V = f2), release the stage and store straight to HBM, rows coalesced, with
+// the ghost copies of edge nodes (flb_layout.cuh).
 //
-// With sampling on, TH sampler warps (one per tile row) read the same stage and
-// accumulate the 9 + 45 correlation sums in packed FP32x2 registers while the
-// consumers collide; the first sampler lane also issues the TMA loads. At the
-// end the CTA reduces the sums to FP64 and adds them to the running sums with
-// FP64 atomics: no separate reduction launch and no serial tail.
+// Who refills a stage: a producer warp beside 8 to 14 consumer warps; with 16
+// consumer warps (no room for a 17th) the last warp to release a stage.
+//
+// Correlation sums on sampling steps: by default each consumer warp stages its
+// nodes' deviations in FP16 and adds them to a Gram matrix on the tensor cores
+// (flb_gram.cuh); otherwise sampler warps read the same stage and accumulate
+// the 9 + 45 sums in packed FP32x2 registers, or the consumers accumulate their
+// own nodes. At the end the CTA reduces the sums to FP64 and adds them to the
+// running sums with FP64 atomics: no separate reduction launch and no serial
+// tail.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
